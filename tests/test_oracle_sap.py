@@ -1,0 +1,183 @@
+"""Pins of the oracle's Schwarz method, block MR and FGMRES.
+
+Sec. 3.1 of the paper names "the MR inversion within a domain" (Table 1) and
+"the entire Schwarz method" (Table 2) without defining them. The oracle's
+reading (red-black multiplicative Schwarz, even-odd Schur complement on odd
+sites, minimal-residual steps, right-preconditioned FGMRES) is pinned here by
+dense linear algebra on tiny lattices and by exact invariances:
+  * MR run to convergence reproduces the dense block inverse D_B^-1,
+  * the even-site block residual vanishes for every MR step count (exact
+    reconstruction), and one MR step is the least-squares optimum on span{bhat},
+  * one sweep with exact block solves equals K0 b + K1 (b - D K0 b),
+  * complex homogeneity and gauge covariance of the fixed-step smoother,
+  * FGMRES reaches a true residual of 1e-10 and agrees with a dense LU solve.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from test_oracle_operator import gauge_transform
+
+DIMS = (4, 4, 4, 4)
+V = 256
+BD = (2, 2, 2, 2)
+
+
+@pytest.fixture(scope="module")
+def op(small_gauge):
+    return oracle.Operator(DIMS, small_gauge, c_sw=1.0, m0=0.1)
+
+
+def _block_dense(op, bd, blk):
+    """D_B on the block's sites as a dense (12 vb) x (12 vb) matrix."""
+    sites = op.block_sites(bd, blk)
+    n = 12 * len(sites)
+    M = np.empty((n, n), dtype=complex)
+    for j in range(n):
+        e = np.zeros((V, 12), dtype=complex)
+        e[sites[j // 12], j % 12] = 1
+        M[:, j] = op.apply_block(bd, blk, e).reshape(V, 12)[sites].reshape(-1)
+    return sites, M
+
+
+def _parity(sites):
+    T, Z, Y, X = DIMS
+    x = sites % X
+    y = (sites // X) % Y
+    z = (sites // (X * Y)) % Z
+    t = sites // (X * Y * Z)
+    return (x + y + z + t) % 2
+
+
+def test_block_operator_drops_outgoing_hops(op):
+    """D_B equals D restricted to the block with hops to outside sites removed:
+    applying D to a vector supported on the block and restricting to it gives D_B."""
+    r = synth.gaussian_spinor(V, 3)
+    for blk in (0, 5):
+        sites = op.block_sites(BD, blk)
+        v = np.zeros_like(r)
+        v[sites] = r[sites]
+        full = op.apply(v)[sites]
+        blockwise = op.apply_block(BD, blk, v)[sites]
+        assert np.allclose(full, blockwise, atol=1e-14)
+
+
+def test_mr_to_convergence_is_dense_block_inverse(op):
+    r = synth.gaussian_spinor(V, 4)
+    for blk in (0, 9):
+        sites, M = _block_dense(op, BD, blk)
+        e = op.block_solve(BD, blk, r, nmr=200)
+        want = np.linalg.solve(M, r[sites].reshape(-1))
+        got = e[sites].reshape(-1)
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-10
+
+
+@pytest.mark.parametrize("nmr", [0, 1, 2, 5])
+def test_even_residual_exact_and_mr_optimal(op, nmr):
+    r = synth.gaussian_spinor(V, 5)
+    blk = 3
+    sites, M = _block_dense(op, BD, blk)
+    par = np.repeat(_parity(sites), 12)
+    ev, od = par == 0, par == 1
+    rb = r[sites].reshape(-1)
+    e = op.block_solve(BD, blk, r, nmr=nmr)[sites].reshape(-1)
+    res = rb - M @ e
+    assert np.linalg.norm(res[ev]) < 1e-13 * np.linalg.norm(rb)
+    # odd residual equals the Schur residual bhat - Dhat e_o
+    Dee, Deo, Doe, Doo = M[np.ix_(ev, ev)], M[np.ix_(ev, od)], M[np.ix_(od, ev)], M[np.ix_(od, od)]
+    Dhat = Doo - Doe @ np.linalg.solve(Dee, Deo)
+    bhat = rb[od] - Doe @ np.linalg.solve(Dee, rb[ev])
+    assert np.allclose(res[od], bhat - Dhat @ e[od], atol=1e-12)
+    if nmr == 1:
+        alpha = np.linalg.lstsq((Dhat @ bhat)[:, None], bhat, rcond=None)[0][0]
+        assert np.allclose(e[od], alpha * bhat, atol=1e-13)
+
+
+def test_mr_residual_decreases(op):
+    r = synth.gaussian_spinor(V, 6)
+    blk = 2
+    sites, M = _block_dense(op, BD, blk)
+    rb = r[sites].reshape(-1)
+    norms = [np.linalg.norm(rb - M @ op.block_solve(BD, blk, r, nmr=k)[sites].reshape(-1))
+             for k in range(6)]
+    assert all(b < a for a, b in zip(norms, norms[1:]))
+
+
+def test_block_colouring_is_red_black(op):
+    nb = op.nblocks(BD)
+    col = np.array([op.block_colour(BD, b) for b in range(nb)])
+    assert col.sum() == nb // 2
+    # neighbouring blocks (differing by one block step) have opposite colours
+    T, Z, Y, X = [a // b for a, b in zip(DIMS, BD)]
+    c = col.reshape(T, Z, Y, X)
+    for ax in range(4):
+        assert np.all(c != np.roll(c, 1, axis=ax))
+
+
+def test_one_sweep_with_exact_block_solves_matches_dense_formula(op):
+    """x = K0 b + K1 (b - D K0 b), K_c = sum over colour-c blocks of I_B D_B^-1 I_B^T."""
+    b = synth.gaussian_spinor(V, 7).reshape(V, 12)
+    D = op.dense()
+    nb = op.nblocks(BD)
+    K = [np.zeros((12 * V, 12 * V), dtype=complex) for _ in range(2)]
+    for blk in range(nb):
+        sites, M = _block_dense(op, BD, blk)
+        idx = (sites[:, None] * 12 + np.arange(12)[None, :]).reshape(-1)
+        K[op.block_colour(BD, blk)][np.ix_(idx, idx)] = np.linalg.inv(M)
+    bv = b.reshape(-1)
+    x0 = K[0] @ bv
+    want = x0 + K[1] @ (bv - D @ x0)
+    got = op.sap(BD, b, nsweep=1, nmr=200).reshape(-1)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-10
+
+
+def test_sweeps_compose(op):
+    b = synth.gaussian_spinor(V, 8)
+    x1 = op.sap(BD, b, nsweep=1, nmr=3)
+    x2 = op.sap(BD, b, nsweep=2, nmr=3)
+    assert np.allclose(op.sap(BD, b, nsweep=1, nmr=3, x0=x1), x2, atol=1e-14)
+
+
+def test_sap_complex_homogeneity(op):
+    b = synth.gaussian_spinor(V, 9)
+    c = 0.37 - 2.1j
+    x = op.sap(BD, b, 4, 3)
+    assert np.allclose(op.sap(BD, c * b, 4, 3), c * x, atol=1e-13)
+
+
+def test_sap_and_fgmres_gauge_covariance(small_gauge):
+    G = synth.su3_field(V, 1.0, seed=44)
+    Up = gauge_transform(small_gauge, G, DIMS)
+    op = oracle.Operator(DIMS, small_gauge, 1.0, 0.1)
+    opp = oracle.Operator(DIMS, Up, 1.0, 0.1)
+    b = synth.gaussian_spinor(V, 2)
+    Gb = np.einsum("nab,nsb->nsa", G, b)
+    Gx = lambda x: np.einsum("nab,nsb->nsa", G, x)
+    x = op.sap(BD, b, 4, 3)
+    assert np.linalg.norm(opp.sap(BD, Gb, 4, 3) - Gx(x)) / np.linalg.norm(x) < 1e-12
+    xs, ok, _ = op.fgmres(BD, b, 16, 1e-10, 200, 4, 3)
+    xps, okp, _ = opp.fgmres(BD, Gb, 16, 1e-10, 200, 4, 3)
+    assert ok and okp
+    assert np.linalg.norm(xps - Gx(xs)) / np.linalg.norm(xs) < 1e-9
+
+
+def test_fgmres_matches_dense_lu(op):
+    """Plain FP64 workload on 4^4: true residual <= 1e-10 and agreement with LU."""
+    b = synth.gaussian_spinor(V, 2)
+    D = op.dense()
+    x_lu = np.linalg.solve(D, b.reshape(-1))
+    x, ok, st = op.fgmres(BD, b, restart=16, tol=1e-10, max_iter=500, nsweep=4, nmr=3)
+    assert ok and st["rel_residual"] <= 1e-10
+    true_res = np.linalg.norm(b.reshape(-1) - D @ x.reshape(-1)) / np.linalg.norm(b)
+    assert true_res <= 1e-10
+    kappa = np.linalg.cond(D)
+    assert np.linalg.norm(x.reshape(-1) - x_lu) / np.linalg.norm(x_lu) <= kappa * 1e-10
+
+
+def test_fgmres_max_iter_and_zero_rhs(op):
+    b = synth.gaussian_spinor(V, 2)
+    x, ok, st = op.fgmres(BD, b, restart=4, tol=1e-14, max_iter=2, nsweep=1, nmr=1)
+    assert not ok and st["iterations"] == 2 and 0 < st["rel_residual"] < 1
+    x, ok, st = op.fgmres(BD, np.zeros_like(b), 16, 1e-10, 10, 4, 3)
+    assert ok and not x.any()
