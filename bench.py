@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Benchmark of the Wilson-clover SAP-FGMRES hot path on GB300.
+
+A step is one full solve of D x = b to a true relative residual of 1e-10 on
+the 64 x 32^3 workload (T x L^3): links exp(i 0.25 H) with two stout steps
+(rho = 0.1), c_sw = 1.7, m0 = -0.02, Gaussian right-hand side; Schwarz
+smoother with 4^4 blocks, 4 sweeps x 4 MR steps in FP32 storage; FGMRES(16)
+with FP64 orthogonalisation, least-squares update and true residual.
+
+Prints one JSON line. `value` is solves/s with all inputs resident in HBM;
+`e2e` is the same metric through dd_solve with host buffers (host-to-device
+copy of b and device-to-host copy of x inside the timed region). `dslash`
+reports apply_D's HBM throughput, `roofline` the dominant kernel against the
+measured peaks. Under torchrun (N > 1) every rank solves its own replica of
+the problem (the path has no exchange between GPUs), so scaling is weak.
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOAD = "sap_fgmres_64x32^3_fp32"
+METRIC = "Dslash GB/s & % HBM peak; SAP-FGMRES solves/s, p50/p99 at 1e-10 residual"
+# Per-site algorithmic traffic (reals): apply_D reads in 24, links 72, clover 72
+# and writes out 24; one Schwarz sweep reads links 72, A 72, A_ee^-1 36 (72 per
+# even site), b 24, x 24 and writes x 24.
+DSLASH_REALS = 192
+SAP_REALS_PER_SWEEP = 252
+# Algorithmic flops per site: Wilson-clover apply 1848 (1320 hopping + 504
+# clover + 24); one Schwarz sweep with n MR steps 1848 + 1500 + 1630 n.
+DSLASH_FLOPS = 1848
+
+
+def sap_flops_per_site(nmr):
+    return 1848 + 1500 + 1630 * nmr
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=d["hbm_gbs"], bf16=d.get("bf16_tflops"), src="measured",
+                    sm_max_mhz=d.get("sm_max_mhz", 2070.0))
+    return dict(hbm_gbs=6800.0, bf16=1900.0, src="fallback", sm_max_mhz=2070.0)
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def kernel_traffic(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary, only while the
+    kernel's source is unchanged since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, d["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] if os.path.exists(src) else None
+    return d["bytes_per_launch"] if h == d.get("source_sha256_16") else None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.samples, self.proc, self.index = [], None, index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 8:
+                self.samples.append(f)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        reasons = set()
+        for s in self.samples:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               s[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(self.samples[0][2]) if self.samples[0][2].replace(".", "").isdigit() else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def setup_problem(wl):
+    dims = wl["dims"]
+    U = synth.gauge(dims, wl["eps"], wl["n_stout"], wl["rho"], wl["gauge_seed"])
+    b = synth.gaussian_spinor(int(np.prod(dims)), wl["rhs_seed"])
+    return U, b
+
+
+def oracle_operator(wl, U):
+    import oracle
+    t0 = time.perf_counter()
+    op = oracle.Operator(wl["dims"], U, wl["c_sw"], wl["m0"])
+    return op, time.perf_counter() - t0
+
+
+def oracle_sample(wl, U, b, iters, cycles, op=None, t_setup=None):
+    """Time the FP64 oracle on a bounded sample of the workload (one Dslash and
+    one Schwarz sweep over the full lattice plus one orthogonalisation step)
+    and scale it to one solve with the given iteration and cycle counts."""
+    if op is None:
+        op, t_setup = oracle_operator(wl, U)
+    t0 = time.perf_counter()
+    op.apply(b)
+    t_apply = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    op.sap(wl["block"], b, 1, wl["mr_steps"])
+    t_sweep = time.perf_counter() - t0
+    v = b.reshape(-1)
+    t0 = time.perf_counter()
+    for _ in range(wl["restart"] // 2 + 1):    # average Gram-Schmidt length
+        h = np.vdot(v, v)
+        v = v - h * 1e-3 * v
+    t_orth = 2 * (time.perf_counter() - t0)
+    t_iter = wl["sweeps"] * t_sweep + t_apply + t_orth
+    t_solve = iters * t_iter + (cycles + 1) * t_apply
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dict(value=1.0 / t_solve, unit="solves/s", cores=cores, kind="oracle",
+                sample=(f"FP64 oracle on the full {'x'.join(map(str, wl['dims']))} lattice: one apply_D "
+                        f"({t_apply:.2f} s), one Schwarz sweep ({t_sweep:.2f} s), one Gram-Schmidt pass "
+                        f"({t_orth:.2f} s); scaled to {iters} iterations x ({wl['sweeps']} sweeps + apply + "
+                        f"orthogonalisation) + {cycles + 1} true residuals; operator set-up {t_setup:.1f} s "
+                        f"not counted"),
+                seconds_per_solve=t_solve)
+
+
+# iteration / cycle counts of this workload's solve (FP32 smoother), used to
+# scale the oracle's bounded sample to one solve
+REF_ITERS, REF_CYCLES = 62, 4
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    wl = synth.WORKLOADS[args.workload]
+    U, b = setup_problem(wl)
+    op, t_setup = oracle_operator(wl, U)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(wl, U, b, REF_ITERS, REF_CYCLES, op, t_setup)
+        if i >= args.warmup:
+            vals.append(r)
+    v = float(np.median([r["value"] for r in vals]))
+    cb = dict(vals[-1])
+    cb["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_of(wl), "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def config_of(wl):
+    return {"workload": WORKLOAD if wl is synth.WORKLOADS.get(WORKLOAD) else "custom",
+            "dims_TZYX": list(wl["dims"]), "block_TZYX": list(wl["block"]), "sweeps": wl["sweeps"],
+            "mr_steps": wl["mr_steps"], "restart": wl["restart"], "tol": 1e-10, "smoother_storage": "f32",
+            "outer": "f64", "c_sw": wl["c_sw"], "m0": wl["m0"], "eps": wl["eps"], "n_stout": wl["n_stout"],
+            "l2": "inputs larger than L2 (operator fields 1.8 GB, each vector 0.2-0.4 GB)"}
+
+
+def ev_time(fn, reps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_1710_07041_gb300 as dd
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        dist = tdist
+    wl = synth.WORKLOADS[args.workload]
+    prec = dd.PREC[args.prec]
+    U, b = setup_problem(wl)
+    V = int(np.prod(wl["dims"]))
+    lat = dd.Lattice(wl["dims"], wl["block"])
+    gauge = dd.Gauge(lat, U)
+    op = dd.Op(gauge, wl["c_sw"], wl["m0"], prec)
+    stream = torch.cuda.current_stream()
+    L = dd.lib()
+    kw = dict(tol=1e-10, restart=wl["restart"], sweeps=wl["sweeps"], mr_steps=wl["mr_steps"], max_iter=2000)
+
+    # device-resident inputs
+    b_dev = torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda()
+    x_dev = torch.zeros_like(b_dev)
+    for _ in range(args.warmup):
+        op.solve(b_dev, x_dev, **kw)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    lat_ms, infos = [], []
+    l0 = L.dd_kernel_launches()
+    with Clocks(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            _, info = op.solve(b_dev, x_dev, **kw)
+            s1.record(stream)
+            s1.synchronize()
+            lat_ms.append(s0.elapsed_time(s1))
+            infos.append(info[0])
+        e1.record(stream)
+        e1.synchronize()
+    launches = L.dd_kernel_launches() - l0
+    total_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    value = world * args.steps / (total_ms / 1e3)
+
+    # end to end through dd_solve with pinned host buffers
+    bh = torch.from_numpy(b.view(np.float64).reshape(-1).copy()).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    bh_np, xh_np = bh.numpy(), xh.numpy()
+    op.solve(bh_np, xh_np, **kw)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 2)):
+        op.solve(bh_np, xh_np, **kw)
+    e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # kernel-level timing: apply_D and one Schwarz phase (launch), FP32
+    fin = lat.to_field(b, dd.F32)
+    fout = lat.new_field(dd.F32)
+    for _ in range(5):
+        op.apply_D(dd.F32, fin, fout)
+    dslash_ms = ev_time(lambda: op.apply_D(dd.F32, fin, fout), 50, stream)
+    fbp = lat.to_field(b, prec)
+    fxp = lat.new_field(prec)
+    op.sap_smooth(fbp, fxp, wl["sweeps"], wl["mr_steps"])
+    sap_ms = ev_time(lambda: op.sap_smooth(fbp, fxp, wl["sweeps"], wl["mr_steps"]), 5, stream)
+    sap_launch_ms = sap_ms / (2 * wl["sweeps"])
+
+    peaks = measured_peaks()
+    real_b = {dd.F64: 8, dd.F32: 4, dd.F16: 2, dd.BF16: 2}
+    dslash_bytes = DSLASH_REALS * 4 * V
+    dslash_gbs = dslash_bytes / (dslash_ms * 1e-3) / 1e9
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or peaks["sm_max_mhz"]
+    alu_peak = fp32_alu_peak_tflops(peaks["sm_max_mhz"])
+    sap_flops_launch = sap_flops_per_site(wl["mr_steps"]) * V / 2
+    sap_tflops = sap_flops_launch / (sap_launch_ms * 1e-3) / 1e12
+    sap_bytes_launch = SAP_REALS_PER_SWEEP * real_b[prec] * V / 2
+    mean_info = {k: float(np.mean([i[k] for i in infos])) for k in ("ms_sap", "ms_dirac", "ms_orth", "ms_total")}
+    roofline_sap = {"kernel": "k_sap_phase", "bound": "alu", "achieved": sap_tflops, "peak": alu_peak,
+                    "unit": "TFLOP/s", "frac": sap_tflops / alu_peak,
+                    "traffic": kernel_traffic("k_sap_phase"),
+                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz",
+                    "algorithmic_bytes_per_launch": sap_bytes_launch,
+                    "hbm_frac": sap_bytes_launch / (sap_launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                    "ms_per_launch": sap_launch_ms}
+    roofline_dslash = {"kernel": "k_dirac<float>", "bound": "hbm", "achieved": dslash_gbs,
+                       "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": dslash_gbs / peaks["hbm_gbs"],
+                       "traffic": kernel_traffic("k_dirac<float>"), "peak_source": peaks["src"],
+                       "ms_per_launch": dslash_ms}
+    dominant = roofline_sap if mean_info["ms_sap"] >= mean_info["ms_dirac"] else roofline_dslash
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == dd.F32 else args.prec,
+        "data": "synthetic", "config": config_of(wl),
+        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99))},
+        "solve": {"iterations": int(infos[-1]["iterations"]), "cycles": int(infos[-1]["cycles"]),
+                  "true_rel_residual": max(i["true_rel_residual"] for i in infos), **mean_info},
+        "dslash": {"GB/s": dslash_gbs, "frac_hbm": dslash_gbs / peaks["hbm_gbs"], "ms": dslash_ms,
+                   "hbm_peak_gbs": peaks["hbm_gbs"], "peak_source": peaks["src"]},
+        "roofline": dominant,
+        "roofline_other": roofline_dslash if dominant is roofline_sap else roofline_sap,
+        "e2e": {"value": world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": V * 24 * 8,
+                "d2h_bytes_per_step": V * 24 * 8},
+        "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_sample(wl, U, b, int(infos[-1]["iterations"]), int(infos[-1]["cycles"]))
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    op.close()
+    gauge.close()
+    lat.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_kernels(args):
+    """Kernel-level loop for profiler captures: apply_D (F32 and the smoother
+    precision) and Schwarz sweeps on the workload, plus one short solve."""
+    import torch
+
+    import paper_1710_07041_gb300 as dd
+
+    wl = synth.WORKLOADS[args.workload]
+    prec = dd.PREC[args.prec]
+    U, b = setup_problem(wl)
+    lat = dd.Lattice(wl["dims"], wl["block"])
+    gauge = dd.Gauge(lat, U)
+    op = dd.Op(gauge, wl["c_sw"], wl["m0"], prec)
+    stream = torch.cuda.current_stream()
+    fin, fout = lat.to_field(b, dd.F32), lat.new_field(dd.F32)
+    fbp, fxp = lat.to_field(b, prec), lat.new_field(prec)
+    res = {}
+    for name, fn, reps in (("apply_D_f32", lambda: op.apply_D(dd.F32, fin, fout), 20),
+                           ("sap", lambda: op.sap_smooth(fbp, fxp, wl["sweeps"], wl["mr_steps"]), 3)):
+        for _ in range(args.warmup):
+            fn()
+        res[name + "_ms"] = ev_time(fn, max(1, min(reps, args.steps)), stream)
+    _, info = op.solve(b, tol=1e-10, restart=wl["restart"], sweeps=wl["sweeps"], mr_steps=wl["mr_steps"],
+                       max_iter=args.solve_iters, raise_on_notconv=False)
+    res["solve"] = info[0]
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],
+                    help="kernels: short kernel loop for profiler captures (no contract line)")
+    ap.add_argument("--solve-iters", type=int, default=20, help="iteration cap of the solve in --mode kernels")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.mode == "kernels":
+        run_kernels(args)
+    elif args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

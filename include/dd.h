@@ -1,0 +1,237 @@
+/*
+ * dd.h - C ABI of the GB300 Wilson-clover SAP-FGMRES library (sm_103a).
+ *
+ * What it computes. The paper (arXiv:1710.07041, "DD-alpha-AMG on QPACE 3")
+ * ports the DD-alpha-AMG solver for "the discretized form of the Dirac
+ * equation" (Sec. 1); its two hot code parts are "the MR inversion within a
+ * domain" (Sec. 3.1, Table 1) and "the entire Schwarz method" (Sec. 3.1,
+ * Table 2), the fine-grid smoother, with some data stored in half precision
+ * (Sec. 3, Listing 1: round-to-nearest conversion). The paper does not print
+ * the formulas; this library implements the standard ones:
+ *
+ *   (D psi)(n) = A(n) psi(n)
+ *       - 1/2 sum_mu [(1 - g_mu) U_mu(n) psi(n+mu) + (1 + g_mu) U_mu(n-mu)^+ psi(n-mu)]
+ *   A(n) = (4 + m0) + C(n),
+ *   C(n) = -(c_sw/32) sum_{mu,nu} g_mu g_nu (x) (Q_mu,nu(n) - Q_nu,mu(n)),
+ *
+ * Q_mu,nu the four-leaf clover sum; chiral gamma basis g_k = [[0,-i s_k],[i s_k,0]],
+ * g_t = [[0,1],[1,0]]; periodic space, antiperiodic time (optional). The
+ * smoother is red-black multiplicative Schwarz over lattice blocks, each block
+ * solved by even-odd (odd-site Schur complement) minimal-residual steps; the
+ * outer solver is FGMRES(m) right-preconditioned by it, with its Arnoldi
+ * orthogonalisation, least-squares update and true residual in FP64.
+ *
+ * Conventions.
+ *   dims  = {T, Z, Y, X}; canonical site n = x + X*(y + Y*(z + Z*t)).
+ *   block = {bt, bz, by, bx}: Schwarz block and storage tile; each extent a
+ *           power of two >= 2, dividing the lattice, with an even number of
+ *           blocks in every direction (red-black colouring).
+ *   Canonical host arrays are FP64, complex = [re, im]:
+ *     links  [V][4][3][3][2]  (mu = 0:x 1:y 2:z 3:t, row-major colour matrix)
+ *     spinor [V][4][3][2]     (spin-major, colour minor), nrhs of them back to back.
+ *   Device fields passed to dd_apply_D / dd_sap_smooth are in the library's
+ *   internal blocked layout for a given precision; dd_field_bytes gives the
+ *   size of one field and dd_pack / dd_unpack convert from / to canonical FP64.
+ *
+ * Ownership. dd_create_* copy what they need into library-owned device memory;
+ *   the caller may free its arrays on return. dd_destroy frees a handle. Device
+ *   buffers passed to compute calls are owned by the caller and must stay
+ *   valid until the work queued on the given stream has finished.
+ *
+ * Errors. Every int-returning call returns DD_OK (0) or a negative DD_E* code
+ *   and never aborts or traps; dd_last_error() returns a message for the
+ *   calling thread's most recent failure.
+ *
+ * Streams. `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream). Compute calls are asynchronous on that stream unless stated.
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DD_OK = 0,
+  DD_EINVAL = -1,     /* bad argument (null pointer, bad sizes or layout)      */
+  DD_ENOMEM = -2,     /* device or host allocation failed                      */
+  DD_ECUDA = -3,      /* a CUDA runtime call failed                            */
+  DD_ENOTCONV = -4,   /* max_iter reached; x holds the best iterate            */
+  DD_ETIMEOUT = -5,   /* a bounded device or host wait expired                 */
+  DD_ECANCELLED = -6, /* the request was cancelled                             */
+  DD_EBUSY = -7,      /* admission refused (memory budget or slots)            */
+  DD_ENOTFOUND = -8   /* unknown ticket                                        */
+};
+
+/* storage precisions; arithmetic is FP32 for all but DD_F64 */
+enum { DD_F64 = 0, DD_F32 = 1, DD_F16 = 2, DD_BF16 = 3 };
+
+/* data location flags for dd_solve / requests */
+enum { DD_HOST = 0, DD_DEVICE = 1 };
+
+typedef struct dd_lattice_s *dd_lattice_t;
+typedef struct dd_gauge_s *dd_gauge_t;
+typedef struct dd_op_s *dd_op_t;
+typedef struct dd_server_s *dd_server_t;
+
+/* Library version string, never NULL. */
+const char *dd_version(void);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *dd_last_error(void);
+
+/* Diagnostics: number of CUDA kernels this library has launched so far in
+ * this process (all threads). */
+uint64_t dd_kernel_launches(void);
+
+/* ------------------------------------------------------------------ setup */
+
+/* Lattice geometry and storage tiling. dims {T,Z,Y,X} >= 2 each; block as in
+ * Conventions. antiperiodic_t != 0 puts a -1 on fermion hops across the time
+ * edge. Returns DD_EINVAL on a bad shape. */
+int dd_create_lattice(const int dims[4], const int block[4], int antiperiodic_t, dd_lattice_t *out);
+
+/* Number of sites V and the bytes of one spinor field of precision `prec`. */
+long dd_lattice_volume(dd_lattice_t lat);
+size_t dd_field_bytes(dd_lattice_t lat, int prec);
+
+/* Gauge field from host links [V][4][3][3][2] (canonical, FP64). Synchronous. */
+int dd_create_gauge(dd_lattice_t lat, const double *links_host, dd_gauge_t *out);
+
+/* Wilson-clover operator on `gauge` with clover coefficient c_sw and bare mass
+ * m0, for the Schwarz smoother's storage precision `prec` (DD_F64, DD_F32,
+ * DD_F16, DD_BF16). Builds on the device (FP64): the clover term C(n) from the
+ * four-leaf plaquette sum, A(n) = 4 + m0 + C(n) as two 6x6 Hermitian chirality
+ * blocks per site, and the inverses of the even-site blocks; stores them in
+ * FP64 (true residual), FP32 (outer-solver operator) and `prec` (smoother).
+ * Returns DD_EINVAL if a 6x6 block is singular. Synchronous. */
+int dd_create_op(dd_gauge_t gauge, double c_sw, double m0, int prec, dd_op_t *out);
+
+/* Copy the clover site blocks A(n) of `op` (FP64) to host memory as
+ * [V][2][6][6][2] (chirality block h = spins {2h, 2h+1}; row/column index
+ * 3*(spin - 2h) + colour), canonical site order. Synchronous. */
+int dd_op_get_clover(dd_op_t op, double *host_out);
+
+/* Free any handle returned by this library (lattice, gauge, op, server).
+ * Destroying a lattice or gauge still used by an op is deferred until the op
+ * is destroyed. NULL is ignored. */
+void dd_destroy(void *handle);
+
+/* ----------------------------------------------------------- layouts */
+
+/* Canonical FP64 spinors (device memory, [nrhs][V][4][3][2]) -> internal
+ * layout of precision `prec`, each value multiplied by `scale`, rounded to
+ * nearest even. Asynchronous on `stream`. */
+int dd_pack(dd_lattice_t lat, int prec, const double *canon_dev, void *field_dev, int nrhs,
+            double scale, void *stream);
+
+/* Internal layout of precision `prec` -> canonical FP64 (device memory),
+ * multiplied by `scale`. Asynchronous on `stream`. */
+int dd_unpack(dd_lattice_t lat, int prec, const void *field_dev, double *canon_dev, int nrhs,
+              double scale, void *stream);
+
+/* ------------------------------------------------------------ compute */
+
+/* out = D in for nrhs fields (internal layout, precision `prec`, field r at
+ * byte offset r * dd_field_bytes). `prec` must be DD_F64, DD_F32 or the op's
+ * smoother precision. in and out must not overlap. Asynchronous. */
+int dd_apply_D(dd_op_t op, int prec, const void *in_dev, void *out_dev, int nrhs, void *stream);
+
+typedef struct {
+  int sweeps;     /* Schwarz sweeps (each = colour 0 then colour 1), >= 1        */
+  int mr_steps;   /* MR steps per block solve, >= 0                              */
+  int x_is_zero;  /* 1: x is not read and taken as 0 (preconditioner use)        */
+  int rhs_tile;   /* right-hand sides sharing one staged block (0 = autotuned)   */
+} dd_sap_params;
+
+/* Schwarz alternating procedure in the op's smoother precision: x is updated
+ * by `sweeps` red-black sweeps for the system D x = b, each block solved by
+ * even-odd MR (Sec. 3.1, Tables 1-2). b and x: nrhs internal-layout fields of
+ * that precision. Asynchronous. */
+int dd_sap_smooth(dd_op_t op, const dd_sap_params *p, const void *b_dev, void *x_dev, int nrhs,
+                  void *stream);
+
+typedef struct {
+  double tol;           /* target true relative residual ||b - D x|| / ||b||        */
+  int restart;          /* FGMRES restart length m (1..64)                          */
+  int max_iter;         /* cap on preconditioned Arnoldi steps per right-hand side  */
+  dd_sap_params sap;    /* smoother applied once per Arnoldi step                   */
+  double inner_reduction; /* a cycle stops once its estimate fell by this factor
+                             (0: run to tol; mixed precision uses ~1e-5)            */
+  int where;            /* DD_HOST or DD_DEVICE for b and x                          */
+  int use_x0;           /* 1: x holds the initial guess; 0: start from x = 0         */
+} dd_solve_params;
+
+typedef struct {
+  int status;             /* DD_OK, DD_ENOTCONV, ...                               */
+  int iterations;         /* preconditioned Arnoldi steps                          */
+  int cycles;             /* restart cycles                                        */
+  double true_rel_residual; /* ||b - D x|| / ||b|| in FP64 at exit                  */
+  double est_rel_residual;  /* FGMRES estimate at exit                              */
+  double ms_total, ms_sap, ms_dirac, ms_orth; /* wall time split (ms)               */
+} dd_solve_info;
+
+/* Solve D x = b for nrhs canonical FP64 right-hand sides ([nrhs][V][4][3][2],
+ * host or device per p->where) with SAP-preconditioned FGMRES. The smoother
+ * runs in the op's precision; FP64 is used for orthogonalisation, the
+ * least-squares update and the true residual. x receives the solutions
+ * (and holds the initial guesses if p->use_x0). info (may be NULL) receives
+ * nrhs records. Returns DD_OK when every right-hand side converged, else
+ * DD_ENOTCONV (x holds the best iterates) or an error. Synchronous with
+ * respect to the host; work runs on `stream`. */
+int dd_solve(dd_op_t op, const dd_solve_params *p, const double *b, double *x, int nrhs,
+             dd_solve_info *info, void *stream);
+
+/* ------------------------------------------------------------ serving */
+
+typedef struct {
+  size_t hbm_budget_bytes; /* device bytes the server may hold for requests (0 = 80% of free) */
+  int max_slots;           /* requests on the device at once (1..64)                 */
+  int max_batch_rhs;       /* right-hand sides batched per solve launch (1..64)       */
+} dd_server_params;
+
+typedef struct {
+  dd_op_t op;             /* resident operator the request solves with                  */
+  const double *b_host;   /* nrhs canonical FP64 right-hand sides (copied on submit)     */
+  int nrhs;
+  dd_solve_params params; /* `where` is ignored: requests are host-to-host               */
+} dd_request;
+
+enum { DD_QUEUED = 0, DD_RUNNING = 1, DD_DONE = 2, DD_FAILED = 3, DD_CANCELLED_STATE = 4 };
+
+/* Start a server: a host scheduler thread that admits requests while device
+ * memory and slots allow, batches right-hand sides of the same operator, runs
+ * batches on separate streams so they overlap, and retires each right-hand
+ * side as it converges. */
+int dd_server_create(const dd_server_params *p, dd_server_t *out);
+
+/* Queue a request (b is copied). *ticket identifies it. DD_EBUSY if the
+ * request alone can never fit the memory budget. */
+int dd_submit(dd_server_t s, const dd_request *req, uint64_t *ticket);
+
+/* State of a ticket. When DONE, x_out (may be NULL) receives nrhs canonical
+ * solutions and info (may be NULL) nrhs records; the ticket is then released.
+ * Times in info are measured from submission. */
+int dd_poll(dd_server_t s, uint64_t ticket, int *state, double *x_out, dd_solve_info *info);
+
+/* Cancel a queued or running request (its work stops at the next step). */
+int dd_cancel(dd_server_t s, uint64_t ticket);
+
+typedef struct {
+  uint64_t submitted, completed, failed, cancelled;
+  double p50_ms, p99_ms;    /* latency from submit to done, completed requests */
+  double rhs_per_s;         /* completed right-hand sides per second of server time */
+  size_t bytes_in_use;      /* device bytes held by admitted requests */
+} dd_server_stats;
+
+int dd_server_get_stats(dd_server_t s, dd_server_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_H */

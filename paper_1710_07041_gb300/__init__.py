@@ -1,0 +1,279 @@
+"""GB300-native Wilson-clover SAP-FGMRES (the fine-grid hot path of DD-alpha-AMG).
+
+Thin Python binding over the C ABI in ``include/dd.h``: argument marshalling
+only, every computation runs in the CUDA library ``_build/libdd.so``. PyTorch
+provides device memory (tensors passed by data pointer) and streams. There is
+no CPU fallback: if the library cannot be built or loaded, every call raises.
+
+Names follow the C ABI: ``create_lattice``, ``create_gauge``, ``create_op``,
+``apply_D``, ``sap_smooth``, ``solve``, ``pack``/``unpack``, ``server_*``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+F64, F32, F16, BF16 = 0, 1, 2, 3
+PREC = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+HOST, DEVICE = 0, 1
+QUEUED, RUNNING, DONE, FAILED, CANCELLED = 0, 1, 2, 3, 4
+ERRORS = {0: "DD_OK", -1: "DD_EINVAL", -2: "DD_ENOMEM", -3: "DD_ECUDA", -4: "DD_ENOTCONV",
+          -5: "DD_ETIMEOUT", -6: "DD_ECANCELLED", -7: "DD_EBUSY", -8: "DD_ENOTFOUND"}
+
+_lib = None
+
+
+class DDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SapParams(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("mr_steps", ctypes.c_int), ("x_is_zero", ctypes.c_int),
+                ("rhs_tile", ctypes.c_int)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("sap", SapParams), ("inner_reduction", ctypes.c_double), ("where", ctypes.c_int),
+                ("use_x0", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("cycles", ctypes.c_int),
+                ("true_rel_residual", ctypes.c_double), ("est_rel_residual", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("ms_sap", ctypes.c_double), ("ms_dirac", ctypes.c_double),
+                ("ms_orth", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerParams(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
+                ("max_batch_rhs", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_void_p), ("b_host", ctypes.c_void_p), ("nrhs", ctypes.c_int),
+                ("params", SolveParams)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("rhs_per_s", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t)]
+
+
+EXPORTS = {
+    "dd_version": ([], ctypes.c_char_p),
+    "dd_last_error": ([], ctypes.c_char_p),
+    "dd_kernel_launches": ([], ctypes.c_uint64),
+    "dd_create_lattice": ([ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                           ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "dd_lattice_volume": ([ctypes.c_void_p], ctypes.c_long),
+    "dd_field_bytes": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_size_t),
+    "dd_create_gauge": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "dd_create_op": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                      ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "dd_op_get_clover": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "dd_destroy": ([ctypes.c_void_p], None),
+    "dd_pack": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                 ctypes.c_void_p], ctypes.c_int),
+    "dd_unpack": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                   ctypes.c_void_p], ctypes.c_int),
+    "dd_apply_D": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                    ctypes.c_void_p], ctypes.c_int),
+    "dd_sap_smooth": ([ctypes.c_void_p, ctypes.POINTER(SapParams), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                       ctypes.c_void_p], ctypes.c_int),
+    "dd_solve": ([ctypes.c_void_p, ctypes.POINTER(SolveParams), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "dd_server_create": ([ctypes.POINTER(ServerParams), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "dd_submit": ([ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "dd_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
+                 ctypes.c_void_p], ctypes.c_int),
+    "dd_cancel": ([ctypes.c_void_p, ctypes.c_uint64], ctypes.c_int),
+    "dd_server_get_stats": ([ctypes.c_void_p, ctypes.POINTER(ServerStats)], ctypes.c_int),
+}
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load (building first if needed) the CUDA library; raise if impossible."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        for name, (args, res) in EXPORTS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise DDError(rc, f"{what}: {lib().dd_last_error().decode()}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if isinstance(t, np.ndarray):
+        assert t.flags.c_contiguous
+        return ctypes.c_void_p(t.ctypes.data)
+    assert t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Handle:
+    _h = None
+
+    def close(self):
+        if self._h:
+            lib().dd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+
+class Lattice(Handle):
+    """dims (T, Z, Y, X); block (T, Z, Y, X) Schwarz block / storage tile."""
+
+    def __init__(self, dims, block, antiperiodic: bool = True):
+        h = ctypes.c_void_p()
+        d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+        b = (ctypes.c_int * 4)(*[int(x) for x in block])
+        _check(lib().dd_create_lattice(d, b, int(bool(antiperiodic)), ctypes.byref(h)), "dd_create_lattice")
+        self._h = h.value
+        self.dims, self.block = tuple(dims), tuple(block)
+        self.V = int(lib().dd_lattice_volume(self._h))
+
+    def field_bytes(self, prec: int) -> int:
+        return int(lib().dd_field_bytes(self._h, prec))
+
+    def new_field(self, prec: int, nrhs: int = 1, device="cuda"):
+        import torch
+        return torch.zeros(self.field_bytes(prec) * nrhs, dtype=torch.uint8, device=device)
+
+    def pack(self, prec: int, canon_dev, field, nrhs: int = 1, scale: float = 1.0, stream=None):
+        """canonical complex128 device tensor (nrhs, V, 4, 3) -> internal field."""
+        _check(lib().dd_pack(self._h, prec, _ptr(canon_dev), _ptr(field), nrhs, scale, _stream_ptr(stream)),
+               "dd_pack")
+
+    def unpack(self, prec: int, field, canon_dev, nrhs: int = 1, scale: float = 1.0, stream=None):
+        _check(lib().dd_unpack(self._h, prec, _ptr(field), _ptr(canon_dev), nrhs, scale, _stream_ptr(stream)),
+               "dd_unpack")
+
+    def to_field(self, psi: np.ndarray, prec: int, scale: float = 1.0):
+        """numpy canonical spinors (..., V, 4, 3) -> new device field tensor."""
+        import torch
+        a = np.ascontiguousarray(psi, dtype=np.complex128)
+        nrhs = a.size // (12 * self.V)
+        dev = torch.from_numpy(a.view(np.float64).reshape(-1)).cuda()
+        f = self.new_field(prec, nrhs)
+        self.pack(prec, dev, f, nrhs, scale)
+        return f
+
+    def from_field(self, field, prec: int, nrhs: int = 1, scale: float = 1.0) -> np.ndarray:
+        import torch
+        dev = torch.empty(nrhs * self.V * 24, dtype=torch.float64, device=field.device)
+        self.unpack(prec, field, dev, nrhs, scale)
+        torch.cuda.synchronize()
+        out = dev.cpu().numpy().view(np.complex128)
+        return out.reshape(nrhs, self.V, 4, 3) if nrhs > 1 else out.reshape(self.V, 4, 3)
+
+
+class Gauge(Handle):
+    def __init__(self, lat: Lattice, links: np.ndarray):
+        a = np.ascontiguousarray(links, dtype=np.complex128)
+        assert a.size == lat.V * 36
+        h = ctypes.c_void_p()
+        _check(lib().dd_create_gauge(lat.handle, _ptr(a), ctypes.byref(h)), "dd_create_gauge")
+        self._h = h.value
+        self.lat = lat
+
+
+class Op(Handle):
+    """Wilson-clover operator; ``prec`` is the Schwarz smoother's storage precision."""
+
+    def __init__(self, gauge: Gauge, c_sw: float, m0: float, prec: int = F32):
+        h = ctypes.c_void_p()
+        _check(lib().dd_create_op(gauge.handle, float(c_sw), float(m0), int(prec), ctypes.byref(h)),
+               "dd_create_op")
+        self._h = h.value
+        self.gauge, self.lat, self.prec = gauge, gauge.lat, prec
+
+    def clover(self) -> np.ndarray:
+        """Site blocks A(n) as (V, 2, 6, 6) complex128."""
+        out = np.empty((self.lat.V, 2, 6, 6), dtype=np.complex128)
+        _check(lib().dd_op_get_clover(self._h, _ptr(out)), "dd_op_get_clover")
+        return out
+
+    def apply_D(self, prec: int, inp, out, nrhs: int = 1, stream=None):
+        _check(lib().dd_apply_D(self._h, prec, _ptr(inp), _ptr(out), nrhs, _stream_ptr(stream)), "dd_apply_D")
+
+    def sap_smooth(self, b, x, sweeps: int, mr_steps: int, nrhs: int = 1, x_is_zero: bool = True,
+                   rhs_tile: int = 0, stream=None):
+        p = SapParams(sweeps, mr_steps, int(bool(x_is_zero)), rhs_tile)
+        _check(lib().dd_sap_smooth(self._h, ctypes.byref(p), _ptr(b), _ptr(x), nrhs, _stream_ptr(stream)),
+               "dd_sap_smooth")
+
+    def solve(self, b, x=None, tol=1e-10, restart=16, max_iter=1000, sweeps=4, mr_steps=4,
+              inner_reduction=None, use_x0=False, stream=None, raise_on_notconv=True):
+        """Solve D x = b. b: numpy (host) or torch (device) canonical spinors
+        (nrhs, V, 4, 3) complex128 or their float64 view. Returns (x, infos)."""
+        if inner_reduction is None:
+            inner_reduction = 0.0 if self.prec == F64 else 1e-5
+        on_dev = not isinstance(b, np.ndarray)
+        if on_dev:
+            nrhs = b.numel() // (24 * self.lat.V) if b.dtype != _complex_dtype() else b.numel() // (12 * self.lat.V)
+        else:
+            b = np.ascontiguousarray(b, dtype=np.complex128)
+            nrhs = b.size // (12 * self.lat.V)
+        if x is None:
+            x = (np.zeros_like(b) if not on_dev else b.new_zeros(b.shape))
+        p = SolveParams(tol, restart, max_iter, SapParams(sweeps, mr_steps, 1, 0), inner_reduction,
+                        DEVICE if on_dev else HOST, int(bool(use_x0)))
+        infos = (SolveInfo * nrhs)()
+        rc = lib().dd_solve(self._h, ctypes.byref(p), _ptr(b), _ptr(x), nrhs, infos, _stream_ptr(stream))
+        if rc != 0 and not (rc == -4 and not raise_on_notconv):
+            _check(rc, "dd_solve")
+        return x, [i.as_dict() for i in infos]
+
+
+def _complex_dtype():
+    import torch
+    return torch.complex128
+
+
+def version() -> str:
+    return lib().dd_version().decode()

@@ -1,0 +1,336 @@
+// C ABI: handles, set-up (the "data-layout transformations at solver entry"
+// of Sec. 5 happen in dd_create_* and dd_pack), and the compute entry points.
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "dd_internal.cuh"
+
+namespace dd {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+  if (e == cudaSuccess) return DD_OK;
+  set_error("%s: %s", where, cudaGetErrorString(e));
+  return DD_ECUDA;
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+
+int launched(const char *where) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cuda_fail(cudaGetLastError(), where);
+}
+
+enum : int { MAGIC_LAT = 0x4c415431, MAGIC_GAUGE = 0x47415531, MAGIC_OP = 0x4f505231, MAGIC_SERVER = 0x53525631 };
+
+static bool pow2(int v) { return v >= 2 && (v & (v - 1)) == 0; }
+static int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) l++;
+  return l;
+}
+
+const OpFields *fields_for(const Op *op, int prec) {
+  if (prec == DD_F64) return &op->f64;
+  if (prec == DD_F32) return &op->f32;
+  if (prec == op->prec) return &op->fp;
+  return nullptr;
+}
+
+static void free_fields(OpFields &f) {
+  cudaFree(f.links);
+  cudaFree(f.clov);
+  cudaFree(f.cinv);
+  f = OpFields{};
+}
+
+static void release_lattice(Lattice *l) {
+  if (l && --l->refs == 0) {
+    l->magic = 0;
+    delete l;
+  }
+}
+static void release_gauge(Gauge *g) {
+  if (g && --g->refs == 0) {
+    cudaFree(g->links_canon);
+    release_lattice(g->lat);
+    g->magic = 0;
+    delete g;
+  }
+}
+
+void destroy_server(void *s);  // dd_server.cu
+int server_magic_ok(void *s);
+
+}  // namespace dd
+
+using namespace dd;
+
+extern "C" {
+
+const char *dd_version(void) { return "dd-gb300 0.1 (sm_103a)"; }
+
+const char *dd_last_error(void) { return g_err.c_str(); }
+
+uint64_t dd_kernel_launches(void) { return g_launches.load(); }
+
+int dd_create_lattice(const int dims[4], const int block[4], int antiperiodic_t, dd_lattice_t *out) {
+  if (!dims || !block || !out) {
+    set_error("dd_create_lattice: null argument");
+    return DD_EINVAL;
+  }
+  Geom g{};
+  long long V = 1;
+  for (int mu = 0; mu < 4; mu++) {
+    int L = dims[3 - mu], B = block[3 - mu];
+    if (L < 2 || !pow2(B) || L % B != 0 || (L / B) % 2 != 0) {
+      set_error("dd_create_lattice: direction %d: extent %d, block %d (block must be a power of two >= 2 "
+                "dividing the extent an even number of times)", mu, L, B);
+      return DD_EINVAL;
+    }
+    g.L[mu] = L;
+    g.bd[mu] = B;
+    g.lbd[mu] = ilog2(B);
+    g.nb[mu] = L / B;
+    V *= L;
+  }
+  g.bstride[0] = 1;
+  for (int mu = 1; mu < 4; mu++) g.bstride[mu] = g.bstride[mu - 1] * g.nb[mu - 1];
+  g.Vb = g.bd[0] * g.bd[1] * g.bd[2] * g.bd[3];
+  g.Vh = g.Vb / 2;
+  g.nblocks = (int)(V / g.Vb);
+  g.V = V;
+  g.antiperiodic = antiperiodic_t ? 1 : 0;
+  Lattice *l = new (std::nothrow) Lattice;
+  if (!l) return DD_ENOMEM;
+  l->magic = MAGIC_LAT;
+  l->g = g;
+  memcpy(l->dims, dims, sizeof l->dims);
+  memcpy(l->block, block, sizeof l->block);
+  l->refs = 1;
+  *out = (dd_lattice_t)l;
+  return DD_OK;
+}
+
+long dd_lattice_volume(dd_lattice_t lat) {
+  Lattice *l = (Lattice *)lat;
+  return (l && l->magic == MAGIC_LAT) ? (long)l->g.V : -1;
+}
+
+size_t dd_field_bytes(dd_lattice_t lat, int prec) {
+  Lattice *l = (Lattice *)lat;
+  if (!l || l->magic != MAGIC_LAT || prec < DD_F64 || prec > DD_BF16) return 0;
+  return (size_t)l->g.V * 24 * real_bytes(prec);
+}
+
+int dd_create_gauge(dd_lattice_t lat, const double *links, dd_gauge_t *out) {
+  Lattice *l = (Lattice *)lat;
+  if (!l || l->magic != MAGIC_LAT || !links || !out) {
+    set_error("dd_create_gauge: bad argument");
+    return DD_EINVAL;
+  }
+  Gauge *g = new (std::nothrow) Gauge;
+  if (!g) return DD_ENOMEM;
+  size_t bytes = (size_t)l->g.V * 72 * sizeof(double);
+  if (cudaMalloc(&g->links_canon, bytes) != cudaSuccess) {
+    delete g;
+    set_error("dd_create_gauge: out of device memory (%zu bytes)", bytes);
+    return DD_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpy(g->links_canon, links, bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(g->links_canon);
+    delete g;
+    return cuda_fail(e, "dd_create_gauge: copy");
+  }
+  g->magic = MAGIC_GAUGE;
+  g->lat = l;
+  l->refs++;
+  g->refs = 1;
+  *out = (dd_gauge_t)g;
+  return DD_OK;
+}
+
+static int alloc_fields(const Geom &g, int prec, OpFields &f) {
+  f.prec = prec;
+  size_t pb = pair_bytes(prec);
+  if (cudaMalloc(&f.links, (size_t)g.V * 36 * pb) != cudaSuccess || cudaMalloc(&f.clov, (size_t)g.V * 36 * pb) != cudaSuccess ||
+      cudaMalloc(&f.cinv, (size_t)g.V / 2 * 36 * pb) != cudaSuccess) {
+    free_fields(f);
+    set_error("dd_create_op: out of device memory");
+    return DD_ENOMEM;
+  }
+  return DD_OK;
+}
+
+int dd_create_op(dd_gauge_t gauge, double c_sw, double m0, int prec, dd_op_t *out) {
+  Gauge *ga = (Gauge *)gauge;
+  if (!ga || ga->magic != MAGIC_GAUGE || !out || prec < DD_F64 || prec > DD_BF16 || !std::isfinite(c_sw) ||
+      !std::isfinite(m0)) {
+    set_error("dd_create_op: bad argument");
+    return DD_EINVAL;
+  }
+  const Geom &g = ga->lat->g;
+  Op *op = new (std::nothrow) Op;
+  if (!op) return DD_ENOMEM;
+  op->magic = MAGIC_OP;
+  op->gauge = ga;
+  op->lat = ga->lat;
+  op->c_sw = c_sw;
+  op->m0 = m0;
+  op->prec = prec;
+  int rc = alloc_fields(g, DD_F64, op->f64);
+  if (rc == DD_OK) rc = alloc_fields(g, DD_F32, op->f32);
+  if (rc == DD_OK && (prec == DD_F16 || prec == DD_BF16)) rc = alloc_fields(g, prec, op->fp);
+  int *bad = nullptr;
+  if (rc == DD_OK && cudaMalloc(&bad, sizeof(int)) != cudaSuccess) rc = DD_ENOMEM;
+  cudaStream_t st = 0;
+  if (rc == DD_OK) rc = cuda_fail(cudaMemsetAsync(bad, 0, sizeof(int), st), "memset");
+  if (rc == DD_OK)
+    rc = launch_build_clover(g, ga->links_canon, c_sw, m0, (double *)op->f64.clov, (double *)op->f64.cinv, bad, st);
+  if (rc == DD_OK) rc = launch_pack_links(g, DD_F64, ga->links_canon, op->f64.links, st);
+  if (rc == DD_OK) rc = launch_pack_links(g, DD_F32, ga->links_canon, op->f32.links, st);
+  if (rc == DD_OK) rc = launch_convert_pairs(DD_F32, (const double *)op->f64.clov, op->f32.clov, (size_t)g.V * 36, st);
+  if (rc == DD_OK)
+    rc = launch_convert_pairs(DD_F32, (const double *)op->f64.cinv, op->f32.cinv, (size_t)g.V / 2 * 36, st);
+  if (rc == DD_OK && (prec == DD_F16 || prec == DD_BF16)) {
+    rc = launch_pack_links(g, prec, ga->links_canon, op->fp.links, st);
+    if (rc == DD_OK) rc = launch_convert_pairs(prec, (const double *)op->f64.clov, op->fp.clov, (size_t)g.V * 36, st);
+    if (rc == DD_OK)
+      rc = launch_convert_pairs(prec, (const double *)op->f64.cinv, op->fp.cinv, (size_t)g.V / 2 * 36, st);
+  }
+  int hbad = 0;
+  if (rc == DD_OK) rc = cuda_fail(cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost), "dd_create_op");
+  cudaFree(bad);
+  if (rc == DD_OK && hbad) {
+    set_error("dd_create_op: a clover block A = 4 + m0 + C is singular");
+    rc = DD_EINVAL;
+  }
+  if (rc != DD_OK) {
+    free_fields(op->f64);
+    free_fields(op->f32);
+    free_fields(op->fp);
+    delete op;
+    return rc;
+  }
+  if (prec == DD_F64) op->fp = op->f64;
+  if (prec == DD_F32) op->fp = op->f32;
+  ga->refs++;
+  *out = (dd_op_t)op;
+  return DD_OK;
+}
+
+int dd_op_get_clover(dd_op_t opp, double *host_out) {
+  Op *op = (Op *)opp;
+  if (!op || op->magic != MAGIC_OP || !host_out) {
+    set_error("dd_op_get_clover: bad argument");
+    return DD_EINVAL;
+  }
+  const Geom &g = op->lat->g;
+  std::vector<double> tile((size_t)g.V * 72);
+  int rc = cuda_fail(cudaMemcpy(tile.data(), op->f64.clov, tile.size() * sizeof(double), cudaMemcpyDeviceToHost),
+                     "dd_op_get_clover");
+  if (rc) return rc;
+  for (int b = 0; b < g.nblocks; b++)
+    for (int s = 0; s < g.Vb; s++) {
+      long long n = canonical_index(g, b, s);
+      for (int h = 0; h < 2; h++) {
+        auto pr = [&](int i) {
+          size_t idx = (((size_t)b * 36 + 18 * h + i) * g.Vb + s) * 2;
+          return std::complex<double>(tile[idx], tile[idx + 1]);
+        };
+        double *dst = host_out + ((size_t)n * 2 + h) * 72;
+        double dg[6] = {pr(0).real(), pr(0).imag(), pr(1).real(), pr(1).imag(), pr(2).real(), pr(2).imag()};
+        for (int i = 0; i < 6; i++)
+          for (int j = 0; j < 6; j++) {
+            std::complex<double> v;
+            if (i == j) v = dg[i];
+            else if (i < j) v = pr(herm_off(i, j));
+            else v = std::conj(pr(herm_off(j, i)));
+            dst[(i * 6 + j) * 2] = v.real();
+            dst[(i * 6 + j) * 2 + 1] = v.imag();
+          }
+      }
+    }
+  return DD_OK;
+}
+
+void dd_destroy(void *h) {
+  if (!h) return;
+  int m = *(int *)h;
+  if (m == MAGIC_LAT) {
+    release_lattice((Lattice *)h);
+  } else if (m == MAGIC_GAUGE) {
+    release_gauge((Gauge *)h);
+  } else if (m == MAGIC_OP) {
+    Op *op = (Op *)h;
+    free_fields(op->f64);
+    free_fields(op->f32);
+    if (op->prec == DD_F16 || op->prec == DD_BF16) free_fields(op->fp);
+    release_gauge(op->gauge);
+    op->magic = 0;
+    delete op;
+  } else if (m == MAGIC_SERVER) {
+    destroy_server(h);
+  }
+}
+
+int dd_pack(dd_lattice_t lat, int prec, const double *canon, void *field, int nrhs, double scale, void *stream) {
+  Lattice *l = (Lattice *)lat;
+  if (!l || l->magic != MAGIC_LAT || !canon || !field || nrhs < 1 || prec < DD_F64 || prec > DD_BF16) {
+    set_error("dd_pack: bad argument");
+    return DD_EINVAL;
+  }
+  return launch_pack(l->g, prec, canon, field, nrhs, scale, (cudaStream_t)stream);
+}
+
+int dd_unpack(dd_lattice_t lat, int prec, const void *field, double *canon, int nrhs, double scale, void *stream) {
+  Lattice *l = (Lattice *)lat;
+  if (!l || l->magic != MAGIC_LAT || !canon || !field || nrhs < 1 || prec < DD_F64 || prec > DD_BF16) {
+    set_error("dd_unpack: bad argument");
+    return DD_EINVAL;
+  }
+  return launch_unpack(l->g, prec, field, canon, nrhs, scale, (cudaStream_t)stream);
+}
+
+int dd_apply_D(dd_op_t opp, int prec, const void *in, void *out, int nrhs, void *stream) {
+  Op *op = (Op *)opp;
+  if (!op || op->magic != MAGIC_OP || !in || !out || in == out || nrhs < 1) {
+    set_error("dd_apply_D: bad argument");
+    return DD_EINVAL;
+  }
+  const OpFields *f = fields_for(op, prec);
+  if (!f) {
+    set_error("dd_apply_D: precision %d not held by this operator", prec);
+    return DD_EINVAL;
+  }
+  return launch_dirac(op->lat->g, *f, in, out, nrhs, (cudaStream_t)stream);
+}
+
+int dd_sap_smooth(dd_op_t opp, const dd_sap_params *p, const void *b, void *x, int nrhs, void *stream) {
+  Op *op = (Op *)opp;
+  if (!op || op->magic != MAGIC_OP || !p || !b || !x || b == x || nrhs < 1 || p->sweeps < 1 || p->mr_steps < 0) {
+    set_error("dd_sap_smooth: bad argument");
+    return DD_EINVAL;
+  }
+  return launch_sap(op->lat->g, op->fp, *p, b, x, nrhs, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// Wilson-clover operator y = D x over the whole lattice (Sec. 1's "discretized
+// form of the Dirac equation"; the operator every step of the Schwarz method
+// of Sec. 3.1 applies):
+//   (D x)(n) = A(n) x(n) - 1/2 sum_mu [(1 - g_mu) U_mu(n) x(n+mu) + (1 + g_mu) U_mu(n-mu)^+ x(n-mu)]
+// One thread per (site, right-hand side), right-hand side fastest so that the
+// threads of one site share its link and clover loads in L1. The kernel is
+// HBM-bound: per site it moves 24 (in) + 24 (out) + 72 (links) + 72 (clover)
+// reals once, neighbour spinors being re-read from L1/L2.
+#include "dd_internal.cuh"
+
+namespace dd {
+namespace {
+
+constexpr int DIRAC_TPB = 128;
+
+template <int MU, typename S, typename C>
+__device__ __forceinline__ void dirac_dir(const Geom &g, const Site &t, const void *links, const void *in,
+                                          Spinor<C> &acc) {
+  int nb, ns;
+  float sg;
+  bool inside;
+  Link<C> u;
+  Spinor<C> psi;
+  neighbour(g, t, MU, +1, &nb, &ns, &sg, &inside);
+  load_spinor<S, C>(in, g, nb, ns, psi);
+  load_link<S, C>(links, g, t.b, t.s, MU, u);
+  hop<MU, true>(acc, u, psi, (C)(-0.5f * sg));
+  neighbour(g, t, MU, -1, &nb, &ns, &sg, &inside);
+  load_spinor<S, C>(in, g, nb, ns, psi);
+  load_link<S, C>(links, g, nb, ns, MU, u);
+  hop<MU, false>(acc, u, psi, (C)(-0.5f * sg));
+}
+
+template <typename S>
+__global__ void __launch_bounds__(DIRAC_TPB) k_dirac(Geom g, const void *__restrict__ links,
+                                                     const void *__restrict__ clov, const void *__restrict__ in,
+                                                     void *__restrict__ out, int nrhs, size_t fbytes) {
+  using C = typename Store<S>::comp_t;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= g.V * nrhs) return;
+  long long site = t / nrhs;
+  int r = (int)(t - site * nrhs);
+  int b = (int)(site / g.Vb), s = (int)(site - (long long)b * g.Vb);
+  const char *inr = (const char *)in + r * fbytes;
+  Site st = decode(g, b, s);
+  Spinor<C> x, acc;
+  load_spinor<S, C>(inr, g, b, s, x);
+  clover_apply<S, C>(clov, g.Vb, b, s, x, acc);
+  dirac_dir<0, S, C>(g, st, links, inr, acc);
+  dirac_dir<1, S, C>(g, st, links, inr, acc);
+  dirac_dir<2, S, C>(g, st, links, inr, acc);
+  dirac_dir<3, S, C>(g, st, links, inr, acc);
+  store_spinor<S, C>((char *)out + r * fbytes, g, b, s, acc);
+}
+
+template <typename S>
+int dirac_t(const Geom &g, const OpFields &f, const void *in, void *out, int nrhs, cudaStream_t st) {
+  long long n = g.V * nrhs;
+  size_t fbytes = (size_t)g.V * 24 * sizeof(S);
+  k_dirac<S><<<(unsigned)((n + DIRAC_TPB - 1) / DIRAC_TPB), DIRAC_TPB, 0, st>>>(g, f.links, f.clov, in, out, nrhs,
+                                                                               fbytes);
+  return launched("k_dirac");
+}
+
+}  // namespace
+
+int launch_dirac(const Geom &g, const OpFields &f, const void *in, void *out, int nrhs, cudaStream_t st) {
+  switch (f.prec) {
+    case DD_F64: return dirac_t<double>(g, f, in, out, nrhs, st);
+    case DD_F32: return dirac_t<float>(g, f, in, out, nrhs, st);
+    case DD_F16: return dirac_t<__half>(g, f, in, out, nrhs, st);
+    case DD_BF16: return dirac_t<__nv_bfloat16>(g, f, in, out, nrhs, st);
+  }
+  set_error("apply_D: precision %d not available", f.prec);
+  return DD_EINVAL;
+}
+
+}  // namespace dd

@@ -1,0 +1,488 @@
+// Internal declarations shared by the library's CUDA translation units.
+//
+// Layout in HBM. Every field is stored block-major so that one Schwarz block
+// (the SAP "domain" of Sec. 3.1) is a contiguous tile:
+//   tile index b = lexicographic block coordinate (x fastest),
+//   inside a tile: even-parity sites first, then odd; within a parity the
+//   position is (local lexicographic index) / 2.
+// A spinor field of precision P is [block][chunk][Vb] with 16-byte chunks
+// (F64: 2 reals, F32: 4 reals, F16/BF16: 8 reals), so a warp reading one chunk
+// of 32 consecutive sites issues one fully coalesced 512-byte request.
+// Links and clover site blocks are [block][36 pairs][Vb] with "pairs" of two
+// reals (double2 / float2 / half2): 4 links x 18 reals = 72 reals per site,
+// clover 2 chirality blocks x 36 reals (6 real diagonal + 15 complex upper
+// entries, row-major) = 72 reals per site. The even-site inverse clover is
+// [block][36 pairs][Vb/2].
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/dd.h"
+
+namespace dd {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *where);
+// Count a kernel launch and report a launch error (if any).
+int launched(const char *where);
+#define DD_LAUNCHED()                          \
+  do {                                         \
+    int rc_ = ::dd::launched("kernel launch"); \
+    if (rc_) return rc_;                       \
+  } while (0)
+#define DD_CUDA(call)                                          \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return ::dd::cuda_fail(e_, #call);  \
+  } while (0)
+
+// -------------------------------------------------------------- geometry
+struct Geom {
+  int L[4];         // extents by direction: 0:x 1:y 2:z 3:t
+  int bd[4];        // block extents (powers of two >= 2)
+  int lbd[4];       // log2 of block extents
+  int nb[4];        // blocks per direction
+  int bstride[4];   // block-index stride per direction
+  int Vb, Vh;       // sites per block, per block and parity
+  int nblocks;
+  long long V;
+  int antiperiodic;
+};
+
+// Decoded site: block b, position s in the tile, local and block coordinates.
+struct Site {
+  int b, s, p;      // block, tile position, parity
+  int lc[4];        // local coordinates
+  int bc[4];        // block coordinates
+};
+
+__host__ __device__ inline int parity_of(const int lc[4]) { return (lc[0] + lc[1] + lc[2] + lc[3]) & 1; }
+
+__host__ __device__ inline int local_lex(const Geom &g, const int lc[4]) {
+  return lc[0] + ((lc[1] + ((lc[2] + (lc[3] << g.lbd[2])) << g.lbd[1])) << g.lbd[0]);
+}
+
+// tile position s -> local coordinates (inverse of pos_of)
+__host__ __device__ inline void local_coords(const Geom &g, int s, int lc[4]) {
+  int p = s >= g.Vh;
+  int j = s - p * g.Vh;
+  int k = 2 * j;
+  int x0 = k & (g.bd[0] - 1);
+  int r = k >> g.lbd[0];
+  lc[1] = r & (g.bd[1] - 1);
+  r >>= g.lbd[1];
+  lc[2] = r & (g.bd[2] - 1);
+  lc[3] = r >> g.lbd[2];
+  int q = (lc[1] + lc[2] + lc[3]) & 1;
+  lc[0] = x0 + (p ^ q);
+}
+
+__host__ __device__ inline int pos_of(const Geom &g, const int lc[4]) {
+  return parity_of(lc) * g.Vh + (local_lex(g, lc) >> 1);
+}
+
+__host__ __device__ inline void block_coords(const Geom &g, int b, int bc[4]) {
+  bc[0] = b % g.nb[0];
+  int r = b / g.nb[0];
+  bc[1] = r % g.nb[1];
+  r /= g.nb[1];
+  bc[2] = r % g.nb[2];
+  bc[3] = r / g.nb[2];
+}
+
+__host__ __device__ inline Site decode(const Geom &g, int b, int s) {
+  Site t;
+  t.b = b;
+  t.s = s;
+  t.p = s >= g.Vh;
+  local_coords(g, s, t.lc);
+  block_coords(g, b, t.bc);
+  return t;
+}
+
+// Neighbour of site t in direction mu (dir = +1 / -1): its block and tile
+// position; *sign is -1 for a hop across the antiperiodic time edge; *inside
+// tells whether it lies in the same block.
+__host__ __device__ inline void neighbour(const Geom &g, const Site &t, int mu, int dir, int *nb_b,
+                                          int *nb_s, float *sign, bool *inside) {
+  int lc[4] = {t.lc[0], t.lc[1], t.lc[2], t.lc[3]};
+  int v = lc[mu] + dir;
+  int b = t.b;
+  *sign = 1.f;
+  *inside = true;
+  if (v < 0 || v >= g.bd[mu]) {
+    *inside = false;
+    v &= g.bd[mu] - 1;
+    int bcv = t.bc[mu] + dir;
+    if (bcv < 0) {
+      bcv += g.nb[mu];
+      if (mu == 3 && g.antiperiodic) *sign = -1.f;
+    } else if (bcv >= g.nb[mu]) {
+      bcv -= g.nb[mu];
+      if (mu == 3 && g.antiperiodic) *sign = -1.f;
+    }
+    b += (bcv - t.bc[mu]) * g.bstride[mu];
+  }
+  lc[mu] = v;
+  *nb_b = b;
+  *nb_s = pos_of(g, lc);
+}
+
+// canonical (lexicographic) site index of (b, s)
+__host__ __device__ inline long long canonical_index(const Geom &g, int b, int s) {
+  Site t = decode(g, b, s);
+  long long c[4];
+  for (int mu = 0; mu < 4; mu++) c[mu] = (long long)t.bc[mu] * g.bd[mu] + t.lc[mu];
+  return c[0] + g.L[0] * (c[1] + (long long)g.L[1] * (c[2] + (long long)g.L[2] * c[3]));
+}
+
+// ------------------------------------------------------------- precisions
+template <typename S> struct Store;
+template <> struct Store<double> {
+  static constexpr int prec = DD_F64;
+  static constexpr int reals_per_chunk = 2;   // spinor chunk: double2
+  using pair_t = double2;                      // link / clover pair
+  using comp_t = double;
+};
+template <> struct Store<float> {
+  static constexpr int prec = DD_F32;
+  static constexpr int reals_per_chunk = 4;   // float4
+  using pair_t = float2;
+  using comp_t = float;
+};
+template <> struct Store<__half> {
+  static constexpr int prec = DD_F16;
+  static constexpr int reals_per_chunk = 8;   // 8 halves in a uint4
+  using pair_t = __half2;
+  using comp_t = float;
+};
+template <> struct Store<__nv_bfloat16> {
+  static constexpr int prec = DD_BF16;
+  static constexpr int reals_per_chunk = 8;
+  using pair_t = __nv_bfloat162;
+  using comp_t = float;
+};
+
+inline size_t real_bytes(int prec) { return prec == DD_F64 ? 8 : prec == DD_F32 ? 4 : 2; }
+inline size_t pair_bytes(int prec) { return 2 * real_bytes(prec); }
+
+template <typename S> __host__ __device__ constexpr int spinor_chunks() { return 24 / Store<S>::reals_per_chunk; }
+
+// pair conversions (round to nearest even on narrowing)
+template <typename C> struct cpx { C re, im; };
+
+template <typename C, typename P> __device__ __forceinline__ cpx<C> from_pair(P v);
+template <> __device__ __forceinline__ cpx<double> from_pair<double, double2>(double2 v) { return {v.x, v.y}; }
+template <> __device__ __forceinline__ cpx<float> from_pair<float, float2>(float2 v) { return {v.x, v.y}; }
+template <> __device__ __forceinline__ cpx<float> from_pair<float, __half2>(__half2 v) {
+  float2 f = __half22float2(v);
+  return {f.x, f.y};
+}
+template <> __device__ __forceinline__ cpx<float> from_pair<float, __nv_bfloat162>(__nv_bfloat162 v) {
+  float2 f = __bfloat1622float2(v);
+  return {f.x, f.y};
+}
+
+template <typename P, typename C> __device__ __forceinline__ P to_pair(C re, C im);
+template <> __device__ __forceinline__ double2 to_pair<double2, double>(double re, double im) { return make_double2(re, im); }
+template <> __device__ __forceinline__ float2 to_pair<float2, float>(float re, float im) { return make_float2(re, im); }
+template <> __device__ __forceinline__ __half2 to_pair<__half2, float>(float re, float im) {
+  return __floats2half2_rn(re, im);
+}
+template <> __device__ __forceinline__ __nv_bfloat162 to_pair<__nv_bfloat162, float>(float re, float im) {
+  return __floats2bfloat162_rn(re, im);
+}
+template <> __device__ __forceinline__ float2 to_pair<float2, double>(double re, double im) {
+  return make_float2((float)re, (float)im);
+}
+template <> __device__ __forceinline__ __half2 to_pair<__half2, double>(double re, double im) {
+  return __halves2half2(__double2half(re), __double2half(im));
+}
+template <> __device__ __forceinline__ __nv_bfloat162 to_pair<__nv_bfloat162, double>(double re, double im) {
+  return __halves2bfloat162(__double2bfloat16(re), __double2bfloat16(im));
+}
+
+// ---------------------------------------------------------- spinor access
+// A spinor in registers: 12 complex, index 3*spin + colour.
+template <typename C> struct Spinor { cpx<C> c[12]; };
+
+// Load spinor (b, s) from a field of storage S.
+template <typename S, typename C>
+__device__ __forceinline__ void load_spinor(const void *field, const Geom &g, int b, int s, Spinor<C> &out) {
+  constexpr int NC = spinor_chunks<S>();
+  const char *base = (const char *)field + (((size_t)b * NC) * g.Vb + s) * 16;
+  const size_t cstride = (size_t)g.Vb * 16;
+  if constexpr (Store<S>::prec == DD_F64) {
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+      double2 v = __ldg((const double2 *)(base + c * cstride));
+      out.c[c] = {(C)v.x, (C)v.y};
+    }
+  } else if constexpr (Store<S>::prec == DD_F32) {
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+      float4 v = __ldg((const float4 *)(base + c * cstride));
+      out.c[2 * c] = {(C)v.x, (C)v.y};
+      out.c[2 * c + 1] = {(C)v.z, (C)v.w};
+    }
+  } else {
+    using P = typename Store<S>::pair_t;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      uint4 v = __ldg((const uint4 *)(base + c * cstride));
+      const P *h = (const P *)&v;
+#pragma unroll
+      for (int k = 0; k < 4; k++) out.c[4 * c + k] = from_pair<C, P>(h[k]);
+    }
+  }
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ void store_spinor(void *field, const Geom &g, int b, int s, const Spinor<C> &v) {
+  constexpr int NC = spinor_chunks<S>();
+  char *base = (char *)field + (((size_t)b * NC) * g.Vb + s) * 16;
+  const size_t cstride = (size_t)g.Vb * 16;
+  if constexpr (Store<S>::prec == DD_F64) {
+#pragma unroll
+    for (int c = 0; c < 12; c++) *(double2 *)(base + c * cstride) = make_double2(v.c[c].re, v.c[c].im);
+  } else if constexpr (Store<S>::prec == DD_F32) {
+#pragma unroll
+    for (int c = 0; c < 6; c++)
+      *(float4 *)(base + c * cstride) =
+          make_float4((float)v.c[2 * c].re, (float)v.c[2 * c].im, (float)v.c[2 * c + 1].re, (float)v.c[2 * c + 1].im);
+  } else {
+    using P = typename Store<S>::pair_t;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      uint4 w;
+      P *h = (P *)&w;
+#pragma unroll
+      for (int k = 0; k < 4; k++) h[k] = to_pair<P, C>(v.c[4 * c + k].re, v.c[4 * c + k].im);
+      *(uint4 *)(base + c * cstride) = w;
+    }
+  }
+}
+
+// ------------------------------------------------------------ SU(3) hops
+template <typename C> struct Link { cpx<C> m[9]; };
+
+template <typename S, typename C>
+__device__ __forceinline__ void load_link(const void *links, const Geom &g, int b, int s, int mu, Link<C> &u) {
+  using P = typename Store<S>::pair_t;
+  const P *base = (const P *)links + ((size_t)b * 36 + 9 * mu) * g.Vb + s;
+#pragma unroll
+  for (int i = 0; i < 9; i++) u.m[i] = from_pair<C, P>(__ldg(base + (size_t)i * g.Vb));
+}
+
+template <typename C> __device__ __forceinline__ cpx<C> cmul(cpx<C> a, cpx<C> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// conj(a) * b
+template <typename C> __device__ __forceinline__ cpx<C> cmulc(cpx<C> a, cpx<C> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+
+// h = U chi (two spin components of colour vectors)
+template <typename C>
+__device__ __forceinline__ void su3_mul(const Link<C> &u, const cpx<C> *chi, cpx<C> *h) {
+#pragma unroll
+  for (int sp = 0; sp < 2; sp++)
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+      cpx<C> a = {0, 0};
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        cpx<C> p = cmul(u.m[3 * r + k], chi[3 * sp + k]);
+        a.re += p.re;
+        a.im += p.im;
+      }
+      h[3 * sp + r] = a;
+    }
+}
+// h = U^dagger chi
+template <typename C>
+__device__ __forceinline__ void su3_dmul(const Link<C> &u, const cpx<C> *chi, cpx<C> *h) {
+#pragma unroll
+  for (int sp = 0; sp < 2; sp++)
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+      cpx<C> a = {0, 0};
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        cpx<C> p = cmulc(u.m[3 * k + r], chi[3 * sp + k]);
+        a.re += p.re;
+        a.im += p.im;
+      }
+      h[3 * sp + r] = a;
+    }
+}
+
+// Spin projection for a hop in direction MU, chiral basis. FWD: the term
+// (1 - g_mu) U_mu(n) psi(n+mu); otherwise (1 + g_mu) U_mu(n-mu)^+ psi(n-mu).
+// With g_mu = [[0, A],[A^+, 0]] (A_x = -i s1, A_y = -i s2, A_z = -i s3, A_t = 1):
+//   (1 -+ g) psi = [chi ; -+ A^+ chi],  chi = psi_up -+ A psi_down,
+// so only the 2-spin chi is multiplied by the link.
+template <int MU, bool FWD, typename C>
+__device__ __forceinline__ void project(const Spinor<C> &p, cpx<C> *chi) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    cpx<C> u0 = p.c[c], u1 = p.c[3 + c], d0 = p.c[6 + c], d1 = p.c[9 + c];
+    if constexpr (MU == 0) {       // A d = (-i d1, -i d0)
+      if (FWD) { chi[c] = {u0.re - d1.im, u0.im + d1.re}; chi[3 + c] = {u1.re - d0.im, u1.im + d0.re}; }
+      else     { chi[c] = {u0.re + d1.im, u0.im - d1.re}; chi[3 + c] = {u1.re + d0.im, u1.im - d0.re}; }
+    } else if constexpr (MU == 1) { // A d = (-d1, d0)
+      if (FWD) { chi[c] = {u0.re + d1.re, u0.im + d1.im}; chi[3 + c] = {u1.re - d0.re, u1.im - d0.im}; }
+      else     { chi[c] = {u0.re - d1.re, u0.im - d1.im}; chi[3 + c] = {u1.re + d0.re, u1.im + d0.im}; }
+    } else if constexpr (MU == 2) { // A d = (-i d0, i d1)
+      if (FWD) { chi[c] = {u0.re - d0.im, u0.im + d0.re}; chi[3 + c] = {u1.re + d1.im, u1.im - d1.re}; }
+      else     { chi[c] = {u0.re + d0.im, u0.im - d0.re}; chi[3 + c] = {u1.re - d1.im, u1.im + d1.re}; }
+    } else {                        // A d = d
+      if (FWD) { chi[c] = {u0.re - d0.re, u0.im - d0.im}; chi[3 + c] = {u1.re - d1.re, u1.im - d1.im}; }
+      else     { chi[c] = {u0.re + d0.re, u0.im + d0.im}; chi[3 + c] = {u1.re + d1.re, u1.im + d1.im}; }
+    }
+  }
+}
+
+// acc += sgn * reconstruct(h): upper spins h, lower spins -+ A^+ h.
+template <int MU, bool FWD, typename C>
+__device__ __forceinline__ void accum_recon(Spinor<C> &acc, const cpx<C> *h, C sgn) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    cpx<C> h0 = {sgn * h[c].re, sgn * h[c].im}, h1 = {sgn * h[3 + c].re, sgn * h[3 + c].im};
+    acc.c[c].re += h0.re; acc.c[c].im += h0.im;
+    acc.c[3 + c].re += h1.re; acc.c[3 + c].im += h1.im;
+    cpx<C> l0, l1;
+    if constexpr (MU == 0) {        // A^+ h = (i h1, i h0)
+      l0 = {-h1.im, h1.re}; l1 = {-h0.im, h0.re};
+    } else if constexpr (MU == 1) { // A^+ h = (h1, -h0)
+      l0 = h1; l1 = {-h0.re, -h0.im};
+    } else if constexpr (MU == 2) { // A^+ h = (i h0, -i h1)
+      l0 = {-h0.im, h0.re}; l1 = {h1.im, -h1.re};
+    } else {                        // A^+ h = h
+      l0 = h0; l1 = h1;
+    }
+    if (FWD) {
+      acc.c[6 + c].re -= l0.re; acc.c[6 + c].im -= l0.im;
+      acc.c[9 + c].re -= l1.re; acc.c[9 + c].im -= l1.im;
+    } else {
+      acc.c[6 + c].re += l0.re; acc.c[6 + c].im += l0.im;
+      acc.c[9 + c].re += l1.re; acc.c[9 + c].im += l1.im;
+    }
+  }
+}
+
+// One hop: acc += sgn * (1 -+ g_mu) W psi, W = U (FWD) or U^dagger.
+template <int MU, bool FWD, typename C>
+__device__ __forceinline__ void hop(Spinor<C> &acc, const Link<C> &u, const Spinor<C> &psi, C sgn) {
+  cpx<C> chi[6], h[6];
+  project<MU, FWD>(psi, chi);
+  if (FWD) su3_mul(u, chi, h);
+  else su3_dmul(u, chi, h);
+  accum_recon<MU, FWD>(acc, h, sgn);
+}
+
+// ------------------------------------------------------------ clover blocks
+// Packed Hermitian 6x6: [0..5] real diagonal as 3 pairs, then 15 complex
+// upper entries (i<j) row-major. Pair index of (i,j), i<j:
+__host__ __device__ constexpr int herm_off(int i, int j) {
+  // entries before row i: sum_{r<i} (5 - r)
+  return 3 + (i * (11 - i)) / 2 + (j - i - 1);
+}
+
+// y = M x for one packed block (M given as 18 pairs).
+template <typename C>
+__device__ __forceinline__ void herm6_mv(const cpx<C> *m, const cpx<C> *x, cpx<C> *y) {
+  C d[6] = {m[0].re, m[0].im, m[1].re, m[1].im, m[2].re, m[2].im};
+#pragma unroll
+  for (int i = 0; i < 6; i++) y[i] = {d[i] * x[i].re, d[i] * x[i].im};
+#pragma unroll
+  for (int i = 0; i < 6; i++)
+#pragma unroll
+    for (int j = i + 1; j < 6; j++) {
+      cpx<C> a = m[herm_off(i, j)];
+      // y_i += a x_j ; y_j += conj(a) x_i
+      y[i].re += a.re * x[j].re - a.im * x[j].im;
+      y[i].im += a.re * x[j].im + a.im * x[j].re;
+      y[j].re += a.re * x[i].re + a.im * x[i].im;
+      y[j].im += a.re * x[i].im - a.im * x[i].re;
+    }
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ void load_clover_block(const void *clov, size_t tile_sites, int b, int s, int h,
+                                                  cpx<C> *m) {
+  using P = typename Store<S>::pair_t;
+  const P *base = (const P *)clov + ((size_t)b * 36 + 18 * h) * tile_sites + s;
+#pragma unroll
+  for (int i = 0; i < 18; i++) m[i] = from_pair<C, P>(__ldg(base + (size_t)i * tile_sites));
+}
+
+// out = A psi for a full site (both chirality blocks)
+template <typename S, typename C>
+__device__ __forceinline__ void clover_apply(const void *clov, size_t tile_sites, int b, int s, const Spinor<C> &in,
+                                             Spinor<C> &out) {
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    cpx<C> m[18];
+    load_clover_block<S, C>(clov, tile_sites, b, s, h, m);
+    herm6_mv(m, &in.c[6 * h], &out.c[6 * h]);
+  }
+}
+
+// -------------------------------------------------------------- objects
+struct Lattice {
+  int magic;
+  Geom g;
+  int dims[4];
+  int block[4];
+  int refs;
+};
+
+struct Gauge {
+  int magic;
+  Lattice *lat;
+  double *links_canon;   // device [V][4][3][3][2] FP64, canonical order
+  int refs;
+};
+
+// Operator fields in one storage precision.
+struct OpFields {
+  int prec = -1;
+  void *links = nullptr;  // [nblocks][36][Vb] pairs
+  void *clov = nullptr;   // A, [nblocks][36][Vb] pairs
+  void *cinv = nullptr;   // A^-1 on even sites, [nblocks][36][Vh] pairs
+};
+
+struct Op {
+  int magic;
+  Gauge *gauge;
+  Lattice *lat;
+  double c_sw, m0;
+  int prec;             // smoother precision
+  OpFields f64, f32, fp;  // fp = smoother precision fields (aliases f64/f32 when equal)
+};
+
+const OpFields *fields_for(const Op *op, int prec);
+
+// --------------------------------------------------------- kernel launchers
+int launch_pack(const Geom &g, int prec, const double *canon, void *field, int nrhs, double scale, cudaStream_t st);
+int launch_unpack(const Geom &g, int prec, const void *field, double *canon, int nrhs, double scale, cudaStream_t st);
+int launch_pack_links(const Geom &g, int prec, const double *links_canon, void *out, cudaStream_t st);
+int launch_build_clover(const Geom &g, const double *links_canon, double c_sw, double m0, double *clov64,
+                        double *cinv64, int *bad, cudaStream_t st);
+int launch_convert_pairs(int prec, const double *in, void *out, size_t npairs, cudaStream_t st);
+int launch_dirac(const Geom &g, const OpFields &f, const void *in, void *out, int nrhs, cudaStream_t st);
+int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const void *b, void *x, int nrhs,
+               cudaStream_t st);
+// spinor precision conversion between two internal layouts, y = scale * x
+int launch_convert_field(const Geom &g, int prec_in, const void *in, int prec_out, void *out, int nrhs, double scale,
+                         cudaStream_t st);
+
+}  // namespace dd

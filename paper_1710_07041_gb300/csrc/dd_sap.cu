@@ -1,0 +1,453 @@
+// Schwarz alternating procedure (Sec. 3.1, Table 2 "Schwarz method") with the
+// block solve by minimal-residual steps (Sec. 3.1, Table 1 "MR inversion
+// within a domain"). Red-black multiplicative Schwarz: per sweep, all blocks
+// of colour 0 and then all blocks of colour 1 are solved, each from the
+// current global residual, and the block correction is added to x.
+//
+// One CTA per block (x one right-hand side). Per phase the CTA
+//   1. stages the block's links, odd-site clover A_oo and even-site inverse
+//      A_ee^-1 into shared memory with cp.async (overlapping step 2),
+//   2. forms r = b - D x on its sites (neighbour x read from the other colour's
+//      blocks in HBM; skipped when x = 0),
+//   3. Schur right-hand side  bhat = r_o - D_oe A_ee^-1 r_e,
+//   4. n_MR steps on Dhat = A_oo - D_oe A_ee^-1 D_eo from e_o = 0:
+//        p = Dhat rho, alpha = <p,rho>/<p,p>, e_o += alpha rho, rho -= alpha p,
+//   5. reconstructs e_e = A_ee^-1 (r_e - D_eo e_o) and writes x += e.
+// All MR vectors stay in shared memory for the whole block solve. Threads:
+// 2 per even/odd site pair; thread half h owns spin components {2h, 2h+1}
+// (chirality block h of the clover) and evaluates the hops in directions
+// {2h, 2h+1}; the two halves exchange partial hop sums through shared memory.
+// With Vh = block sites / 2 a multiple of 32, h is warp-uniform, so the
+// per-direction code never diverges inside a warp.
+#include "dd_internal.cuh"
+
+namespace dd {
+namespace {
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// cooperative async copy of `bytes` (multiple of 16) from global to shared
+__device__ __forceinline__ void stage(void *dst, const void *src, size_t bytes) {
+  for (size_t o = (size_t)threadIdx.x * 16; o < bytes; o += (size_t)blockDim.x * 16)
+    cp_async16((char *)dst + o, (const char *)src + o);
+}
+
+// Strided view of one block's pair tile: element (i, site) at p[i * stride + site].
+template <typename P> struct Tile {
+  const P *p;
+  int stride;
+};
+
+template <typename C, typename P>
+__device__ __forceinline__ void tile_link(const Tile<P> &t, int s, int mu, Link<C> &u) {
+#pragma unroll
+  for (int i = 0; i < 9; i++) u.m[i] = from_pair<C, P>(t.p[(9 * mu + i) * t.stride + s]);
+}
+template <typename C, typename P>
+__device__ __forceinline__ void tile_block(const Tile<P> &t, int s, int h, cpx<C> *m) {
+#pragma unroll
+  for (int i = 0; i < 18; i++) m[i] = from_pair<C, P>(t.p[(18 * h + i) * t.stride + s]);
+}
+
+// shared-memory vector: [12][Vh] complex, one parity of the block
+template <typename C>
+__device__ __forceinline__ void vec_load(const cpx<C> *v, int Vh, int q, Spinor<C> &o) {
+#pragma unroll
+  for (int i = 0; i < 12; i++) o.c[i] = v[i * Vh + q];
+}
+
+// acc += hops into site t from in-block neighbours held in shared vector v,
+// directions {2h, 2h+1}. Links from the block's tile.
+template <int MU, typename C, typename P>
+__device__ __forceinline__ void hop_inner_dir(const Geom &g, const Site &t, const cpx<C> *v, const Tile<P> &L,
+                                              Spinor<C> &acc) {
+  int nb, ns;
+  float sg;
+  bool inside;
+  Link<C> u;
+  Spinor<C> psi;
+  neighbour(g, t, MU, +1, &nb, &ns, &sg, &inside);
+  if (inside) {
+    vec_load(v, g.Vh, ns - (t.p ? 0 : g.Vh), psi);
+    tile_link(L, t.s, MU, u);
+    hop<MU, true>(acc, u, psi, (C)-0.5);
+  }
+  neighbour(g, t, MU, -1, &nb, &ns, &sg, &inside);
+  if (inside) {
+    vec_load(v, g.Vh, ns - (t.p ? 0 : g.Vh), psi);
+    tile_link(L, ns, MU, u);
+    hop<MU, false>(acc, u, psi, (C)-0.5);
+  }
+}
+
+template <typename C, typename P>
+__device__ __forceinline__ void hops_inner(const Geom &g, const Site &t, int h, const cpx<C> *v, const Tile<P> &L,
+                                           Spinor<C> &acc) {
+#pragma unroll
+  for (int i = 0; i < 12; i++) acc.c[i] = {0, 0};
+  if (h == 0) {
+    hop_inner_dir<0>(g, t, v, L, acc);
+    hop_inner_dir<1>(g, t, v, L, acc);
+  } else {
+    hop_inner_dir<2>(g, t, v, L, acc);
+    hop_inner_dir<3>(g, t, v, L, acc);
+  }
+}
+
+// acc += hops into site t from the global field x, directions {2h, 2h+1};
+// neighbours inside the block are skipped when self_zero (x known to be 0
+// there), neighbours outside when halo_zero.
+template <int MU, typename S, typename C>
+__device__ __forceinline__ void hop_global_dir(const Geom &g, const Site &t, const void *links, const void *x,
+                                               bool self_zero, bool halo_zero, Spinor<C> &acc) {
+  int nb, ns;
+  float sg;
+  bool inside;
+  Link<C> u;
+  Spinor<C> psi;
+  neighbour(g, t, MU, +1, &nb, &ns, &sg, &inside);
+  if (inside ? !self_zero : !halo_zero) {
+    load_spinor<S, C>(x, g, nb, ns, psi);
+    load_link<S, C>(links, g, t.b, t.s, MU, u);
+    hop<MU, true>(acc, u, psi, (C)(-0.5f * sg));
+  }
+  neighbour(g, t, MU, -1, &nb, &ns, &sg, &inside);
+  if (inside ? !self_zero : !halo_zero) {
+    load_spinor<S, C>(x, g, nb, ns, psi);
+    load_link<S, C>(links, g, nb, ns, MU, u);
+    hop<MU, false>(acc, u, psi, (C)(-0.5f * sg));
+  }
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ void hops_global(const Geom &g, const Site &t, int h, const void *links, const void *x,
+                                            bool self_zero, bool halo_zero, Spinor<C> &acc) {
+#pragma unroll
+  for (int i = 0; i < 12; i++) acc.c[i] = {0, 0};
+  if (h == 0) {
+    hop_global_dir<0, S, C>(g, t, links, x, self_zero, halo_zero, acc);
+    hop_global_dir<1, S, C>(g, t, links, x, self_zero, halo_zero, acc);
+  } else {
+    hop_global_dir<2, S, C>(g, t, links, x, self_zero, halo_zero, acc);
+    hop_global_dir<3, S, C>(g, t, links, x, self_zero, halo_zero, acc);
+  }
+}
+
+// the six components of spin half h (selects, so the register arrays are
+// never indexed at run time)
+template <typename C>
+__device__ __forceinline__ void half_of(const Spinor<C> &s, int h, cpx<C> *out) {
+#pragma unroll
+  for (int i = 0; i < 6; i++) out[i] = h ? s.c[6 + i] : s.c[i];
+}
+
+// Exchange partial hop sums between the two halves of a site pair: on return
+// own[0..5] = full sum of the components of half h. xch: [12][Vh] smem.
+template <typename C>
+__device__ __forceinline__ void exchange(cpx<C> *xch, int Vh, int j, int h, const Spinor<C> &part, cpx<C> *own) {
+  const int other = 6 * (1 - h), mine = 6 * h;
+#pragma unroll
+  for (int i = 0; i < 6; i++) xch[(other + i) * Vh + j] = h ? part.c[i] : part.c[6 + i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    cpx<C> a = h ? part.c[6 + i] : part.c[i], b = xch[(mine + i) * Vh + j];
+    own[i] = {a.re + b.re, a.im + b.im};
+  }
+  __syncthreads();
+}
+
+// deterministic block sum of three values; red: smem [3][32]
+template <typename C>
+__device__ __forceinline__ void block_sum3(C &a, C &b, C &c, C *red) {
+  const int width = blockDim.x < 32 ? blockDim.x : 32;
+  const unsigned mask = width == 32 ? 0xffffffffu : ((1u << width) - 1u);
+  for (int o = width / 2; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(mask, a, o);
+    b += __shfl_xor_sync(mask, b, o);
+    c += __shfl_xor_sync(mask, c, o);
+  }
+  const int w = threadIdx.x / 32, nw = (blockDim.x + 31) / 32;
+  if ((threadIdx.x & 31) == 0) {
+    red[w] = a;
+    red[32 + w] = b;
+    red[64 + w] = c;
+  }
+  __syncthreads();
+  a = b = c = 0;
+  for (int i = 0; i < nw; i++) {
+    a += red[i];
+    b += red[32 + i];
+    c += red[64 + i];
+  }
+  __syncthreads();
+}
+
+template <typename S> struct SapSmem {
+  using C = typename Store<S>::comp_t;
+  using P = typename Store<S>::pair_t;
+  static size_t vec_bytes(const Geom &g) { return (size_t)12 * g.Vh * sizeof(cpx<C>); }
+  static size_t bytes(const Geom &g, bool stage) {
+    size_t b = 4 * vec_bytes(g) + 96 * sizeof(C);
+    if (stage) b += (size_t)36 * (g.Vb + 2 * g.Vh) * sizeof(P);
+    return b;
+  }
+};
+
+template <typename S, bool STAGE>
+__global__ void __launch_bounds__(256, 1) k_sap_phase(Geom g, const void *__restrict__ links,
+                                                   const void *__restrict__ clov, const void *__restrict__ cinv,
+                                                   const void *__restrict__ bvec, void *__restrict__ xvec,
+                                                   int colour, int self_zero, int halo_zero, int nmr,
+                                                   size_t fbytes) {
+  using C = typename Store<S>::comp_t;
+  using P = typename Store<S>::pair_t;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int Vh = g.Vh, Vb = g.Vb;
+  const int h = threadIdx.x / Vh, j = threadIdx.x - h * Vh;
+
+  // the blockIdx.x-th block of this colour: blocks 2i and 2i+1 differ in colour
+  int b = 2 * blockIdx.x;
+  {
+    int bc[4];
+    block_coords(g, b, bc);
+    if (((bc[0] + bc[1] + bc[2] + bc[3]) & 1) != colour) b += 1;
+  }
+  const int r = blockIdx.y;
+  const void *bf = (const char *)bvec + r * fbytes;
+  void *xf = (char *)xvec + r * fbytes;
+
+  cpx<C> *rho = (cpx<C> *)smem;
+  cpx<C> *te = rho + 12 * Vh;
+  cpx<C> *re = te + 12 * Vh;
+  cpx<C> *xch = re + 12 * Vh;
+  C *red = (C *)(xch + 12 * Vh);
+
+  Tile<P> Lt, Ao, Ai;
+  if constexpr (STAGE) {
+    P *sl = (P *)(red + 96);
+    P *sa = sl + (size_t)36 * Vb;
+    P *si = sa + (size_t)36 * Vh;
+    const P *gl = (const P *)links + (size_t)b * 36 * Vb;
+    const P *ga = (const P *)clov + (size_t)b * 36 * Vb;
+    stage(sl, gl, (size_t)36 * Vb * sizeof(P));
+    for (int i = 0; i < 36; i++) stage(sa + (size_t)i * Vh, ga + (size_t)i * Vb + Vh, (size_t)Vh * sizeof(P));
+    stage(si, (const P *)cinv + (size_t)b * 36 * Vh, (size_t)36 * Vh * sizeof(P));
+    Lt = {sl, Vb};
+    Ao = {sa, Vh};
+    Ai = {si, Vh};
+  } else {
+    Lt = {(const P *)links + (size_t)b * 36 * Vb, Vb};
+    Ao = {(const P *)clov + (size_t)b * 36 * Vb + Vh, Vb};
+    Ai = {(const P *)cinv + (size_t)b * 36 * Vh, Vh};
+  }
+
+  const Site se = decode(g, b, j), so = decode(g, b, Vh + j);
+  cpx<C> r_e[6], r_o[6];
+
+  // ---- 2. block residual r = b - D x (halves h of the even and odd site)
+  {
+    Spinor<C> bb;
+    load_spinor<S, C>(bf, g, b, j, bb);
+    half_of(bb, h, r_e);
+    load_spinor<S, C>(bf, g, b, Vh + j, bb);
+    half_of(bb, h, r_o);
+  }
+  if (!(self_zero && halo_zero)) {
+    for (int par = 0; par < 2; par++) {
+      const Site &t = par ? so : se;
+      Spinor<C> part;
+      hops_global<S, C>(g, t, h, links, xf, self_zero, halo_zero, part);
+      cpx<C> hx[6], ax[6] = {}, m[18], xh[6];
+      exchange(xch, Vh, j, h, part, hx);
+      if (!self_zero) {
+        Spinor<C> xs;
+        load_spinor<S, C>(xf, g, b, t.s, xs);
+        half_of(xs, h, xh);
+        load_clover_block<S, C>(clov, Vb, b, t.s, h, m);
+        herm6_mv(m, xh, ax);
+      }
+#pragma unroll
+      for (int i = 0; i < 6; i++) {
+        cpx<C> d = {ax[i].re + hx[i].re, ax[i].im + hx[i].im};
+        if (par) { r_o[i].re -= d.re; r_o[i].im -= d.im; }
+        else     { r_e[i].re -= d.re; r_e[i].im -= d.im; }
+      }
+    }
+  }
+  if constexpr (STAGE) {
+    cp_async_wait_all();
+    __syncthreads();
+  }
+
+  // ---- 3. Schur right-hand side: te = A_ee^-1 r_e ; rho = r_o - D_oe te
+  cpx<C> m[18], tmp[6];
+  tile_block(Ai, j, h, m);
+  herm6_mv(m, r_e, tmp);
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    te[(6 * h + i) * Vh + j] = tmp[i];
+    re[(6 * h + i) * Vh + j] = r_e[i];
+  }
+  __syncthreads();
+  Spinor<C> part;
+  cpx<C> hv[6], rh[6], eo[6];
+  hops_inner(g, so, h, te, Lt, part);
+  exchange(xch, Vh, j, h, part, hv);
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    rh[i] = {r_o[i].re - hv[i].re, r_o[i].im - hv[i].im};
+    rho[(6 * h + i) * Vh + j] = rh[i];
+    eo[i] = {0, 0};
+  }
+  __syncthreads();
+
+  // ---- 4. MR steps
+  for (int it = 0; it < nmr; it++) {
+    // te = A_ee^-1 D_eo rho
+    hops_inner(g, se, h, rho, Lt, part);
+    exchange(xch, Vh, j, h, part, hv);
+    tile_block(Ai, j, h, m);
+    herm6_mv(m, hv, tmp);
+#pragma unroll
+    for (int i = 0; i < 6; i++) te[(6 * h + i) * Vh + j] = tmp[i];
+    __syncthreads();
+    // p = A_oo rho - D_oe te
+    hops_inner(g, so, h, te, Lt, part);
+    exchange(xch, Vh, j, h, part, hv);
+    cpx<C> p[6];
+    tile_block(Ao, j, h, m);
+    herm6_mv(m, rh, p);
+    C pr_re = 0, pr_im = 0, pp = 0;
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+      p[i].re -= hv[i].re;
+      p[i].im -= hv[i].im;
+      pr_re += p[i].re * rh[i].re + p[i].im * rh[i].im;
+      pr_im += p[i].re * rh[i].im - p[i].im * rh[i].re;
+      pp += p[i].re * p[i].re + p[i].im * p[i].im;
+    }
+    block_sum3(pr_re, pr_im, pp, red);
+    C a_re = 0, a_im = 0;
+    if (pp > (C)0) {
+      a_re = pr_re / pp;
+      a_im = pr_im / pp;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+      eo[i].re += a_re * rh[i].re - a_im * rh[i].im;
+      eo[i].im += a_re * rh[i].im + a_im * rh[i].re;
+      rh[i].re -= a_re * p[i].re - a_im * p[i].im;
+      rh[i].im -= a_re * p[i].im + a_im * p[i].re;
+      rho[(6 * h + i) * Vh + j] = rh[i];
+    }
+    __syncthreads();
+  }
+
+  // ---- 5. reconstruct e_e = A_ee^-1 (r_e - D_eo e_o), then x += e
+#pragma unroll
+  for (int i = 0; i < 6; i++) rho[(6 * h + i) * Vh + j] = eo[i];
+  __syncthreads();
+  hops_inner(g, se, h, rho, Lt, part);
+  exchange(xch, Vh, j, h, part, hv);
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    cpx<C> a = re[(6 * h + i) * Vh + j];
+    tmp[i] = {a.re - hv[i].re, a.im - hv[i].im};
+  }
+  tile_block(Ai, j, h, m);
+  cpx<C> ee[6];
+  herm6_mv(m, tmp, ee);
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    te[(6 * h + i) * Vh + j] = ee[i];
+    xch[(6 * h + i) * Vh + j] = eo[i];
+  }
+  __syncthreads();
+  {
+    // thread half 0 writes the even site j, half 1 the odd site j
+    const cpx<C> *src = h ? xch : te;
+    const int s = h ? Vh + j : j;
+    Spinor<C> xs, e;
+    vec_load(src, Vh, j, e);
+    if (self_zero) {
+      xs = e;
+    } else {
+      load_spinor<S, C>(xf, g, b, s, xs);
+#pragma unroll
+      for (int i = 0; i < 12; i++) {
+        xs.c[i].re += e.c[i].re;
+        xs.c[i].im += e.c[i].im;
+      }
+    }
+    store_spinor<S, C>(xf, g, b, s, xs);
+  }
+}
+
+template <typename S, bool STAGE>
+int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const void *bv, void *xv, int nrhs,
+          cudaStream_t st) {
+  size_t smem = SapSmem<S>::bytes(g, STAGE);
+  auto kern = k_sap_phase<S, STAGE>;
+  DD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  size_t fbytes = (size_t)g.V * 24 * sizeof(S);
+  dim3 grid(g.nblocks / 2, nrhs);
+  for (int sw = 0; sw < p.sweeps; sw++)
+    for (int colour = 0; colour < 2; colour++) {
+      // with x = 0 on entry: the first phase sees x = 0 everywhere, the
+      // second still has x = 0 on its own (colour-1) blocks
+      int self_zero = (p.x_is_zero && sw == 0) ? 1 : 0;
+      int halo_zero = (p.x_is_zero && sw == 0 && colour == 0) ? 1 : 0;
+      kern<<<grid, g.Vb, smem, st>>>(g, f.links, f.clov, f.cinv, bv, xv, colour, self_zero, halo_zero, p.mr_steps,
+                                     fbytes);
+      DD_LAUNCHED();
+    }
+  return DD_OK;
+}
+
+}  // namespace
+
+size_t sap_smem_bytes(const Geom &g, int prec, bool stage) {
+  switch (prec) {
+    case DD_F64: return SapSmem<double>::bytes(g, stage);
+    case DD_F32: return SapSmem<float>::bytes(g, stage);
+    case DD_F16: return SapSmem<__half>::bytes(g, stage);
+    default: return SapSmem<__nv_bfloat16>::bytes(g, stage);
+  }
+}
+
+int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const void *b, void *x, int nrhs,
+               cudaStream_t st) {
+  // stage the block's operator tiles in shared memory when they fit
+  const size_t limit = 227 * 1024;
+  if (g.Vb > 256) {
+    set_error("sap: blocks of more than 256 sites are not supported (got %d)", g.Vb);
+    return DD_EINVAL;
+  }
+  bool stage = sap_smem_bytes(g, f.prec, true) <= limit;
+  if (!stage && sap_smem_bytes(g, f.prec, false) > limit) {
+    set_error("sap: block of %d sites needs more shared memory than available", g.Vb);
+    return DD_EINVAL;
+  }
+  switch (f.prec) {
+    case DD_F64:
+      return stage ? sap_t<double, true>(g, f, p, b, x, nrhs, st) : sap_t<double, false>(g, f, p, b, x, nrhs, st);
+    case DD_F32:
+      return stage ? sap_t<float, true>(g, f, p, b, x, nrhs, st) : sap_t<float, false>(g, f, p, b, x, nrhs, st);
+    case DD_F16:
+      return stage ? sap_t<__half, true>(g, f, p, b, x, nrhs, st) : sap_t<__half, false>(g, f, p, b, x, nrhs, st);
+    case DD_BF16:
+      return stage ? sap_t<__nv_bfloat16, true>(g, f, p, b, x, nrhs, st)
+                   : sap_t<__nv_bfloat16, false>(g, f, p, b, x, nrhs, st);
+  }
+  set_error("sap: bad precision %d", f.prec);
+  return DD_EINVAL;
+}
+
+}  // namespace dd

@@ -131,6 +131,10 @@ WORKLOADS = {
     "sap_fgmres_96x48^3_mixed": dict(
         dims=(96, 48, 48, 48), eps=0.2, n_stout=3, rho=0.1, c_sw=1.7, m0=0.0,
         gauge_seed=31, rhs_seed=32, block=(4, 4, 4, 4), sweeps=4, mr_steps=4, restart=32),
+    # small case of the 64x32^3 workload for profiler captures (~1.8 GB on the device)
+    "profile_32x32x16x16_fp32": dict(
+        dims=(32, 32, 16, 16), eps=0.25, n_stout=2, rho=0.1, c_sw=1.7, m0=-0.02,
+        gauge_seed=21, rhs_seed=22, block=(4, 4, 4, 4), sweeps=4, mr_steps=4, restart=16),
     "batched_48^3x96_24rhs": dict(
         dims=(96, 48, 48, 48), eps=0.2, n_stout=3, rho=0.1, c_sw=1.7, m0=-0.02,
         gauge_seed=41, rhs_seed=42, block=(4, 4, 4, 4), sweeps=4, mr_steps=4, restart=16),

@@ -1,0 +1,82 @@
+"""GPU parity of the Schwarz smoother (SAP with even-odd MR block solves)
+against the FP64 oracle on the same seeded inputs.
+
+Fixed-step SAP has no closed form; GPU and oracle share one reading of it
+(red-black colouring, odd-site Schur complement, MR from zero, x0 = 0).
+Bounds (relative L2): FP64 1e-12 (rounding order only); FP32 1e-5;
+FP16 1e-2 and BF16 5e-2, from the storage unit roundoff (2^-11, 2^-8)
+amplified by the MR step count.
+"""
+import numpy as np
+import pytest
+
+import paper_1710_07041_gb300 as dd
+import synth
+from gpu_common import Setup, relerr
+
+pytestmark = pytest.mark.gpu
+
+TOL = {dd.F64: 1e-12, dd.F32: 1e-5, dd.F16: 1e-2, dd.BF16: 5e-2}
+CASES = [((4, 4, 4, 4), (2, 2, 2, 2), 4, 3),     # plain FP64 workload geometry (Vh = 8 < warp)
+         ((8, 8, 8, 8), (4, 4, 4, 4), 2, 4),
+         ((8, 8, 16, 8), (4, 4, 4, 4), 1, 4),
+         ((8, 8, 8, 16), (4, 2, 4, 4), 2, 2)]
+
+
+@pytest.mark.parametrize("prec", [dd.F64, dd.F32, dd.F16, dd.BF16])
+@pytest.mark.parametrize("dims,block,sweeps,nmr", CASES)
+def test_sap_matches_oracle(prec, dims, block, sweeps, nmr):
+    s = Setup(dims, block, eps=0.3, n_stout=1, c_sw=1.7, m0=-0.02, prec=prec, seed=11)
+    b = synth.gaussian_spinor(s.V, 12)
+    fb = s.lat.to_field(b, prec)
+    fx = s.lat.new_field(prec)
+    fx.fill_(0xFF)   # x is not read when x_is_zero
+    s.op.sap_smooth(fb, fx, sweeps, nmr, x_is_zero=True)
+    got = s.lat.from_field(fx, prec)
+    want = s.ref.sap(block, b, sweeps, nmr)
+    assert relerr(got, want) <= TOL[prec]
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [dd.F64, dd.F32])
+def test_sap_from_initial_guess(prec):
+    s = Setup((8, 8, 8, 8), (4, 4, 4, 4), prec=prec, seed=13)
+    b = synth.gaussian_spinor(s.V, 14)
+    x0 = synth.gaussian_spinor(s.V, 15) * 0.1
+    fb = s.lat.to_field(b, prec)
+    fx = s.lat.to_field(x0, prec)
+    s.op.sap_smooth(fb, fx, 2, 3, x_is_zero=False)
+    got = s.lat.from_field(fx, prec)
+    want = s.ref.sap(s.block, b, 2, 3, x0=s.lat.from_field(s.lat.to_field(x0, prec), prec))
+    assert relerr(got, want) <= TOL[prec]
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [dd.F64, dd.F32, dd.F16])
+def test_sap_batched_equals_single(prec):
+    s = Setup((8, 8, 8, 8), (4, 4, 4, 4), prec=prec, seed=16)
+    bs = np.stack([synth.gaussian_spinor(s.V, 30 + r) for r in range(3)])
+    fb = s.lat.to_field(bs, prec)
+    fx = s.lat.new_field(prec, 3)
+    s.op.sap_smooth(fb, fx, 2, 4, nrhs=3)
+    batched = s.lat.from_field(fx, prec, 3)
+    for r in range(3):
+        f1 = s.lat.to_field(bs[r], prec)
+        x1 = s.lat.new_field(prec)
+        s.op.sap_smooth(f1, x1, 2, 4)
+        assert np.array_equal(s.lat.from_field(x1, prec), batched[r])
+    s.close()
+
+
+def test_sap_reduces_residual():
+    s = Setup((8, 8, 8, 8), (4, 4, 4, 4), prec=dd.F32, seed=17)
+    b = synth.gaussian_spinor(s.V, 18)
+    fb = s.lat.to_field(b, dd.F32)
+    fx = s.lat.new_field(dd.F32)
+    res = []
+    for sw in (1, 2, 4):
+        s.op.sap_smooth(fb, fx, sw, 4)
+        x = s.lat.from_field(fx, dd.F32)
+        res.append(relerr(s.ref.apply(x), b))
+    assert res[0] < 1 and res[1] < res[0] and res[2] < res[1]
+    s.close()
