@@ -254,13 +254,14 @@ class Op(Handle):
         if inner_reduction is None:
             inner_reduction = 0.0 if self.prec == F64 else 1e-5
         on_dev = not isinstance(b, np.ndarray)
-        if on_dev:
-            nrhs = b.numel() // (24 * self.lat.V) if b.dtype != _complex_dtype() else b.numel() // (12 * self.lat.V)
-        else:
-            b = np.ascontiguousarray(b, dtype=np.complex128)
-            nrhs = b.size // (12 * self.lat.V)
+        b = _as_canonical(b, self.lat.V)
+        nrhs = _count_rhs(b, self.lat.V)
         if x is None:
             x = (np.zeros_like(b) if not on_dev else b.new_zeros(b.shape))
+        else:
+            x = _as_canonical(x, self.lat.V)
+            if _count_rhs(x, self.lat.V) != nrhs:
+                raise ValueError("x and b hold different numbers of right-hand sides")
         p = SolveParams(tol, restart, max_iter, SapParams(sweeps, mr_steps, 1, 0), inner_reduction,
                         DEVICE if on_dev else HOST, int(bool(use_x0)))
         infos = (SolveInfo * nrhs)()
@@ -270,9 +271,81 @@ class Op(Handle):
         return x, [i.as_dict() for i in infos]
 
 
-def _complex_dtype():
+def _as_canonical(a, V: int):
+    """Canonical FP64 spinors as complex128 (numpy) or float64/complex128
+    (torch, device); float64 numpy arrays are reinterpreted, never converted."""
+    if isinstance(a, np.ndarray):
+        if a.dtype == np.float64:
+            a = a.view(np.complex128)
+        if a.dtype != np.complex128 or not a.flags.c_contiguous:
+            raise TypeError("host spinors must be C-contiguous complex128 (or their float64 view)")
+        return a
     import torch
-    return torch.complex128
+    if a.dtype not in (torch.float64, torch.complex128) or not a.is_contiguous() or not a.is_cuda:
+        raise TypeError("device spinors must be contiguous CUDA float64/complex128 tensors")
+    return a
+
+
+def _count_rhs(a, V: int) -> int:
+    reals = a.size * 2 if isinstance(a, np.ndarray) else a.numel() * (2 if a.is_complex() else 1)
+    if reals % (24 * V):
+        raise ValueError("spinor array size is not a whole number of lattice fields")
+    return reals // (24 * V)
+
+
+class Server(Handle):
+    """Continuous-batching solve server (dd_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_slots: int = 8, max_batch_rhs: int = 16):
+        h = ctypes.c_void_p()
+        p = ServerParams(hbm_budget_bytes, max_slots, max_batch_rhs)
+        _check(lib().dd_server_create(ctypes.byref(p), ctypes.byref(h)), "dd_server_create")
+        self._h = h.value
+        self._keep = {}
+
+    def submit(self, op: Op, b: np.ndarray, tol=1e-10, restart=16, max_iter=1000, sweeps=4, mr_steps=4,
+               inner_reduction=None) -> int:
+        b = _as_canonical(np.ascontiguousarray(b), op.lat.V)
+        nrhs = _count_rhs(b, op.lat.V)
+        if inner_reduction is None:
+            inner_reduction = 0.0 if op.prec == F64 else 1e-5
+        sp = SolveParams(tol, restart, max_iter, SapParams(sweeps, mr_steps, 1, 0), inner_reduction, HOST, 0)
+        req = Request(op.handle, b.ctypes.data, nrhs, sp)
+        t = ctypes.c_uint64()
+        _check(lib().dd_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "dd_submit")
+        self._keep[t.value] = (op, nrhs)
+        return t.value
+
+    def poll(self, ticket: int):
+        """(state, x or None, infos or None); x/infos once the request has ended."""
+        op, nrhs = self._keep[ticket]
+        st = ctypes.c_int()
+        x = np.empty((nrhs, op.lat.V, 4, 3), dtype=np.complex128)
+        infos = (SolveInfo * nrhs)()
+        _check(lib().dd_poll(self._h, ticket, ctypes.byref(st), _ptr(x), infos), "dd_poll")
+        if st.value in (QUEUED, RUNNING):
+            return st.value, None, None
+        del self._keep[ticket]
+        return st.value, (x[0] if nrhs == 1 else x), [i.as_dict() for i in infos]
+
+    def wait(self, ticket: int, timeout: float = 600.0, interval: float = 0.002):
+        import time
+        t0 = time.time()
+        while True:
+            st, x, info = self.poll(ticket)
+            if x is not None:
+                return st, x, info
+            if time.time() - t0 > timeout:
+                raise TimeoutError(f"ticket {ticket} still in state {st}")
+            time.sleep(interval)
+
+    def cancel(self, ticket: int):
+        _check(lib().dd_cancel(self._h, ticket), "dd_cancel")
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().dd_server_get_stats(self._h, ctypes.byref(s)), "dd_server_get_stats")
+        return {k: getattr(s, k) for k, _ in s._fields_}
 
 
 def version() -> str:

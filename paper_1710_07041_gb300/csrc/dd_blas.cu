@@ -132,6 +132,182 @@ __global__ void k_update_x(Geom g, double *x, const void *Z, size_t zbytes, int 
   store_spinor<double, double>(x, g, b, s, acc);
 }
 
+
+// ------------------------------------------------------------------------
+// Double-float ("DF") vectors: each complex entry is a float4
+// (re_hi, im_hi, re_lo, im_lo) whose value is hi + lo, a 48-bit significand.
+// GB300 executes FP64 at a small fraction of its FP32 rate, so FP64 dot
+// products over the Krylov basis are ALU-bound; DF arithmetic built from
+// error-free FP32 transformations (Dekker's product, Knuth's TwoSum) keeps
+// FP64-class accuracy at FP32 throughput, so these kernels stay HBM-bound.
+
+struct df { float h, l; };
+
+// s += a * b   (a, b double-float; lazy accumulation: error terms collected in s.l)
+__device__ __forceinline__ void df_mac(df &s, float ah, float al, float bh, float bl) {
+  float p = ah * bh;
+  float pe = fmaf(ah, bh, -p);                  // exact error of the product
+  float c = fmaf(ah, bl, al * bh);              // cross terms
+  float t = s.h + p;                            // TwoSum(s.h, p)
+  float z = t - s.h;
+  float e = (s.h - (t - z)) + (p - z);
+  s.h = t;
+  s.l += e + pe + c;
+}
+// s -= a * b
+__device__ __forceinline__ void df_msub(df &s, float ah, float al, float bh, float bl) {
+  df_mac(s, -ah, -al, bh, bl);
+}
+__device__ __forceinline__ double df_val(const df &s) { return (double)s.h + (double)s.l; }
+__device__ __forceinline__ df df_norm(float h, float l) {
+  float t = h + l;
+  return {t, l - (t - h)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  float t = a.h + b.h;
+  float z = t - a.h;
+  float e = (a.h - (t - z)) + (b.h - z);
+  return {t, a.l + b.l + e};
+}
+
+// Block-reduce NV double-float values: warp shuffles in DF, then the warp
+// leaders' results in FP64 (fixed order).
+template <int NV>
+__device__ __forceinline__ void block_reduce_df(df *v, double *smem, double *out) {
+#pragma unroll
+  for (int i = 0; i < NV; i++)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      df u = {__shfl_xor_sync(0xffffffffu, v[i].h, o), __shfl_xor_sync(0xffffffffu, v[i].l, o)};
+      v[i] = df_add(v[i], u);
+    }
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < NV; i++) smem[i * 32 + w] = df_val(v[i]);
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0;
+    for (int k = 0; k < nw; k++) s += smem[threadIdx.x * 32 + k];
+    out[threadIdx.x] = s;
+  }
+}
+
+// partial[blk] = this block's sums of conj(V_i) w (i < k) and |w|^2, as doubles
+template <int KMAX>
+__global__ void __launch_bounds__(RED_TPB) k_df_mdot(const float4 *__restrict__ V, size_t ldv, int k,
+                                                     const float4 *__restrict__ w, size_t n, double *partial) {
+  __shared__ double smem[(2 * KMAX + 1) * 32];
+  df acc[2 * KMAX + 1];
+#pragma unroll
+  for (int i = 0; i < 2 * KMAX + 1; i++) acc[i] = {0.f, 0.f};
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    float4 we = w[e];
+    df_mac(acc[2 * KMAX], we.x, we.z, we.x, we.z);
+    df_mac(acc[2 * KMAX], we.y, we.w, we.y, we.w);
+#pragma unroll
+    for (int i = 0; i < KMAX; i++) {
+      if (i < k) {
+        float4 v = V[i * ldv + e];
+        // re += vr wr + vi wi ; im += vr wi - vi wr
+        df_mac(acc[2 * i], v.x, v.z, we.x, we.z);
+        df_mac(acc[2 * i], v.y, v.w, we.y, we.w);
+        df_mac(acc[2 * i + 1], v.x, v.z, we.y, we.w);
+        df_msub(acc[2 * i + 1], v.y, v.w, we.x, we.z);
+      }
+    }
+  }
+  block_reduce_df<2 * KMAX + 1>(acc, smem, partial + (size_t)blockIdx.x * (2 * KMAX + 1));
+}
+
+// w -= sum_i h_i V_i (h complex doubles on the device); partial[blk] = |w|^2
+template <int KMAX>
+__global__ void __launch_bounds__(RED_TPB) k_df_maxpy_norm(const float4 *__restrict__ V, size_t ldv, int k,
+                                                           const double2 *__restrict__ h, float4 *w, size_t n,
+                                                           double *partial) {
+  __shared__ double smem[32];
+  __shared__ float4 hs[KMAX];   // (re_hi, im_hi, re_lo, im_lo)
+  if (threadIdx.x < KMAX) {
+    double2 c = threadIdx.x < k ? h[threadIdx.x] : make_double2(0, 0);
+    float rh = (float)c.x, ih = (float)c.y;
+    hs[threadIdx.x] = make_float4(rh, ih, (float)(c.x - rh), (float)(c.y - ih));
+  }
+  __syncthreads();
+  df nrm = {0.f, 0.f};
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    float4 we = w[e];
+    df re = {we.x, we.z}, im = {we.y, we.w};
+#pragma unroll
+    for (int i = 0; i < KMAX; i++) {
+      if (i < k) {
+        float4 v = V[i * ldv + e], c = hs[i];
+        // w -= c v : re -= cr vr - ci vi ; im -= cr vi + ci vr
+        df_msub(re, c.x, c.z, v.x, v.z);
+        df_mac(re, c.y, c.w, v.y, v.w);
+        df_msub(im, c.x, c.z, v.y, v.w);
+        df_msub(im, c.y, c.w, v.x, v.z);
+      }
+    }
+    re = df_norm(re.h, re.l);
+    im = df_norm(im.h, im.l);
+    w[e] = make_float4(re.h, im.h, re.l, im.l);
+    df_mac(nrm, re.h, re.l, re.h, re.l);
+    df_mac(nrm, im.h, im.l, im.h, im.l);
+  }
+  block_reduce_df<1>(&nrm, smem, partial + blockIdx.x);
+}
+
+// y = a x (DF), a double
+__global__ void k_df_scale(float4 *y, const float4 *x, double a, size_t n) {
+  const float ah = (float)a, al = (float)(a - (double)ah);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    float4 v = x[e];
+    df re = {0.f, 0.f}, im = {0.f, 0.f};
+    df_mac(re, ah, al, v.x, v.z);
+    df_mac(im, ah, al, v.y, v.w);
+    re = df_norm(re.h, re.l);
+    im = df_norm(im.h, im.l);
+    y[e] = make_float4(re.h, im.h, re.l, im.l);
+  }
+}
+
+// y (DF) = a x (FP64)
+__global__ void k_f64_to_df(float4 *y, const double2 *x, double a, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double2 v = x[e];
+    double r = a * v.x, i = a * v.y;
+    float rh = (float)r, ih = (float)i;
+    y[e] = make_float4(rh, ih, (float)(r - rh), (float)(i - ih));
+  }
+}
+
+// Site-wise conversions between a DF field (FP64 chunk positions) and a
+// field of storage S: out = scale * in.
+template <typename S>
+__global__ void k_df_to_field(Geom g, const float4 *__restrict__ in, void *out, float scale) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= g.V) return;
+  int b = (int)(t / g.Vb), s = (int)(t - (long long)b * g.Vb);
+  Spinor<float> v;
+#pragma unroll
+  for (int c = 0; c < 12; c++) {
+    float4 q = in[((size_t)b * 12 + c) * g.Vb + s];
+    v.c[c] = {(q.x + q.z) * scale, (q.y + q.w) * scale};
+  }
+  store_spinor<S, float>(out, g, b, s, v);
+}
+
+template <typename S>
+__global__ void k_field_to_df(Geom g, const void *in, float4 *__restrict__ out) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= g.V) return;
+  int b = (int)(t / g.Vb), s = (int)(t - (long long)b * g.Vb);
+  Spinor<float> v;
+  load_spinor<S, float>(in, g, b, s, v);
+#pragma unroll
+  for (int c = 0; c < 12; c++) out[((size_t)b * 12 + c) * g.Vb + s] = make_float4(v.c[c].re, v.c[c].im, 0.f, 0.f);
+}
+
 }  // namespace
 
 Blas::~Blas() {
@@ -206,6 +382,76 @@ int Blas::scale(double *y, const double *x, double a, size_t n, cudaStream_t st)
 int Blas::xmy(const double *x, double *y, size_t n, cudaStream_t st) {
   k_xmy<<<nblk, RED_TPB, 0, st>>>((const double2 *)x, (double2 *)y, n);
   return launched("k_xmy");
+}
+
+int Blas::df_mdot(const float *V, size_t ldv, int k, const float *w, size_t n, double *h_dev, double *wnorm2_dev,
+                  cudaStream_t st) {
+  for (int i0 = 0; i0 < k || (k == 0 && i0 == 0); i0 += 16) {
+    int kk = k - i0 < 16 ? k - i0 : 16;
+    if (kk < 0) kk = 0;
+    const float4 *Vi = (const float4 *)V + (size_t)i0 * ldv;
+    if (kk <= 4)
+      k_df_mdot<4><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, (const float4 *)w, n, partial);
+    else
+      k_df_mdot<16><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, (const float4 *)w, n, partial);
+    int stride = kk <= 4 ? 9 : 33;
+    DD_LAUNCHED();
+    k_sum_partials<<<1, 64, 0, st>>>(partial, nblk, stride, stride, result);
+    DD_LAUNCHED();
+    if (kk > 0) DD_CUDA(cudaMemcpyAsync(h_dev + 2 * i0, result, sizeof(double) * 2 * kk, cudaMemcpyDeviceToDevice, st));
+    if (wnorm2_dev && i0 == 0)
+      DD_CUDA(cudaMemcpyAsync(wnorm2_dev, result + (stride - 1), sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (k == 0) break;
+  }
+  return DD_OK;
+}
+
+int Blas::df_maxpy_norm(const float *V, size_t ldv, int k, const double *h_dev, float *w, size_t n, double *norm2_dev,
+                        cudaStream_t st) {
+  if (k == 0) return df_mdot(V, ldv, 0, w, n, nullptr, norm2_dev, st);
+  for (int i0 = 0; i0 < k; i0 += 16) {
+    int kk = k - i0 < 16 ? k - i0 : 16;
+    const float4 *Vi = (const float4 *)V + (size_t)i0 * ldv;
+    const double2 *hi = (const double2 *)h_dev + i0;
+    if (kk <= 4)
+      k_df_maxpy_norm<4><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial);
+    else
+      k_df_maxpy_norm<16><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial);
+    DD_LAUNCHED();
+  }
+  k_sum_partials<<<1, 32, 0, st>>>(partial, nblk, 1, 1, norm2_dev);
+  return launched("k_sum_partials");
+}
+
+int Blas::df_scale(float *y, const float *x, double a, size_t n, cudaStream_t st) {
+  k_df_scale<<<nblk, RED_TPB, 0, st>>>((float4 *)y, (const float4 *)x, a, n);
+  return launched("k_df_scale");
+}
+
+int Blas::f64_to_df(float *y, const double *x, double a, size_t n, cudaStream_t st) {
+  k_f64_to_df<<<nblk, RED_TPB, 0, st>>>((float4 *)y, (const double2 *)x, a, n);
+  return launched("k_f64_to_df");
+}
+
+int Blas::df_to_field(const Geom &g, const float *in, int prec, void *out, double scale, cudaStream_t st) {
+  unsigned grid = (unsigned)((g.V + 127) / 128);
+  const float4 *x = (const float4 *)in;
+  switch (prec) {
+    case DD_F32: k_df_to_field<float><<<grid, 128, 0, st>>>(g, x, out, (float)scale); break;
+    case DD_F16: k_df_to_field<__half><<<grid, 128, 0, st>>>(g, x, out, (float)scale); break;
+    case DD_BF16: k_df_to_field<__nv_bfloat16><<<grid, 128, 0, st>>>(g, x, out, (float)scale); break;
+    default: set_error("df_to_field: bad precision"); return DD_EINVAL;
+  }
+  return launched("k_df_to_field");
+}
+
+int Blas::field_to_df(const Geom &g, int prec, const void *in, float *out, cudaStream_t st) {
+  unsigned grid = (unsigned)((g.V + 127) / 128);
+  switch (prec) {
+    case DD_F32: k_field_to_df<float><<<grid, 128, 0, st>>>(g, in, (float4 *)out); break;
+    default: set_error("field_to_df: bad precision"); return DD_EINVAL;
+  }
+  return launched("k_field_to_df");
 }
 
 int Blas::update_x(const Geom &g, double *x, int zprec, const void *Z, size_t zbytes, int k, const double *y_dev,

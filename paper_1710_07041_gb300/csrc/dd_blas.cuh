@@ -21,6 +21,17 @@ struct Blas {
   int norm2(const double *w, size_t n, double *norm2_dev, cudaStream_t st);
   int scale(double *y, const double *x, double a, size_t n, cudaStream_t st);
   int xmy(const double *x, double *y, size_t n, cudaStream_t st);  // y = x - y
+  // Double-float (DF) variants: vectors of n complex entries stored as float4
+  // (re_hi, im_hi, re_lo, im_lo); V_i = V + i * ldv complex entries.
+  int df_mdot(const float *V, size_t ldv, int k, const float *w, size_t n, double *h_dev, double *wnorm2_dev,
+              cudaStream_t st);
+  int df_maxpy_norm(const float *V, size_t ldv, int k, const double *h_dev, float *w, size_t n, double *norm2_dev,
+                    cudaStream_t st);
+  int df_scale(float *y, const float *x, double a, size_t n, cudaStream_t st);
+  int f64_to_df(float *y, const double *x, double a, size_t n, cudaStream_t st);  // y = a x
+  // site-wise: DF field -> storage `prec` (scaled), and FP32 field -> DF field
+  int df_to_field(const Geom &g, const float *in, int prec, void *out, double scale, cudaStream_t st);
+  int field_to_df(const Geom &g, int prec, const void *in, float *out, cudaStream_t st);
   // x += sum_i y_i Z_i, Z fields of precision zprec with zbytes stride
   int update_x(const Geom &g, double *x, int zprec, const void *Z, size_t zbytes, int k, const double *y_dev,
                cudaStream_t st);

@@ -33,15 +33,15 @@ __device__ __forceinline__ void dirac_dir(const Geom &g, const Site &t, const vo
 
 template <typename S>
 __global__ void __launch_bounds__(DIRAC_TPB) k_dirac(Geom g, const void *__restrict__ links,
-                                                     const void *__restrict__ clov, const void *__restrict__ in,
-                                                     void *__restrict__ out, int nrhs, size_t fbytes) {
+                                                     const void *__restrict__ clov, const RhsPtrs p) {
   using C = typename Store<S>::comp_t;
+  const int nrhs = p.n;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= g.V * nrhs) return;
   long long site = t / nrhs;
   int r = (int)(t - site * nrhs);
   int b = (int)(site / g.Vb), s = (int)(site - (long long)b * g.Vb);
-  const char *inr = (const char *)in + r * fbytes;
+  const void *inr = p.in[r];
   Site st = decode(g, b, s);
   Spinor<C> x, acc;
   load_spinor<S, C>(inr, g, b, s, x);
@@ -50,29 +50,51 @@ __global__ void __launch_bounds__(DIRAC_TPB) k_dirac(Geom g, const void *__restr
   dirac_dir<1, S, C>(g, st, links, inr, acc);
   dirac_dir<2, S, C>(g, st, links, inr, acc);
   dirac_dir<3, S, C>(g, st, links, inr, acc);
-  store_spinor<S, C>((char *)out + r * fbytes, g, b, s, acc);
+  store_spinor<S, C>(p.out[r], g, b, s, acc);
 }
 
 template <typename S>
-int dirac_t(const Geom &g, const OpFields &f, const void *in, void *out, int nrhs, cudaStream_t st) {
-  long long n = g.V * nrhs;
-  size_t fbytes = (size_t)g.V * 24 * sizeof(S);
-  k_dirac<S><<<(unsigned)((n + DIRAC_TPB - 1) / DIRAC_TPB), DIRAC_TPB, 0, st>>>(g, f.links, f.clov, in, out, nrhs,
-                                                                               fbytes);
+int dirac_t(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st) {
+  long long n = g.V * p.n;
+  k_dirac<S><<<(unsigned)((n + DIRAC_TPB - 1) / DIRAC_TPB), DIRAC_TPB, 0, st>>>(g, f.links, f.clov, p);
   return launched("k_dirac");
 }
 
 }  // namespace
 
-int launch_dirac(const Geom &g, const OpFields &f, const void *in, void *out, int nrhs, cudaStream_t st) {
+RhsPtrs contiguous(const void *in, void *out, int nrhs, size_t field_bytes) {
+  RhsPtrs p;
+  p.n = nrhs;
+  for (int r = 0; r < nrhs && r < MAX_RHS; r++) {
+    p.in[r] = (const char *)in + r * field_bytes;
+    p.out[r] = (char *)out + r * field_bytes;
+  }
+  return p;
+}
+
+int launch_dirac(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st) {
+  if (p.n < 1 || p.n > MAX_RHS) {
+    set_error("apply_D: 1..%d right-hand sides per launch", MAX_RHS);
+    return DD_EINVAL;
+  }
   switch (f.prec) {
-    case DD_F64: return dirac_t<double>(g, f, in, out, nrhs, st);
-    case DD_F32: return dirac_t<float>(g, f, in, out, nrhs, st);
-    case DD_F16: return dirac_t<__half>(g, f, in, out, nrhs, st);
-    case DD_BF16: return dirac_t<__nv_bfloat16>(g, f, in, out, nrhs, st);
+    case DD_F64: return dirac_t<double>(g, f, p, st);
+    case DD_F32: return dirac_t<float>(g, f, p, st);
+    case DD_F16: return dirac_t<__half>(g, f, p, st);
+    case DD_BF16: return dirac_t<__nv_bfloat16>(g, f, p, st);
   }
   set_error("apply_D: precision %d not available", f.prec);
   return DD_EINVAL;
+}
+
+int launch_dirac(const Geom &g, const OpFields &f, const void *in, void *out, int nrhs, cudaStream_t st) {
+  const size_t fb = (size_t)g.V * 24 * real_bytes(f.prec);
+  for (int r0 = 0; r0 < nrhs; r0 += MAX_RHS) {
+    int n = nrhs - r0 < MAX_RHS ? nrhs - r0 : MAX_RHS;
+    int rc = launch_dirac(g, f, contiguous((const char *)in + r0 * fb, (char *)out + r0 * fb, n, fb), st);
+    if (rc) return rc;
+  }
+  return DD_OK;
 }
 
 }  // namespace dd

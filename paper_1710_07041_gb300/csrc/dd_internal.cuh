@@ -471,6 +471,17 @@ struct Op {
 
 const OpFields *fields_for(const Op *op, int prec);
 
+// Per-right-hand-side field pointers, passed to kernels by value so that a
+// batch may mix vectors held anywhere in device memory.
+constexpr int MAX_RHS = 64;
+struct RhsPtrs {
+  const void *in[MAX_RHS];
+  void *out[MAX_RHS];
+  int n = 0;
+};
+// pointers of nrhs contiguous fields starting at in / out
+RhsPtrs contiguous(const void *in, void *out, int nrhs, size_t field_bytes);
+
 // --------------------------------------------------------- kernel launchers
 int launch_pack(const Geom &g, int prec, const double *canon, void *field, int nrhs, double scale, cudaStream_t st);
 int launch_unpack(const Geom &g, int prec, const void *field, double *canon, int nrhs, double scale, cudaStream_t st);
@@ -478,8 +489,11 @@ int launch_pack_links(const Geom &g, int prec, const double *links_canon, void *
 int launch_build_clover(const Geom &g, const double *links_canon, double c_sw, double m0, double *clov64,
                         double *cinv64, int *bad, cudaStream_t st);
 int launch_convert_pairs(int prec, const double *in, void *out, size_t npairs, cudaStream_t st);
+int launch_dirac(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st);
 int launch_dirac(const Geom &g, const OpFields &f, const void *in, void *out, int nrhs, cudaStream_t st);
-int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const void *b, void *x, int nrhs,
+// Schwarz sweeps; p.in = right-hand sides b, p.out = iterates x
+int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &sp, const RhsPtrs &p, cudaStream_t st);
+int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &sp, const void *b, void *x, int nrhs,
                cudaStream_t st);
 // spinor precision conversion between two internal layouts, y = scale * x
 int launch_convert_field(const Geom &g, int prec_in, const void *in, int prec_out, void *out, int nrhs, double scale,

@@ -62,41 +62,54 @@ __device__ __forceinline__ void vec_load(const cpx<C> *v, int Vh, int q, Spinor<
   for (int i = 0; i < 12; i++) o.c[i] = v[i * Vh + q];
 }
 
-// acc += hops into site t from in-block neighbours held in shared vector v,
-// directions {2h, 2h+1}. Links from the block's tile.
+// In-block neighbours of one site for the two directions of its thread half:
+// four bytes (dir 2h fwd, dir 2h bwd, dir 2h+1 fwd, dir 2h+1 bwd), each the
+// neighbour's index within the other parity's half-vector, 0xFF if the hop
+// leaves the block.
+__device__ __forceinline__ unsigned inner_neighbours(const Geom &g, const Site &t, int h) {
+  unsigned packed = 0;
+  for (int k = 0; k < 4; k++) {
+    int nb, ns;
+    float sg;
+    bool inside;
+    neighbour(g, t, 2 * h + (k >> 1), (k & 1) ? -1 : +1, &nb, &ns, &sg, &inside);
+    unsigned idx = inside ? (unsigned)(ns - (t.p ? 0 : g.Vh)) : 0xFFu;
+    packed |= idx << (8 * k);
+  }
+  return packed;
+}
+
+// acc += hop pair in direction MU into the site at tile position s from the
+// shared half-vector v (the other parity), links from tile L. nf/nbk: neighbour
+// indices (0xFF: outside the block); off: tile offset of the other parity.
 template <int MU, typename C, typename P>
-__device__ __forceinline__ void hop_inner_dir(const Geom &g, const Site &t, const cpx<C> *v, const Tile<P> &L,
-                                              Spinor<C> &acc) {
-  int nb, ns;
-  float sg;
-  bool inside;
+__device__ __forceinline__ void hop_inner_dir(int Vh, int s, unsigned nf, unsigned nbk, int off, const cpx<C> *v,
+                                              const Tile<P> &L, Spinor<C> &acc) {
   Link<C> u;
   Spinor<C> psi;
-  neighbour(g, t, MU, +1, &nb, &ns, &sg, &inside);
-  if (inside) {
-    vec_load(v, g.Vh, ns - (t.p ? 0 : g.Vh), psi);
-    tile_link(L, t.s, MU, u);
+  if (nf != 0xFFu) {
+    vec_load(v, Vh, (int)nf, psi);
+    tile_link(L, s, MU, u);
     hop<MU, true>(acc, u, psi, (C)-0.5);
   }
-  neighbour(g, t, MU, -1, &nb, &ns, &sg, &inside);
-  if (inside) {
-    vec_load(v, g.Vh, ns - (t.p ? 0 : g.Vh), psi);
-    tile_link(L, ns, MU, u);
+  if (nbk != 0xFFu) {
+    vec_load(v, Vh, (int)nbk, psi);
+    tile_link(L, (int)nbk + off, MU, u);
     hop<MU, false>(acc, u, psi, (C)-0.5);
   }
 }
 
 template <typename C, typename P>
-__device__ __forceinline__ void hops_inner(const Geom &g, const Site &t, int h, const cpx<C> *v, const Tile<P> &L,
-                                           Spinor<C> &acc) {
+__device__ __forceinline__ void hops_inner(int Vh, int s, int h, unsigned nbr, int off, const cpx<C> *v,
+                                           const Tile<P> &L, Spinor<C> &acc) {
 #pragma unroll
   for (int i = 0; i < 12; i++) acc.c[i] = {0, 0};
   if (h == 0) {
-    hop_inner_dir<0>(g, t, v, L, acc);
-    hop_inner_dir<1>(g, t, v, L, acc);
+    hop_inner_dir<0>(Vh, s, nbr & 0xFFu, (nbr >> 8) & 0xFFu, off, v, L, acc);
+    hop_inner_dir<1>(Vh, s, (nbr >> 16) & 0xFFu, nbr >> 24, off, v, L, acc);
   } else {
-    hop_inner_dir<2>(g, t, v, L, acc);
-    hop_inner_dir<3>(g, t, v, L, acc);
+    hop_inner_dir<2>(Vh, s, nbr & 0xFFu, (nbr >> 8) & 0xFFu, off, v, L, acc);
+    hop_inner_dir<3>(Vh, s, (nbr >> 16) & 0xFFu, nbr >> 24, off, v, L, acc);
   }
 }
 
@@ -148,7 +161,9 @@ __device__ __forceinline__ void half_of(const Spinor<C> &s, int h, cpx<C> *out) 
 }
 
 // Exchange partial hop sums between the two halves of a site pair: on return
-// own[0..5] = full sum of the components of half h. xch: [12][Vh] smem.
+// own[0..5] = full sum of the components of half h. xch: [12][Vh] smem. A
+// thread reads only the entries its partner wrote for it, so the next write
+// to xch needs one barrier after this call (every caller has one).
 template <typename C>
 __device__ __forceinline__ void exchange(cpx<C> *xch, int Vh, int j, int h, const Spinor<C> &part, cpx<C> *own) {
   const int other = 6 * (1 - h), mine = 6 * h;
@@ -160,7 +175,6 @@ __device__ __forceinline__ void exchange(cpx<C> *xch, int Vh, int j, int h, cons
     cpx<C> a = h ? part.c[6 + i] : part.c[i], b = xch[(mine + i) * Vh + j];
     own[i] = {a.re + b.re, a.im + b.im};
   }
-  __syncthreads();
 }
 
 // deterministic block sum of three values; red: smem [3][32]
@@ -194,7 +208,7 @@ template <typename S> struct SapSmem {
   using P = typename Store<S>::pair_t;
   static size_t vec_bytes(const Geom &g) { return (size_t)12 * g.Vh * sizeof(cpx<C>); }
   static size_t bytes(const Geom &g, bool stage) {
-    size_t b = 4 * vec_bytes(g) + 96 * sizeof(C);
+    size_t b = 3 * vec_bytes(g) + 96 * sizeof(C);
     if (stage) b += (size_t)36 * (g.Vb + 2 * g.Vh) * sizeof(P);
     return b;
   }
@@ -203,9 +217,8 @@ template <typename S> struct SapSmem {
 template <typename S, bool STAGE>
 __global__ void __launch_bounds__(256, 1) k_sap_phase(Geom g, const void *__restrict__ links,
                                                    const void *__restrict__ clov, const void *__restrict__ cinv,
-                                                   const void *__restrict__ bvec, void *__restrict__ xvec,
-                                                   int colour, int self_zero, int halo_zero, int nmr,
-                                                   size_t fbytes) {
+                                                   const RhsPtrs rp, int colour, int self_zero,
+                                                   int halo_zero, int nmr) {
   using C = typename Store<S>::comp_t;
   using P = typename Store<S>::pair_t;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -219,14 +232,12 @@ __global__ void __launch_bounds__(256, 1) k_sap_phase(Geom g, const void *__rest
     block_coords(g, b, bc);
     if (((bc[0] + bc[1] + bc[2] + bc[3]) & 1) != colour) b += 1;
   }
-  const int r = blockIdx.y;
-  const void *bf = (const char *)bvec + r * fbytes;
-  void *xf = (char *)xvec + r * fbytes;
+  const void *bf = rp.in[blockIdx.y];
+  void *xf = rp.out[blockIdx.y];
 
-  cpx<C> *rho = (cpx<C> *)smem;
-  cpx<C> *te = rho + 12 * Vh;
-  cpx<C> *re = te + 12 * Vh;
-  cpx<C> *xch = re + 12 * Vh;
+  cpx<C> *rho = (cpx<C> *)smem;   // MR residual on odd sites (then e_o)
+  cpx<C> *te = rho + 12 * Vh;     // even-site temporary
+  cpx<C> *xch = te + 12 * Vh;     // partial-sum exchange between thread halves
   C *red = (C *)(xch + 12 * Vh);
 
   Tile<P> Lt, Ao, Ai;
@@ -249,6 +260,7 @@ __global__ void __launch_bounds__(256, 1) k_sap_phase(Geom g, const void *__rest
   }
 
   const Site se = decode(g, b, j), so = decode(g, b, Vh + j);
+  const unsigned nbr_e = inner_neighbours(g, se, h), nbr_o = inner_neighbours(g, so, h);
   cpx<C> r_e[6], r_o[6];
 
   // ---- 2. block residual r = b - D x (halves h of the even and odd site)
@@ -260,6 +272,7 @@ __global__ void __launch_bounds__(256, 1) k_sap_phase(Geom g, const void *__rest
     half_of(bb, h, r_o);
   }
   if (!(self_zero && halo_zero)) {
+#pragma unroll 1
     for (int par = 0; par < 2; par++) {
       const Site &t = par ? so : se;
       Spinor<C> part;
@@ -279,91 +292,89 @@ __global__ void __launch_bounds__(256, 1) k_sap_phase(Geom g, const void *__rest
         if (par) { r_o[i].re -= d.re; r_o[i].im -= d.im; }
         else     { r_e[i].re -= d.re; r_e[i].im -= d.im; }
       }
+      __syncthreads();
     }
   }
   if constexpr (STAGE) {
+    // each thread waits for its own copies; the barrier publishes everyone's
     cp_async_wait_all();
     __syncthreads();
   }
 
-  // ---- 3. Schur right-hand side: te = A_ee^-1 r_e ; rho = r_o - D_oe te
-  cpx<C> m[18], tmp[6];
+  // ---- 3.-5. Schur right-hand side, MR steps, reconstruction: one loop of
+  // half-steps, odd steps on the odd site (input te), even steps on the even
+  // site (input rho). Step 0: rho = r_o - D_oe A_ee^-1 r_e. Steps 1..2 n_MR:
+  // te = A_ee^-1 D_eo rho, then p = A_oo rho - D_oe te and the MR update.
+  // Last step: e_e = A_ee^-1 (r_e - D_eo e_o).
+  cpx<C> m[18], tmp[6], rh[6], eo[6], ee[6];
   tile_block(Ai, j, h, m);
   herm6_mv(m, r_e, tmp);
 #pragma unroll
   for (int i = 0; i < 6; i++) {
     te[(6 * h + i) * Vh + j] = tmp[i];
-    re[(6 * h + i) * Vh + j] = r_e[i];
-  }
-  __syncthreads();
-  Spinor<C> part;
-  cpx<C> hv[6], rh[6], eo[6];
-  hops_inner(g, so, h, te, Lt, part);
-  exchange(xch, Vh, j, h, part, hv);
-#pragma unroll
-  for (int i = 0; i < 6; i++) {
-    rh[i] = {r_o[i].re - hv[i].re, r_o[i].im - hv[i].im};
-    rho[(6 * h + i) * Vh + j] = rh[i];
     eo[i] = {0, 0};
+    rh[i] = {0, 0};
   }
   __syncthreads();
-
-  // ---- 4. MR steps
-  for (int it = 0; it < nmr; it++) {
-    // te = A_ee^-1 D_eo rho
-    hops_inner(g, se, h, rho, Lt, part);
+  const int last = 2 * nmr + 1;
+#pragma unroll 1
+  for (int step = 0; step <= last; step++) {
+    const bool odd = (step & 1) == 0;
+    Spinor<C> part;
+    hops_inner(Vh, odd ? Vh + j : j, h, odd ? nbr_o : nbr_e, odd ? 0 : Vh, odd ? te : rho, Lt, part);
+    cpx<C> hv[6], u[6], mu[6];
     exchange(xch, Vh, j, h, part, hv);
-    tile_block(Ai, j, h, m);
-    herm6_mv(m, hv, tmp);
+    // one clover multiply per step: A_oo rho (odd), A_ee^-1 D_eo rho (even),
+    // A_ee^-1 (r_e - D_eo e_o) (last)
 #pragma unroll
-    for (int i = 0; i < 6; i++) te[(6 * h + i) * Vh + j] = tmp[i];
-    __syncthreads();
-    // p = A_oo rho - D_oe te
-    hops_inner(g, so, h, te, Lt, part);
-    exchange(xch, Vh, j, h, part, hv);
-    cpx<C> p[6];
-    tile_block(Ao, j, h, m);
-    herm6_mv(m, rh, p);
-    C pr_re = 0, pr_im = 0, pp = 0;
+    for (int i = 0; i < 6; i++)
+      u[i] = odd ? rh[i] : (step == last ? cpx<C>{r_e[i].re - hv[i].re, r_e[i].im - hv[i].im} : hv[i]);
+    tile_block(odd ? Ao : Ai, j, h, m);
+    herm6_mv(m, u, mu);
+    if (odd) {
+      if (step == 0) {
 #pragma unroll
-    for (int i = 0; i < 6; i++) {
-      p[i].re -= hv[i].re;
-      p[i].im -= hv[i].im;
-      pr_re += p[i].re * rh[i].re + p[i].im * rh[i].im;
-      pr_im += p[i].re * rh[i].im - p[i].im * rh[i].re;
-      pp += p[i].re * p[i].re + p[i].im * p[i].im;
-    }
-    block_sum3(pr_re, pr_im, pp, red);
-    C a_re = 0, a_im = 0;
-    if (pp > (C)0) {
-      a_re = pr_re / pp;
-      a_im = pr_im / pp;
-    }
+        for (int i = 0; i < 6; i++) rh[i] = {r_o[i].re - hv[i].re, r_o[i].im - hv[i].im};
+      } else {
+        cpx<C> p[6];
+        C pr_re = 0, pr_im = 0, pp = 0;
 #pragma unroll
-    for (int i = 0; i < 6; i++) {
-      eo[i].re += a_re * rh[i].re - a_im * rh[i].im;
-      eo[i].im += a_re * rh[i].im + a_im * rh[i].re;
-      rh[i].re -= a_re * p[i].re - a_im * p[i].im;
-      rh[i].im -= a_re * p[i].im + a_im * p[i].re;
-      rho[(6 * h + i) * Vh + j] = rh[i];
+        for (int i = 0; i < 6; i++) {
+          p[i] = {mu[i].re - hv[i].re, mu[i].im - hv[i].im};
+          pr_re += p[i].re * rh[i].re + p[i].im * rh[i].im;
+          pr_im += p[i].re * rh[i].im - p[i].im * rh[i].re;
+          pp += p[i].re * p[i].re + p[i].im * p[i].im;
+        }
+        block_sum3(pr_re, pr_im, pp, red);
+        C a_re = 0, a_im = 0;
+        if (pp > (C)0) {
+          a_re = pr_re / pp;
+          a_im = pr_im / pp;
+        }
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+          eo[i].re += a_re * rh[i].re - a_im * rh[i].im;
+          eo[i].im += a_re * rh[i].im + a_im * rh[i].re;
+          rh[i].re -= a_re * p[i].re - a_im * p[i].im;
+          rh[i].im -= a_re * p[i].im + a_im * p[i].re;
+        }
+      }
+      // the even half-step after the last MR update reads e_o instead of rho
+      const bool last_odd = step == 2 * nmr;
+#pragma unroll
+      for (int i = 0; i < 6; i++) rho[(6 * h + i) * Vh + j] = last_odd ? eo[i] : rh[i];
+    } else if (step == last) {
+#pragma unroll
+      for (int i = 0; i < 6; i++) ee[i] = mu[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 6; i++) te[(6 * h + i) * Vh + j] = mu[i];
     }
     __syncthreads();
   }
 
-  // ---- 5. reconstruct e_e = A_ee^-1 (r_e - D_eo e_o), then x += e
-#pragma unroll
-  for (int i = 0; i < 6; i++) rho[(6 * h + i) * Vh + j] = eo[i];
-  __syncthreads();
-  hops_inner(g, se, h, rho, Lt, part);
-  exchange(xch, Vh, j, h, part, hv);
-#pragma unroll
-  for (int i = 0; i < 6; i++) {
-    cpx<C> a = re[(6 * h + i) * Vh + j];
-    tmp[i] = {a.re - hv[i].re, a.im - hv[i].im};
-  }
-  tile_block(Ai, j, h, m);
-  cpx<C> ee[6];
-  herm6_mv(m, tmp, ee);
+  // ---- x += e: gather both halves through shared memory, then half 0
+  // writes the even site j and half 1 the odd site j
 #pragma unroll
   for (int i = 0; i < 6; i++) {
     te[(6 * h + i) * Vh + j] = ee[i];
@@ -371,7 +382,6 @@ __global__ void __launch_bounds__(256, 1) k_sap_phase(Geom g, const void *__rest
   }
   __syncthreads();
   {
-    // thread half 0 writes the even site j, half 1 the odd site j
     const cpx<C> *src = h ? xch : te;
     const int s = h ? Vh + j : j;
     Spinor<C> xs, e;
@@ -391,21 +401,18 @@ __global__ void __launch_bounds__(256, 1) k_sap_phase(Geom g, const void *__rest
 }
 
 template <typename S, bool STAGE>
-int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const void *bv, void *xv, int nrhs,
-          cudaStream_t st) {
+int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
   size_t smem = SapSmem<S>::bytes(g, STAGE);
   auto kern = k_sap_phase<S, STAGE>;
   DD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  size_t fbytes = (size_t)g.V * 24 * sizeof(S);
-  dim3 grid(g.nblocks / 2, nrhs);
+  dim3 grid(g.nblocks / 2, rp.n);
   for (int sw = 0; sw < p.sweeps; sw++)
     for (int colour = 0; colour < 2; colour++) {
       // with x = 0 on entry: the first phase sees x = 0 everywhere, the
       // second still has x = 0 on its own (colour-1) blocks
       int self_zero = (p.x_is_zero && sw == 0) ? 1 : 0;
       int halo_zero = (p.x_is_zero && sw == 0 && colour == 0) ? 1 : 0;
-      kern<<<grid, g.Vb, smem, st>>>(g, f.links, f.clov, f.cinv, bv, xv, colour, self_zero, halo_zero, p.mr_steps,
-                                     fbytes);
+      kern<<<grid, g.Vb, smem, st>>>(g, f.links, f.clov, f.cinv, rp, colour, self_zero, halo_zero, p.mr_steps);
       DD_LAUNCHED();
     }
   return DD_OK;
@@ -424,6 +431,20 @@ size_t sap_smem_bytes(const Geom &g, int prec, bool stage) {
 
 int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const void *b, void *x, int nrhs,
                cudaStream_t st) {
+  const size_t fb = (size_t)g.V * 24 * real_bytes(f.prec);
+  for (int r0 = 0; r0 < nrhs; r0 += MAX_RHS) {
+    int n = nrhs - r0 < MAX_RHS ? nrhs - r0 : MAX_RHS;
+    int rc = launch_sap(g, f, p, contiguous((const char *)b + r0 * fb, (char *)x + r0 * fb, n, fb), st);
+    if (rc) return rc;
+  }
+  return DD_OK;
+}
+
+int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
+  if (rp.n < 1 || rp.n > MAX_RHS) {
+    set_error("sap: 1..%d right-hand sides per launch", MAX_RHS);
+    return DD_EINVAL;
+  }
   // stage the block's operator tiles in shared memory when they fit
   const size_t limit = 227 * 1024;
   if (g.Vb > 256) {
@@ -437,14 +458,13 @@ int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const v
   }
   switch (f.prec) {
     case DD_F64:
-      return stage ? sap_t<double, true>(g, f, p, b, x, nrhs, st) : sap_t<double, false>(g, f, p, b, x, nrhs, st);
+      return stage ? sap_t<double, true>(g, f, p, rp, st) : sap_t<double, false>(g, f, p, rp, st);
     case DD_F32:
-      return stage ? sap_t<float, true>(g, f, p, b, x, nrhs, st) : sap_t<float, false>(g, f, p, b, x, nrhs, st);
+      return stage ? sap_t<float, true>(g, f, p, rp, st) : sap_t<float, false>(g, f, p, rp, st);
     case DD_F16:
-      return stage ? sap_t<__half, true>(g, f, p, b, x, nrhs, st) : sap_t<__half, false>(g, f, p, b, x, nrhs, st);
+      return stage ? sap_t<__half, true>(g, f, p, rp, st) : sap_t<__half, false>(g, f, p, rp, st);
     case DD_BF16:
-      return stage ? sap_t<__nv_bfloat16, true>(g, f, p, b, x, nrhs, st)
-                   : sap_t<__nv_bfloat16, false>(g, f, p, b, x, nrhs, st);
+      return stage ? sap_t<__nv_bfloat16, true>(g, f, p, rp, st) : sap_t<__nv_bfloat16, false>(g, f, p, rp, st);
   }
   set_error("sap: bad precision %d", f.prec);
   return DD_EINVAL;

@@ -4,283 +4,412 @@
 // SAP-preconditioned fine-grid Krylov solve, with mixed precision in the
 // spirit of Sec. 3.1's half-precision storage: the smoother works in the
 // operator's storage precision, while the Arnoldi orthogonalisation, the
-// least-squares update and the true residual are FP64. Preconditioned
-// vectors z_j are kept in FP32 (FP64 for an FP64 operator), and the Arnoldi
-// product D z_j uses the operator in that same precision, so D Z = V H holds
-// to that precision; every cycle ends with the FP64 true residual, so the
-// restarts act as iterative refinement.
-#include <chrono>
+// least-squares update and the true residual are FP64. Preconditioned vectors
+// z_j are kept in FP32 (FP64 for an FP64 operator) and the Arnoldi product
+// D z_j uses the operator in that same precision, so D Z = V H holds to that
+// precision; each cycle ends with the FP64 true residual, so restarts act as
+// iterative refinement.
+//
+// Batching: right-hand sides that share an operator occupy the slots of one
+// BatchSolver. Per Arnoldi step all slots' Schwarz sweeps are one launch per
+// colour phase and all Dslash products one launch; each slot's reductions,
+// Givens rotations and convergence decisions are its own, so a right-hand
+// side gets bit-identical results alone or in any mix.
 #include <cmath>
 #include <complex>
 #include <vector>
 
-#include "dd_blas.cuh"
 #include "dd_solver.cuh"
 
 namespace dd {
 
 using cd = std::complex<double>;
-
-SolveWork::~SolveWork() { release(); }
-
-void SolveWork::release() {
-  void *ptrs[] = {Vb, Z, w, r, x, b, tmp, tin, tout, zt, canon, hdev, ydev};
-  for (void *p : ptrs)
-    if (p) cudaFree(p);
-  Vb = nullptr; Z = nullptr; w = r = x = b = tmp = nullptr; tin = tout = zt = nullptr; canon = nullptr;
-  hdev = ydev = nullptr;
-  for (auto &e : ev)
-    if (e) { cudaEventDestroy(e); e = nullptr; }
-  bytes = 0;
-}
-
-size_t SolveWork::bytes_needed(const Geom &g, int prec, int m) {
-  size_t f64 = (size_t)g.V * 24 * 8;
-  int zprec = prec == DD_F64 ? DD_F64 : DD_F32;
-  size_t fz = (size_t)g.V * 24 * real_bytes(zprec), fp = (size_t)g.V * 24 * real_bytes(prec);
-  return (size_t)(m + 1) * f64 + (size_t)m * fz + 6 * f64 + 2 * fp + fz + (1 << 16);
-}
-
-int SolveWork::ensure(const Geom &g, int prec_, int m_) {
-  if (Vb && m_ <= m && prec_ == prec && g.V == V) return DD_OK;
-  release();
-  prec = prec_;
-  m = m_;
-  V = g.V;
-  zprec = prec == DD_F64 ? DD_F64 : DD_F32;
-  size_t f64 = (size_t)g.V * 24 * 8;
-  zbytes = (size_t)g.V * 24 * real_bytes(zprec);
-  pbytes = (size_t)g.V * 24 * real_bytes(prec);
-  bool ok = cudaMalloc((void **)&Vb, (size_t)(m + 1) * f64) == cudaSuccess &&
-            cudaMalloc(&Z, (size_t)m * zbytes) == cudaSuccess && cudaMalloc((void **)&w, f64) == cudaSuccess &&
-            cudaMalloc((void **)&r, f64) == cudaSuccess && cudaMalloc((void **)&x, f64) == cudaSuccess &&
-            cudaMalloc((void **)&b, f64) == cudaSuccess && cudaMalloc((void **)&tmp, f64) == cudaSuccess &&
-            cudaMalloc((void **)&canon, f64) == cudaSuccess && cudaMalloc(&tin, pbytes) == cudaSuccess &&
-            cudaMalloc(&tout, pbytes) == cudaSuccess && cudaMalloc(&zt, zbytes) == cudaSuccess &&
-            cudaMalloc((void **)&hdev, sizeof(double) * 4 * 80) == cudaSuccess &&
-            cudaMalloc((void **)&ydev, sizeof(double) * 2 * 80) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    release();
-    set_error("dd_solve: out of device memory for the FGMRES(%d) workspace", m_);
-    return DD_ENOMEM;
-  }
-  for (auto &e : ev) DD_CUDA(cudaEventCreate(&e));
-  if (!blas.partial) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int rc = blas.init(sms);
-    if (rc) return rc;
-  }
-  bytes = bytes_needed(g, prec, m);
-  return DD_OK;
-}
-
 namespace {
-
-double host_norm2(Blas &bl, const double *v, size_t n, cudaStream_t st, int *rc) {
-  *rc = bl.norm2(v, n, bl.result + 200, st);
-  if (*rc) return 0;
-  *rc = cuda_fail(cudaMemcpyAsync(bl.hpin, bl.result + 200, sizeof(double), cudaMemcpyDeviceToHost, st), "norm");
-  if (!*rc) *rc = cuda_fail(cudaStreamSynchronize(st), "norm sync");
-  return bl.hpin[0];
-}
+constexpr int W0 = 130, W1 = 131, RN = 132, BN = 133;
 
 float ev_ms(cudaEvent_t a, cudaEvent_t b) {
   float t = 0;
   cudaEventElapsedTime(&t, a, b);
   return t;
 }
-
 }  // namespace
-
-// One right-hand side: W.b holds b (FP64 field), W.x the initial guess.
-int fgmres_one(const Op *op, const dd_solve_params &p, SolveWork &W, dd_solve_info &info, cudaStream_t st,
-               const volatile int *cancel) {
-  const Geom &g = op->lat->g;
-  const size_t n = (size_t)g.V * 12;  // complex entries of one field
-  const int m = p.restart;
-  const double sigma = std::sqrt(24.0 * (double)g.V);  // unit-norm vector -> unit RMS entries
-  Blas &bl = W.blas;
-  int rc = 0;
-  auto t0 = std::chrono::steady_clock::now();
-  double ms_sap = 0, ms_dirac = 0, ms_orth = 0;
-
-  double bnorm = std::sqrt(host_norm2(bl, W.b, n, st, &rc));
-  if (rc) return rc;
-  info.iterations = info.cycles = 0;
-  if (bnorm == 0) {
-    DD_CUDA(cudaMemsetAsync(W.x, 0, n * 16, st));
-    DD_CUDA(cudaStreamSynchronize(st));
-    info.status = DD_OK;
-    info.true_rel_residual = info.est_rel_residual = 0;
-    return DD_OK;
-  }
-  std::vector<cd> H((size_t)(m + 1) * m), gv(m + 1), sn(m), y(m);
-  std::vector<double> cs(m);
-  int its = 0;
-  double rel = 1, est = 1;
-  int status = DD_ENOTCONV;
-  for (;;) {
-    // true residual r = b - D x (FP64)
-    cudaEventRecord(W.ev[0], st);
-    if ((rc = launch_dirac(g, op->f64, W.x, W.r, 1, st))) return rc;
-    if ((rc = bl.xmy(W.b, W.r, n, st))) return rc;
-    cudaEventRecord(W.ev[1], st);
-    double beta = std::sqrt(host_norm2(bl, W.r, n, st, &rc));
-    if (rc) return rc;
-    ms_dirac += ev_ms(W.ev[0], W.ev[1]);
-    rel = beta / bnorm;
-    if (!std::isfinite(rel)) {
-      set_error("dd_solve: residual is not finite");
-      status = DD_ENOTCONV;
-      break;
-    }
-    if (rel <= p.tol) { status = DD_OK; est = rel; break; }
-    if (its >= p.max_iter) { status = DD_ENOTCONV; break; }
-    if (cancel && *cancel) { status = DD_ECANCELLED; break; }
-    info.cycles++;
-    if ((rc = bl.scale(W.Vb, W.r, 1.0 / beta, n, st))) return rc;
-    std::fill(gv.begin(), gv.end(), cd(0));
-    gv[0] = beta;
-    const double target = std::max(p.tol * bnorm, p.inner_reduction * beta);
-    int k = 0;
-    for (int j = 0; j < m && its < p.max_iter; j++) {
-      double *vj = W.Vb + 2 * n * j;
-      char *zj = (char *)W.Z + (size_t)j * W.zbytes;
-      // z_j = SAP(v_j) in the smoother's precision, kept in zprec
-      cudaEventRecord(W.ev[0], st);
-      if ((rc = launch_convert_field(g, DD_F64, vj, op->prec, W.tin, 1, sigma, st))) return rc;
-      dd_sap_params sp = p.sap;
-      sp.x_is_zero = 1;
-      if ((rc = launch_sap(g, op->fp, sp, W.tin, W.tout, 1, st))) return rc;
-      if ((rc = launch_convert_field(g, op->prec, W.tout, W.zprec, zj, 1, 1.0 / sigma, st))) return rc;
-      cudaEventRecord(W.ev[1], st);
-      // w = D z_j
-      if (W.zprec == DD_F64) {
-        if ((rc = launch_dirac(g, op->f64, zj, W.w, 1, st))) return rc;
-      } else {
-        if ((rc = launch_dirac(g, op->f32, zj, W.zt, 1, st))) return rc;
-        if ((rc = launch_convert_field(g, DD_F32, W.zt, DD_F64, W.w, 1, 1.0, st))) return rc;
-      }
-      cudaEventRecord(W.ev[2], st);
-      its++;
-      // classical Gram-Schmidt, repeated once when the norm drops by > 1/sqrt(2)
-      const int kk = j + 1;
-      double *hd = W.hdev;  // [0..2kk) h, then norms
-      if ((rc = bl.mdot(W.Vb, n, kk, W.w, n, hd, hd + 2 * 80, st))) return rc;
-      if ((rc = bl.maxpy_norm(W.Vb, n, kk, hd, W.w, n, hd + 2 * 80 + 1, st))) return rc;
-      DD_CUDA(cudaMemcpyAsync(bl.hpin, hd, sizeof(double) * (2 * 80 + 2), cudaMemcpyDeviceToHost, st));
-      cudaEventRecord(W.ev[3], st);
-      DD_CUDA(cudaStreamSynchronize(st));
-      std::vector<cd> h(kk);
-      for (int i = 0; i < kk; i++) h[i] = cd(bl.hpin[2 * i], bl.hpin[2 * i + 1]);
-      double w0 = bl.hpin[160], w1 = bl.hpin[161];
-      if (w1 < 0.5 * w0) {
-        if ((rc = bl.mdot(W.Vb, n, kk, W.w, n, hd, nullptr, st))) return rc;
-        if ((rc = bl.maxpy_norm(W.Vb, n, kk, hd, W.w, n, hd + 2 * 80 + 1, st))) return rc;
-        DD_CUDA(cudaMemcpyAsync(bl.hpin, hd, sizeof(double) * (2 * 80 + 2), cudaMemcpyDeviceToHost, st));
-        cudaEventRecord(W.ev[3], st);
-        DD_CUDA(cudaStreamSynchronize(st));
-        for (int i = 0; i < kk; i++) h[i] += cd(bl.hpin[2 * i], bl.hpin[2 * i + 1]);
-        w1 = bl.hpin[161];
-      }
-      ms_sap += ev_ms(W.ev[0], W.ev[1]);
-      ms_dirac += ev_ms(W.ev[1], W.ev[2]);
-      ms_orth += ev_ms(W.ev[2], W.ev[3]);
-      double hn = std::sqrt(std::max(w1, 0.0));
-      for (int i = 0; i < kk; i++) H[(size_t)i * m + j] = h[i];
-      H[(size_t)(j + 1) * m + j] = hn;
-      if (hn > 0 && j + 1 <= m)
-        if ((rc = bl.scale(W.Vb + 2 * n * (j + 1), W.w, 1.0 / hn, n, st))) return rc;
-      // Givens rotations
-      for (int i = 0; i < j; i++) {
-        cd a = H[(size_t)i * m + j], c2 = H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c2;
-        H[(size_t)(i + 1) * m + j] = -std::conj(sn[i]) * a + cs[i] * c2;
-      }
-      cd a = H[(size_t)j * m + j];
-      double bb = hn, rr = std::sqrt(std::norm(a) + bb * bb);
-      if (std::abs(a) == 0) { cs[j] = 0; sn[j] = 1; }
-      else { cs[j] = std::abs(a) / rr; sn[j] = (a / std::abs(a)) * bb / rr; }
-      H[(size_t)j * m + j] = cs[j] * a + sn[j] * bb;
-      H[(size_t)(j + 1) * m + j] = 0;
-      gv[j + 1] = -std::conj(sn[j]) * gv[j];
-      gv[j] = cs[j] * gv[j];
-      k = j + 1;
-      est = std::abs(gv[j + 1]) / bnorm;
-      if (std::abs(gv[j + 1]) <= target || hn == 0) break;
-      if (cancel && *cancel) break;
-    }
-    // y = R^-1 g ; x += Z y
-    for (int i = k - 1; i >= 0; i--) {
-      cd s = gv[i];
-      for (int l = i + 1; l < k; l++) s -= H[(size_t)i * m + l] * y[l];
-      y[i] = s / H[(size_t)i * m + i];
-    }
-    for (int i = 0; i < k; i++) {
-      bl.hpin[2 * i] = y[i].real();
-      bl.hpin[2 * i + 1] = y[i].imag();
-    }
-    DD_CUDA(cudaMemcpyAsync(W.ydev, bl.hpin, sizeof(double) * 2 * k, cudaMemcpyHostToDevice, st));
-    if ((rc = bl.update_x(g, W.x, W.zprec, W.Z, W.zbytes, k, W.ydev, st))) return rc;
-  }
-  DD_CUDA(cudaStreamSynchronize(st));
-  info.status = status;
-  info.iterations = its;
-  info.true_rel_residual = rel;
-  info.est_rel_residual = est;
-  info.ms_sap = ms_sap;
-  info.ms_dirac = ms_dirac;
-  info.ms_orth = ms_orth;
-  info.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  return status == DD_ECANCELLED ? DD_ECANCELLED : DD_OK;
-}
 
 int check_solve_params(const dd_solve_params *p) {
   if (!p || !(p->tol > 0) || p->restart < 1 || p->restart > 64 || p->max_iter < 1 || p->sap.sweeps < 1 ||
-      p->sap.mr_steps < 0 || p->inner_reduction < 0 || p->inner_reduction >= 1) {
-    set_error("dd_solve: bad parameters (tol > 0, 1 <= restart <= 64, max_iter >= 1, sweeps >= 1)");
+      p->sap.mr_steps < 0 || !(p->inner_reduction >= 0) || p->inner_reduction >= 1) {
+    set_error("dd_solve: bad parameters (tol > 0, 1 <= restart <= 64, max_iter >= 1, sweeps >= 1, "
+              "0 <= inner_reduction < 1)");
     return DD_EINVAL;
   }
   return DD_OK;
 }
 
-// Solve for nrhs canonical right-hand sides, one after the other.
-int solve_canonical(const Op *op, const dd_solve_params &p, const double *b, double *x, int nrhs,
-                    dd_solve_info *info, cudaStream_t st, SolveWork &W, const volatile int *cancel) {
+size_t BatchSolver::bytes_per_slot(const Geom &g, int prec, int m) {
+  size_t f64 = (size_t)g.V * 24 * 8;
+  int zprec = prec == DD_F64 ? DD_F64 : DD_F32;
+  size_t fz = (size_t)g.V * 24 * real_bytes(zprec), fp = (size_t)g.V * 24 * real_bytes(prec);
+  return (size_t)(m + 1) * f64 + (size_t)m * fz + 4 * f64 + 2 * fp + fz;
+}
+
+BatchSolver::BatchSolver(const Op *op, const dd_solve_params &p, int slots, cudaStream_t st)
+    : op_(op), p_(p), st_(st), slots_(slots) {
   const Geom &g = op->lat->g;
-  int rc = W.ensure(g, op->prec, p.restart);
-  if (rc) return rc;
-  const size_t fb = (size_t)g.V * 24 * sizeof(double);
-  const cudaMemcpyKind h2d = p.where == DD_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  const cudaMemcpyKind d2h = p.where == DD_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  int all_ok = 1;
-  for (int r = 0; r < nrhs; r++) {
-    dd_solve_info inf{};
-    DD_CUDA(cudaMemcpyAsync(W.canon, b + (size_t)r * g.V * 24, fb, h2d, st));
-    if ((rc = launch_pack(g, DD_F64, W.canon, W.b, 1, 1.0, st))) return rc;
-    if (p.use_x0) {
-      DD_CUDA(cudaMemcpyAsync(W.canon, x + (size_t)r * g.V * 24, fb, h2d, st));
-      if ((rc = launch_pack(g, DD_F64, W.canon, W.x, 1, 1.0, st))) return rc;
-    } else {
-      DD_CUDA(cudaMemsetAsync(W.x, 0, fb, st));
-    }
-    rc = fgmres_one(op, p, W, inf, st, cancel);
-    if (rc && rc != DD_ECANCELLED) return rc;
-    if ((rc = launch_unpack(g, DD_F64, W.x, W.canon, 1, 1.0, st))) return rc;
-    DD_CUDA(cudaMemcpyAsync(x + (size_t)r * g.V * 24, W.canon, fb, d2h, st));
-    DD_CUDA(cudaStreamSynchronize(st));
-    if (info) info[r] = inf;
-    if (inf.status == DD_ECANCELLED) return DD_ECANCELLED;
-    if (inf.status != DD_OK) all_ok = 0;
+  zprec_ = op->prec == DD_F64 ? DD_F64 : DD_F32;
+  // mixed precision keeps the Krylov basis in double-float (FP32 hi/lo pairs):
+  // FP64-class accuracy at FP32 ALU rate; an FP64 operator keeps native FP64
+  df_ = zprec_ == DD_F32;
+  f64_ = (size_t)g.V * 24 * 8;
+  fz_ = (size_t)g.V * 24 * real_bytes(zprec_);
+  fp_ = (size_t)g.V * 24 * real_bytes(op->prec);
+  sigma_ = std::sqrt(24.0 * (double)g.V);  // unit-norm vector -> unit RMS entries
+}
+
+BatchSolver::~BatchSolver() {
+  for (auto &s : slots_) {
+    void *ptrs[] = {s.Vb, s.Z, s.x, s.b, s.w, s.canon, s.tin, s.tout, s.zt};
+    for (void *q : ptrs)
+      if (q) cudaFree(q);
   }
-  if (!all_ok) {
-    set_error("dd_solve: max_iter reached before the target residual");
-    return DD_ENOTCONV;
+  if (hdev_) cudaFree(hdev_);
+  if (ydev_) cudaFree(ydev_);
+  if (hpin_) cudaFreeHost(hpin_);
+  if (ypin_) cudaFreeHost(ypin_);
+  for (auto &e : ev_)
+    if (e) cudaEventDestroy(e);
+}
+
+int BatchSolver::init() {
+  const int m = p_.restart, n = (int)slots_.size();
+  if (n < 1 || n > MAX_RHS) {
+    set_error("solver: 1..%d slots", MAX_RHS);
+    return DD_EINVAL;
+  }
+  for (auto &s : slots_) {
+    bool ok = cudaMalloc((void **)&s.Vb, (size_t)(m + 1) * f64_) == cudaSuccess &&
+              cudaMalloc((void **)&s.Z, (size_t)m * fz_) == cudaSuccess &&
+              cudaMalloc((void **)&s.x, f64_) == cudaSuccess && cudaMalloc((void **)&s.b, f64_) == cudaSuccess &&
+              cudaMalloc((void **)&s.w, f64_) == cudaSuccess && cudaMalloc((void **)&s.canon, f64_) == cudaSuccess &&
+              cudaMalloc(&s.tin, fp_) == cudaSuccess && cudaMalloc(&s.tout, fp_) == cudaSuccess &&
+              cudaMalloc(&s.zt, fz_) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      set_error("solver: out of device memory for %d FGMRES(%d) slots (%zu bytes each)", n, m,
+                bytes_per_slot(op_->lat->g, op_->prec, m));
+      return DD_ENOMEM;
+    }
+    s.H.assign((size_t)(m + 1) * m, 0);
+    s.g.assign(m + 1, 0);
+    s.sn.assign(m, 0);
+    s.y.assign(m, 0);
+    s.cs.assign(m, 0);
+  }
+  DD_CUDA(cudaMalloc((void **)&hdev_, sizeof(double) * HSTRIDE * n));
+  DD_CUDA(cudaMalloc((void **)&ydev_, sizeof(double) * 2 * 64 * n));
+  DD_CUDA(cudaMallocHost((void **)&hpin_, sizeof(double) * HSTRIDE * n));
+  DD_CUDA(cudaMallocHost((void **)&ypin_, sizeof(double) * 2 * 64 * n));
+  for (auto &e : ev_) DD_CUDA(cudaEventCreate(&e));
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return blas_.init(sms);
+}
+
+int BatchSolver::sync_h() {
+  DD_CUDA(cudaMemcpyAsync(hpin_, hdev_, sizeof(double) * HSTRIDE * slots_.size(), cudaMemcpyDeviceToHost, st_));
+  return cuda_fail(cudaStreamSynchronize(st_), "solver sync");
+}
+
+// Load a job into a slot: b and x0 into the FP64 field layout.
+int BatchSolver::start(Slot &s) {
+  const Geom &g = op_->lat->g;
+  int rc;
+  s.busy = true;
+  s.need_restart = true;
+  s.j = s.its = s.cycles = 0;
+  s.bnorm = -1;
+  s.rel = s.est = 1;
+  s.ms_sap = s.ms_dirac = s.ms_orth = 0;
+  s.t0 = std::chrono::steady_clock::now();
+  DD_CUDA(cudaMemcpyAsync(s.canon, s.job.b, f64_, s.job.b_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          st_));
+  if ((rc = launch_pack(g, DD_F64, s.canon, s.b, 1, 1.0, st_))) return rc;
+  if (s.job.use_x0) {
+    DD_CUDA(cudaMemcpyAsync(s.canon, s.job.x, f64_,
+                            s.job.x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st_));
+    if ((rc = launch_pack(g, DD_F64, s.canon, s.x, 1, 1.0, st_))) return rc;
+  } else {
+    DD_CUDA(cudaMemsetAsync(s.x, 0, f64_, st_));
   }
   return DD_OK;
+}
+
+int BatchSolver::retire(Slot &s, int status) {
+  const Geom &g = op_->lat->g;
+  int rc;
+  if ((rc = launch_unpack(g, DD_F64, s.x, s.canon, 1, 1.0, st_))) return rc;
+  DD_CUDA(cudaMemcpyAsync(s.job.x, s.canon, f64_, s.job.x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          st_));
+  DD_CUDA(cudaStreamSynchronize(st_));
+  if (s.job.info) {
+    dd_solve_info &inf = *s.job.info;
+    inf.status = status;
+    inf.iterations = s.its;
+    inf.cycles = s.cycles;
+    inf.true_rel_residual = s.rel;
+    inf.est_rel_residual = s.est;
+    inf.ms_sap = s.ms_sap;
+    inf.ms_dirac = s.ms_dirac;
+    inf.ms_orth = s.ms_orth;
+    inf.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - s.t0).count();
+  }
+  if (status != DD_OK) failed_ = 1;
+  s.busy = false;
+  if (s.job.done) s.job.done(status);
+  return DD_OK;
+}
+
+// True residual r = b - D x (FP64) for the slots in R; retire or begin a cycle.
+int BatchSolver::restart_phase(std::vector<Slot *> &R) {
+  const Geom &g = op_->lat->g;
+  const size_t n = (size_t)g.V * 12;
+  int rc;
+  RhsPtrs rp;
+  rp.n = (int)R.size();
+  for (int i = 0; i < rp.n; i++) {
+    rp.in[i] = R[i]->x;
+    rp.out[i] = R[i]->w;
+  }
+  cudaEventRecord(ev_[0], st_);
+  if ((rc = launch_dirac(g, op_->f64, rp, st_))) return rc;
+  for (Slot *s : R) {
+    double *hd = hdev_ + HSTRIDE * (s - slots_.data());
+    if ((rc = blas_.xmy(s->b, s->w, n, st_))) return rc;
+    if ((rc = blas_.norm2(s->w, n, hd + RN, st_))) return rc;
+    if (s->bnorm < 0 && (rc = blas_.norm2(s->b, n, hd + BN, st_))) return rc;
+  }
+  cudaEventRecord(ev_[1], st_);
+  if ((rc = sync_h())) return rc;
+  float ms = ev_ms(ev_[0], ev_[1]);
+  for (Slot *s : R) {
+    const double *hp = hpin_ + HSTRIDE * (s - slots_.data());
+    s->ms_dirac += ms;
+    if (s->bnorm < 0) s->bnorm = std::sqrt(hp[BN]);
+    s->beta = std::sqrt(hp[RN]);
+    s->rel = s->bnorm > 0 ? s->beta / s->bnorm : 0.0;
+    if (s->bnorm == 0) {
+      DD_CUDA(cudaMemsetAsync(s->x, 0, f64_, st_));
+      s->est = 0;
+      if ((rc = retire(*s, DD_OK))) return rc;
+      continue;
+    }
+    if (!std::isfinite(s->rel)) {
+      if ((rc = retire(*s, DD_ENOTCONV))) return rc;
+      continue;
+    }
+    if (s->rel <= p_.tol) {
+      s->est = s->rel;
+      if ((rc = retire(*s, DD_OK))) return rc;
+      continue;
+    }
+    if (s->job.cancel && *s->job.cancel) {
+      if ((rc = retire(*s, DD_ECANCELLED))) return rc;
+      continue;
+    }
+    if (s->its >= p_.max_iter) {
+      if ((rc = retire(*s, DD_ENOTCONV))) return rc;
+      continue;
+    }
+    s->cycles++;
+    s->need_restart = false;
+    s->j = 0;
+    std::fill(s->g.begin(), s->g.end(), cd(0));
+    s->g[0] = s->beta;
+    s->target = std::max(p_.tol * s->bnorm, p_.inner_reduction * s->beta);
+    if (df_) rc = blas_.f64_to_df((float *)s->Vb, s->w, 1.0 / s->beta, n, st_);
+    else rc = blas_.scale(s->Vb, s->w, 1.0 / s->beta, n, st_);
+    if (rc) return rc;
+  }
+  return DD_OK;
+}
+
+int BatchSolver::end_cycle(Slot &s) {
+  const Geom &g = op_->lat->g;
+  const int m = p_.restart, k = s.j + 1;
+  for (int i = k - 1; i >= 0; i--) {
+    cd t = s.g[i];
+    for (int l = i + 1; l < k; l++) t -= s.H[(size_t)i * m + l] * s.y[l];
+    s.y[i] = t / s.H[(size_t)i * m + i];
+  }
+  const int idx = (int)(&s - slots_.data());
+  double *yp = ypin_ + 2 * 64 * idx;
+  double *yd = ydev_ + 2 * 64 * idx;
+  for (int i = 0; i < k; i++) {
+    yp[2 * i] = s.y[i].real();
+    yp[2 * i + 1] = s.y[i].imag();
+  }
+  DD_CUDA(cudaMemcpyAsync(yd, yp, sizeof(double) * 2 * k, cudaMemcpyHostToDevice, st_));
+  int rc = blas_.update_x(g, s.x, zprec_, s.Z, fz_, k, yd, st_);
+  s.need_restart = true;
+  return rc;
+}
+
+int BatchSolver::mdot(Slot *s, int kk, double *h, double *wn2) {
+  const size_t n = (size_t)op_->lat->g.V * 12;
+  if (df_) return blas_.df_mdot((const float *)s->Vb, n, kk, (const float *)s->w, n, h, wn2, st_);
+  return blas_.mdot(s->Vb, n, kk, s->w, n, h, wn2, st_);
+}
+
+int BatchSolver::maxpy(Slot *s, int kk, const double *h, double *wn2) {
+  const size_t n = (size_t)op_->lat->g.V * 12;
+  if (df_) return blas_.df_maxpy_norm((const float *)s->Vb, n, kk, h, (float *)s->w, n, wn2, st_);
+  return blas_.maxpy_norm(s->Vb, n, kk, h, s->w, n, wn2, st_);
+}
+
+// One preconditioned Arnoldi step for every slot in A.
+int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
+  const Geom &g = op_->lat->g;
+  const size_t n = (size_t)g.V * 12;
+  const int m = p_.restart;
+  int rc;
+  // z_j = SAP(v_j): pack with scale sigma, smooth, keep z_j / sigma in zprec
+  cudaEventRecord(ev_[0], st_);
+  RhsPtrs sp_ptrs, d_ptrs;
+  sp_ptrs.n = d_ptrs.n = (int)A.size();
+  for (int i = 0; i < (int)A.size(); i++) {
+    Slot *s = A[i];
+    if (df_) rc = blas_.df_to_field(g, (const float *)(s->Vb + 2 * n * s->j), op_->prec, s->tin, sigma_, st_);
+    else rc = launch_convert_field(g, DD_F64, s->Vb + 2 * n * s->j, op_->prec, s->tin, 1, sigma_, st_);
+    if (rc) return rc;
+    sp_ptrs.in[i] = s->tin;
+    sp_ptrs.out[i] = s->tout;
+  }
+  dd_sap_params sp = p_.sap;
+  sp.x_is_zero = 1;
+  if ((rc = launch_sap(g, op_->fp, sp, sp_ptrs, st_))) return rc;
+  for (int i = 0; i < (int)A.size(); i++) {
+    Slot *s = A[i];
+    char *zj = s->Z + (size_t)s->j * fz_;
+    if ((rc = launch_convert_field(g, op_->prec, s->tout, zprec_, zj, 1, 1.0 / sigma_, st_))) return rc;
+    d_ptrs.in[i] = zj;
+    d_ptrs.out[i] = zprec_ == DD_F64 ? (void *)s->w : s->zt;
+  }
+  cudaEventRecord(ev_[1], st_);
+  // w = D z_j in zprec
+  if ((rc = launch_dirac(g, zprec_ == DD_F64 ? op_->f64 : op_->f32, d_ptrs, st_))) return rc;
+  if (zprec_ != DD_F64)
+    for (Slot *s : A)
+      if ((rc = blas_.field_to_df(g, DD_F32, s->zt, (float *)s->w, st_))) return rc;
+  cudaEventRecord(ev_[2], st_);
+  // classical Gram-Schmidt, repeated once for slots whose norm drops by more than 1/sqrt(2)
+  for (Slot *s : A) {
+    double *hd = hdev_ + HSTRIDE * (s - slots_.data());
+    const int kk = s->j + 1;
+    if ((rc = mdot(s, kk, hd, hd + W0))) return rc;
+    if ((rc = maxpy(s, kk, hd, hd + W1))) return rc;
+  }
+  if ((rc = sync_h())) return rc;
+  std::vector<std::vector<cd>> hcol(A.size());
+  std::vector<Slot *> again;
+  for (size_t i = 0; i < A.size(); i++) {
+    Slot *s = A[i];
+    const double *hp = hpin_ + HSTRIDE * (s - slots_.data());
+    hcol[i].resize(s->j + 1);
+    for (int q = 0; q <= s->j; q++) hcol[i][q] = cd(hp[2 * q], hp[2 * q + 1]);
+    if (hp[W1] < 0.5 * hp[W0]) again.push_back(s);
+  }
+  if (!again.empty()) {
+    for (Slot *s : again) {
+      double *hd = hdev_ + HSTRIDE * (s - slots_.data());
+      const int kk = s->j + 1;
+      if ((rc = mdot(s, kk, hd, nullptr))) return rc;
+      if ((rc = maxpy(s, kk, hd, hd + W1))) return rc;
+    }
+    if ((rc = sync_h())) return rc;
+    for (size_t i = 0; i < A.size(); i++) {
+      Slot *s = A[i];
+      bool re = false;
+      for (Slot *t : again) re |= t == s;
+      if (!re) continue;
+      const double *hp = hpin_ + HSTRIDE * (s - slots_.data());
+      for (int q = 0; q <= s->j; q++) hcol[i][q] += cd(hp[2 * q], hp[2 * q + 1]);
+    }
+  }
+  cudaEventRecord(ev_[3], st_);
+  cudaEventSynchronize(ev_[3]);
+  const float t_sap = ev_ms(ev_[0], ev_[1]), t_d = ev_ms(ev_[1], ev_[2]), t_o = ev_ms(ev_[2], ev_[3]);
+  for (size_t i = 0; i < A.size(); i++) {
+    Slot &s = *A[i];
+    const double *hp = hpin_ + HSTRIDE * (&s - slots_.data());
+    s.ms_sap += t_sap;
+    s.ms_dirac += t_d;
+    s.ms_orth += t_o;
+    s.its++;
+    const int j = s.j;
+    const double hn = std::sqrt(std::max(hp[W1], 0.0));
+    for (int q = 0; q <= j; q++) s.H[(size_t)q * m + j] = hcol[i][q];
+    if (hn > 0) {
+      if (df_) rc = blas_.df_scale((float *)(s.Vb + 2 * n * (j + 1)), (const float *)s.w, 1.0 / hn, n, st_);
+      else rc = blas_.scale(s.Vb + 2 * n * (j + 1), s.w, 1.0 / hn, n, st_);
+      if (rc) return rc;
+    }
+    for (int q = 0; q < j; q++) {
+      cd a = s.H[(size_t)q * m + j], c2 = s.H[(size_t)(q + 1) * m + j];
+      s.H[(size_t)q * m + j] = s.cs[q] * a + s.sn[q] * c2;
+      s.H[(size_t)(q + 1) * m + j] = -std::conj(s.sn[q]) * a + s.cs[q] * c2;
+    }
+    cd a = s.H[(size_t)j * m + j];
+    double rr = std::sqrt(std::norm(a) + hn * hn);
+    if (std::abs(a) == 0) {
+      s.cs[j] = 0;
+      s.sn[j] = 1;
+    } else {
+      s.cs[j] = std::abs(a) / rr;
+      s.sn[j] = (a / std::abs(a)) * hn / rr;
+    }
+    s.H[(size_t)j * m + j] = s.cs[j] * a + s.sn[j] * hn;
+    s.g[j + 1] = -std::conj(s.sn[j]) * s.g[j];
+    s.g[j] = s.cs[j] * s.g[j];
+    s.est = std::abs(s.g[j + 1]) / s.bnorm;
+    bool cancel = s.job.cancel && *s.job.cancel;
+    if (std::abs(s.g[j + 1]) <= s.target || j + 1 == m || s.its >= p_.max_iter || hn == 0 || cancel) {
+      if ((rc = end_cycle(s))) return rc;
+    } else {
+      s.j++;
+    }
+  }
+  return DD_OK;
+}
+
+int BatchSolver::run(const std::function<bool(RhsJob &)> &next) {
+  failed_ = 0;
+  bool more = true;
+  int rc;
+  for (;;) {
+    for (auto &s : slots_) {
+      if (s.busy || !more) continue;
+      RhsJob job;
+      if (!next(job)) {
+        more = false;
+        break;
+      }
+      s.job = job;
+      if ((rc = start(s))) return rc;
+    }
+    std::vector<Slot *> R, A;
+    for (auto &s : slots_)
+      if (s.busy && s.need_restart) R.push_back(&s);
+    if (!R.empty() && (rc = restart_phase(R))) return rc;
+    for (auto &s : slots_)
+      if (s.busy && !s.need_restart) A.push_back(&s);
+    if (A.empty()) {
+      bool any = false;
+      for (auto &s : slots_) any |= s.busy;
+      if (!any && !more) break;
+      continue;
+    }
+    if ((rc = arnoldi_step(A))) return rc;
+  }
+  return failed_ ? DD_ENOTCONV : DD_OK;
 }
 
 }  // namespace dd
@@ -296,6 +425,27 @@ extern "C" int dd_solve(dd_op_t opp, const dd_solve_params *p, const double *b, 
   }
   int rc = check_solve_params(p);
   if (rc) return rc;
-  SolveWork W;
-  return solve_canonical(op, *p, b, x, nrhs, info, (cudaStream_t)stream, W, nullptr);
+  const Geom &g = op->lat->g;
+  // as many slots as right-hand sides, bounded by free device memory
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  size_t per = BatchSolver::bytes_per_slot(g, op->prec, p->restart);
+  int slots = nrhs < MAX_RHS ? nrhs : MAX_RHS;
+  while (slots > 1 && (size_t)slots * per > free_b / 10 * 9) slots--;
+  BatchSolver bs(op, *p, slots, (cudaStream_t)stream);
+  if ((rc = bs.init())) return rc;
+  int next = 0;
+  std::vector<dd_solve_info> tmp(nrhs);
+  rc = bs.run([&](RhsJob &j) {
+    if (next >= nrhs) return false;
+    j.b = b + (size_t)next * g.V * 24;
+    j.x = x + (size_t)next * g.V * 24;
+    j.b_on_device = j.x_on_device = p->where == DD_DEVICE;
+    j.use_x0 = p->use_x0;
+    j.info = info ? info + next : &tmp[next];
+    next++;
+    return true;
+  });
+  if (rc == DD_ENOTCONV) set_error("dd_solve: max_iter reached before the target residual");
+  return rc;
 }

@@ -1,31 +1,91 @@
 // Outer FGMRES solver internals (see dd_solver.cu).
 #pragma once
+#include <chrono>
+#include <complex>
+#include <functional>
+#include <vector>
+
 #include "dd_blas.cuh"
 
 namespace dd {
 
-// Device workspace of one FGMRES(m) solve on one lattice.
-struct SolveWork {
-  int prec = -1, zprec = -1, m = 0;
-  long long V = 0;
-  size_t zbytes = 0, pbytes = 0, bytes = 0;
-  double *Vb = nullptr;            // (m+1) FP64 basis fields
-  void *Z = nullptr;               // m preconditioned fields (zprec)
-  double *w = nullptr, *r = nullptr, *x = nullptr, *b = nullptr, *tmp = nullptr, *canon = nullptr;
-  void *tin = nullptr, *tout = nullptr, *zt = nullptr;
-  double *hdev = nullptr, *ydev = nullptr;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  Blas blas;
-  ~SolveWork();
-  void release();
-  int ensure(const Geom &g, int prec, int m);
-  static size_t bytes_needed(const Geom &g, int prec, int m);
+// One right-hand side to solve.
+struct RhsJob {
+  const double *b = nullptr;  // canonical FP64 right-hand side [V][4][3][2]
+  int b_on_device = 0;
+  double *x = nullptr;        // canonical FP64 solution (initial guess if use_x0)
+  int x_on_device = 0;
+  int use_x0 = 0;
+  dd_solve_info *info = nullptr;      // result record (may be null)
+  const volatile int *cancel = nullptr;
+  std::function<void(int status)> done;  // called after x and info are written
 };
 
+// Device buffers and FGMRES state of one batch slot.
+struct Slot {
+  bool busy = false, need_restart = true;
+  RhsJob job;
+  int j = 0, its = 0, cycles = 0;
+  double bnorm = -1, beta = 0, rel = 1, est = 1, target = 0;
+  std::vector<std::complex<double>> H, g, sn, y;
+  std::vector<double> cs;
+  double ms_sap = 0, ms_dirac = 0, ms_orth = 0;
+  std::chrono::steady_clock::time_point t0;
+  // device memory
+  double *Vb = nullptr;  // (m+1) basis fields: FP64, or double-float (float4 per complex)
+  char *Z = nullptr;     // m preconditioned fields (zprec)
+  double *x = nullptr, *b = nullptr, *w = nullptr, *canon = nullptr;
+  void *tin = nullptr, *tout = nullptr, *zt = nullptr;
+};
+
+// FGMRES(m) right-preconditioned by SAP over a batch of right-hand sides that
+// share one operator: the slots' Schwarz sweeps and Dslash products run as
+// single batched launches, orthogonalisation and Givens rotations per slot.
+// Slots retire when their right-hand side converges and are refilled from
+// the job source at the next Arnoldi step (continuous batching).
+class BatchSolver {
+ public:
+  BatchSolver(const Op *op, const dd_solve_params &p, int slots, cudaStream_t st);
+  ~BatchSolver();
+  int init();
+  // Device bytes one slot needs for this lattice, precision and restart.
+  static size_t bytes_per_slot(const Geom &g, int prec, int m);
+  // Solve jobs until next() returns false and every slot has retired.
+  int run(const std::function<bool(RhsJob &)> &next);
+  int nslots() const { return (int)slots_.size(); }
+  const Op *op() const { return op_; }
+  const dd_solve_params &params() const { return p_; }
+  void set_params(const dd_solve_params &p) { p_ = p; }
+
+ private:
+  int start(Slot &s);
+  int restart_phase(std::vector<Slot *> &R);
+  int arnoldi_step(std::vector<Slot *> &A);
+  int end_cycle(Slot &s);
+  int retire(Slot &s, int status);
+  int sync_h();
+  int mdot(Slot *s, int kk, double *h, double *wn2);
+  int maxpy(Slot *s, int kk, const double *h, double *wn2);
+
+  const Op *op_;
+  dd_solve_params p_;
+  cudaStream_t st_;
+  std::vector<Slot> slots_;
+  int zprec_;
+  bool df_;  // Krylov basis and w in double-float
+  size_t f64_, fz_, fp_;
+  double sigma_;
+  Blas blas_;
+  double *hdev_ = nullptr;   // [slots][HSTRIDE]
+  double *hpin_ = nullptr;   // pinned mirror [slots][HSTRIDE]
+  double *ydev_ = nullptr;   // [slots][2*64]
+  double *ypin_ = nullptr;
+  cudaEvent_t ev_[4] = {};
+  int failed_ = 0;
+};
+
+constexpr int HSTRIDE = 2 * 65 + 6;  // h column (complex) + norms
+
 int check_solve_params(const dd_solve_params *p);
-int fgmres_one(const Op *op, const dd_solve_params &p, SolveWork &W, dd_solve_info &info, cudaStream_t st,
-               const volatile int *cancel);
-int solve_canonical(const Op *op, const dd_solve_params &p, const double *b, double *x, int nrhs,
-                    dd_solve_info *info, cudaStream_t st, SolveWork &W, const volatile int *cancel);
 
 }  // namespace dd
