@@ -186,6 +186,32 @@ typedef struct {
 int dd_solve(dd_op_t op, const dd_solve_params *p, const double *b, double *x, int nrhs,
              dd_solve_info *info, void *stream);
 
+/* Size of the fixed device scratch array behind dd_solve_noalloc: 64 MiB. */
+#define DD_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* Solve D x = b for ONE right-hand side without allocating any memory.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device (or pinned host) memory at solve time - for example
+ * code running where cudaMalloc is forbidden or would disturb a fixed memory
+ * plan. It runs the same SAP-preconditioned FGMRES as dd_solve, with the
+ * whole workspace taken from one file-scope device array of
+ * DD_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * process exit. b_dev and x_dev are canonical FP64 spinors in DEVICE memory
+ * ([V][4][3][2]); x_dev receives the solution (and holds the initial guess if
+ * p->use_x0; p->where is ignored). info may be NULL.
+ * Limits and rules: returns DD_EINVAL, before doing any work, when the
+ * lattice and restart length need more scratch than the array holds (about
+ * 6 kB per site at restart 16 with an FP32 smoother, so lattices up to
+ * roughly 10^4 sites); all calls in the process share the array, so calls
+ * whose GPU work overlaps (other streams, threads or concurrent calls) race
+ * and must be serialised by the caller; the array keeps the previous call's
+ * contents, and each call clears what it needs zeroed itself. The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture
+ * on the device. Synchronous with respect to the host; work runs on `stream`. */
+int dd_solve_noalloc(dd_op_t op, const dd_solve_params *p, const double *b_dev, double *x_dev,
+                     dd_solve_info *info, void *stream);
+
 /* ------------------------------------------------------------ serving */
 
 typedef struct {

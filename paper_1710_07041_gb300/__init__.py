@@ -93,6 +93,8 @@ EXPORTS = {
                        ctypes.c_void_p], ctypes.c_int),
     "dd_solve": ([ctypes.c_void_p, ctypes.POINTER(SolveParams), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                   ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "dd_solve_noalloc": ([ctypes.c_void_p, ctypes.POINTER(SolveParams), ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "dd_server_create": ([ctypes.POINTER(ServerParams), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "dd_submit": ([ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "dd_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
@@ -269,6 +271,30 @@ class Op(Handle):
         if rc != 0 and not (rc == -4 and not raise_on_notconv):
             _check(rc, "dd_solve")
         return x, [i.as_dict() for i in infos]
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def solve_noalloc(op: "Op", b_dev, x_dev, tol=1e-10, restart=16, max_iter=1000, sweeps=4, mr_steps=4,
+                  inner_reduction=None, use_x0=False, stream=None):
+    """dd_solve_noalloc: one right-hand side, device buffers, no allocation.
+    b_dev and x_dev are contiguous CUDA float64/complex128 tensors holding one
+    canonical spinor field each. Returns the solve record as a dict."""
+    b_dev = _as_canonical(b_dev, op.lat.V)
+    x_dev = _as_canonical(x_dev, op.lat.V)
+    if isinstance(b_dev, np.ndarray) or isinstance(x_dev, np.ndarray):
+        raise TypeError("solve_noalloc takes device tensors")
+    if _count_rhs(b_dev, op.lat.V) != 1 or _count_rhs(x_dev, op.lat.V) != 1:
+        raise ValueError("solve_noalloc solves exactly one right-hand side")
+    if inner_reduction is None:
+        inner_reduction = 0.0 if op.prec == F64 else 1e-5
+    p = SolveParams(tol, restart, max_iter, SapParams(sweeps, mr_steps, 1, 0), inner_reduction, DEVICE,
+                    int(bool(use_x0)))
+    info = SolveInfo()
+    _check(lib().dd_solve_noalloc(op.handle, ctypes.byref(p), _ptr(b_dev), _ptr(x_dev), ctypes.byref(info),
+                                  _stream_ptr(stream)), "dd_solve_noalloc")
+    return info.as_dict()
 
 
 def _as_canonical(a, V: int):
