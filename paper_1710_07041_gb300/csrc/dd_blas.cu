@@ -193,7 +193,8 @@ __device__ __forceinline__ void block_reduce_df(df *v, double *smem, double *out
   }
 }
 
-// partial[blk] = this block's sums of conj(V_i) w (i < k) and |w|^2, as doubles
+// partial[blk] = this block's sums of conj(V_i) w (i < k) and |w|^2, as doubles.
+// Two elements per thread and iteration keep more loads in flight.
 template <int KMAX>
 __global__ void __launch_bounds__(RED_TPB) k_df_mdot(const float4 *__restrict__ V, size_t ldv, int k,
                                                      const float4 *__restrict__ w, size_t n, double *partial) {
@@ -201,19 +202,34 @@ __global__ void __launch_bounds__(RED_TPB) k_df_mdot(const float4 *__restrict__ 
   df acc[2 * KMAX + 1];
 #pragma unroll
   for (int i = 0; i < 2 * KMAX + 1; i++) acc[i] = {0.f, 0.f};
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    float4 we = w[e];
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += 2 * stride) {
+    const size_t e2 = e + stride;
+    const bool two = e2 < n;
+    float4 we = w[e], we2 = two ? w[e2] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 v[KMAX], v2[KMAX];
+#pragma unroll
+    for (int i = 0; i < KMAX; i++)
+      if (i < k) {
+        v[i] = V[i * ldv + e];
+        v2[i] = two ? V[i * ldv + e2] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     df_mac(acc[2 * KMAX], we.x, we.z, we.x, we.z);
     df_mac(acc[2 * KMAX], we.y, we.w, we.y, we.w);
+    df_mac(acc[2 * KMAX], we2.x, we2.z, we2.x, we2.z);
+    df_mac(acc[2 * KMAX], we2.y, we2.w, we2.y, we2.w);
 #pragma unroll
     for (int i = 0; i < KMAX; i++) {
       if (i < k) {
-        float4 v = V[i * ldv + e];
         // re += vr wr + vi wi ; im += vr wi - vi wr
-        df_mac(acc[2 * i], v.x, v.z, we.x, we.z);
-        df_mac(acc[2 * i], v.y, v.w, we.y, we.w);
-        df_mac(acc[2 * i + 1], v.x, v.z, we.y, we.w);
-        df_msub(acc[2 * i + 1], v.y, v.w, we.x, we.z);
+        df_mac(acc[2 * i], v[i].x, v[i].z, we.x, we.z);
+        df_mac(acc[2 * i], v[i].y, v[i].w, we.y, we.w);
+        df_mac(acc[2 * i + 1], v[i].x, v[i].z, we.y, we.w);
+        df_msub(acc[2 * i + 1], v[i].y, v[i].w, we.x, we.z);
+        df_mac(acc[2 * i], v2[i].x, v2[i].z, we2.x, we2.z);
+        df_mac(acc[2 * i], v2[i].y, v2[i].w, we2.y, we2.w);
+        df_mac(acc[2 * i + 1], v2[i].x, v2[i].z, we2.y, we2.w);
+        df_msub(acc[2 * i + 1], v2[i].y, v2[i].w, we2.x, we2.z);
       }
     }
   }
@@ -234,18 +250,32 @@ __global__ void __launch_bounds__(RED_TPB) k_df_maxpy_norm(const float4 *__restr
   }
   __syncthreads();
   df nrm = {0.f, 0.f};
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    float4 we = w[e];
-    df re = {we.x, we.z}, im = {we.y, we.w};
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += 2 * stride) {
+    const size_t e2 = e + stride;
+    const bool two = e2 < n;
+    float4 we = w[e], we2 = two ? w[e2] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 v[KMAX], v2[KMAX];
+#pragma unroll
+    for (int i = 0; i < KMAX; i++)
+      if (i < k) {
+        v[i] = V[i * ldv + e];
+        v2[i] = two ? V[i * ldv + e2] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    df re = {we.x, we.z}, im = {we.y, we.w}, re2 = {we2.x, we2.z}, im2 = {we2.y, we2.w};
 #pragma unroll
     for (int i = 0; i < KMAX; i++) {
       if (i < k) {
-        float4 v = V[i * ldv + e], c = hs[i];
+        const float4 c = hs[i];
         // w -= c v : re -= cr vr - ci vi ; im -= cr vi + ci vr
-        df_msub(re, c.x, c.z, v.x, v.z);
-        df_mac(re, c.y, c.w, v.y, v.w);
-        df_msub(im, c.x, c.z, v.y, v.w);
-        df_msub(im, c.y, c.w, v.x, v.z);
+        df_msub(re, c.x, c.z, v[i].x, v[i].z);
+        df_mac(re, c.y, c.w, v[i].y, v[i].w);
+        df_msub(im, c.x, c.z, v[i].y, v[i].w);
+        df_msub(im, c.y, c.w, v[i].x, v[i].z);
+        df_msub(re2, c.x, c.z, v2[i].x, v2[i].z);
+        df_mac(re2, c.y, c.w, v2[i].y, v2[i].w);
+        df_msub(im2, c.x, c.z, v2[i].y, v2[i].w);
+        df_msub(im2, c.y, c.w, v2[i].x, v2[i].z);
       }
     }
     re = df_norm(re.h, re.l);
@@ -253,6 +283,13 @@ __global__ void __launch_bounds__(RED_TPB) k_df_maxpy_norm(const float4 *__restr
     w[e] = make_float4(re.h, im.h, re.l, im.l);
     df_mac(nrm, re.h, re.l, re.h, re.l);
     df_mac(nrm, im.h, im.l, im.h, im.l);
+    if (two) {
+      re2 = df_norm(re2.h, re2.l);
+      im2 = df_norm(im2.h, im2.l);
+      w[e2] = make_float4(re2.h, im2.h, re2.l, im2.l);
+      df_mac(nrm, re2.h, re2.l, re2.h, re2.l);
+      df_mac(nrm, im2.h, im2.l, im2.h, im2.l);
+    }
   }
   block_reduce_df<1>(&nrm, smem, partial + blockIdx.x);
 }
@@ -386,15 +423,15 @@ int Blas::xmy(const double *x, double *y, size_t n, cudaStream_t st) {
 
 int Blas::df_mdot(const float *V, size_t ldv, int k, const float *w, size_t n, double *h_dev, double *wnorm2_dev,
                   cudaStream_t st) {
-  for (int i0 = 0; i0 < k || (k == 0 && i0 == 0); i0 += 16) {
-    int kk = k - i0 < 16 ? k - i0 : 16;
+  for (int i0 = 0; i0 < k || (k == 0 && i0 == 0); i0 += 8) {
+    int kk = k - i0 < 8 ? k - i0 : 8;
     if (kk < 0) kk = 0;
     const float4 *Vi = (const float4 *)V + (size_t)i0 * ldv;
     if (kk <= 4)
       k_df_mdot<4><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, (const float4 *)w, n, partial);
     else
-      k_df_mdot<16><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, (const float4 *)w, n, partial);
-    int stride = kk <= 4 ? 9 : 33;
+      k_df_mdot<8><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, (const float4 *)w, n, partial);
+    int stride = kk <= 4 ? 9 : 17;
     DD_LAUNCHED();
     k_sum_partials<<<1, 64, 0, st>>>(partial, nblk, stride, stride, result);
     DD_LAUNCHED();
@@ -409,14 +446,14 @@ int Blas::df_mdot(const float *V, size_t ldv, int k, const float *w, size_t n, d
 int Blas::df_maxpy_norm(const float *V, size_t ldv, int k, const double *h_dev, float *w, size_t n, double *norm2_dev,
                         cudaStream_t st) {
   if (k == 0) return df_mdot(V, ldv, 0, w, n, nullptr, norm2_dev, st);
-  for (int i0 = 0; i0 < k; i0 += 16) {
-    int kk = k - i0 < 16 ? k - i0 : 16;
+  for (int i0 = 0; i0 < k; i0 += 8) {
+    int kk = k - i0 < 8 ? k - i0 : 8;
     const float4 *Vi = (const float4 *)V + (size_t)i0 * ldv;
     const double2 *hi = (const double2 *)h_dev + i0;
     if (kk <= 4)
       k_df_maxpy_norm<4><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial);
     else
-      k_df_maxpy_norm<16><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial);
+      k_df_maxpy_norm<8><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial);
     DD_LAUNCHED();
   }
   k_sum_partials<<<1, 32, 0, st>>>(partial, nblk, 1, 1, norm2_dev);

@@ -6,12 +6,11 @@
 // threads of one site share its link and clover loads in L1. The kernel is
 // HBM-bound: per site it moves 24 (in) + 24 (out) + 72 (links) + 72 (clover)
 // reals once, neighbour spinors being re-read from L1/L2.
-#include "dd_internal.cuh"
+#include "dd_tune.cuh"
 
 namespace dd {
 namespace {
 
-constexpr int DIRAC_TPB = 128;
 
 template <int MU, typename S, typename C>
 __device__ __forceinline__ void dirac_dir(const Geom &g, const Site &t, const void *links, const void *in,
@@ -31,8 +30,10 @@ __device__ __forceinline__ void dirac_dir(const Geom &g, const Site &t, const vo
   hop<MU, false>(acc, u, psi, (C)(-0.5f * sg));
 }
 
-template <typename S>
-__global__ void __launch_bounds__(DIRAC_TPB) k_dirac(Geom g, const void *__restrict__ links,
+// TPB threads per CTA; MINB resident CTAs per SM requested from the compiler
+// (caps registers so more warps keep loads in flight).
+template <typename S, int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_dirac(Geom g, const void *__restrict__ links,
                                                      const void *__restrict__ clov, const RhsPtrs p) {
   using C = typename Store<S>::comp_t;
   const int nrhs = p.n;
@@ -53,11 +54,33 @@ __global__ void __launch_bounds__(DIRAC_TPB) k_dirac(Geom g, const void *__restr
   store_spinor<S, C>(p.out[r], g, b, s, acc);
 }
 
+template <typename S, int TPB, int MINB>
+int dirac_v(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st) {
+  long long n = g.V * p.n;
+  k_dirac<S, TPB, MINB><<<(unsigned)((n + TPB - 1) / TPB), TPB, 0, st>>>(g, f.links, f.clov, p);
+  return launched("k_dirac");
+}
+
+// Launch variants (threads per CTA, CTAs per SM the register budget must
+// allow): (128, 5) ~100 registers, (128, 6) ~80, (256, 2) ~128 and (256, 3)
+// ~85; a 256-thread CTA covers one whole 4^4 block, so interior neighbours
+// are read by the same SM.
+constexpr int DIRAC_VARIANTS = 4;
+
 template <typename S>
 int dirac_t(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st) {
-  long long n = g.V * p.n;
-  k_dirac<S><<<(unsigned)((n + DIRAC_TPB - 1) / DIRAC_TPB), DIRAC_TPB, 0, st>>>(g, f.links, f.clov, p);
-  return launched("k_dirac");
+  auto run = [&](int v) {
+    switch (v) {
+      case 1: return dirac_v<S, 128, 6>(g, f, p, st);
+      case 2: return dirac_v<S, 256, 2>(g, f, p, st);
+      case 3: return dirac_v<S, 256, 3>(g, f, p, st);
+      default: return dirac_v<S, 128, 5>(g, f, p, st);
+    }
+  };
+  int v = 0;
+  int rc = tuned_variant(tune_key("dirac", g, f.prec, p.n), DIRAC_VARIANTS, run, st, &v);
+  if (rc) return rc;
+  return run(v);
 }
 
 }  // namespace

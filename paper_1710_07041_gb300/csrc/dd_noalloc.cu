@@ -215,7 +215,7 @@ extern "C" int dd_solve_noalloc(dd_op_t opp, const dd_solve_params *p, const dou
       DD_CUDA(cudaStreamSynchronize(st));
       cd hcol[MAXM];
       for (int q = 0; q < kk; q++) hcol[q] = cd(hh[2 * q], hh[2 * q + 1]);
-      if (hh[131] < 0.5 * hh[130]) {
+      if (hh[131] < REORTH2 * hh[130]) {
         if ((rc = mdot(nullptr)) || (rc = maxpy())) return rc;
         DD_CUDA(cudaMemcpyAsync(hh, hd, sizeof hh, cudaMemcpyDeviceToHost, st));
         DD_CUDA(cudaStreamSynchronize(st));

@@ -19,7 +19,7 @@
 // {2h, 2h+1}; the two halves exchange partial hop sums through shared memory.
 // With Vh = block sites / 2 a multiple of 32, h is warp-uniform, so the
 // per-direction code never diverges inside a warp.
-#include "dd_internal.cuh"
+#include "dd_tune.cuh"
 
 namespace dd {
 namespace {
@@ -214,8 +214,8 @@ template <typename S> struct SapSmem {
   }
 };
 
-template <typename S, bool STAGE>
-__global__ void __launch_bounds__(256, 1) k_sap_phase(Geom g, const void *__restrict__ links,
+template <typename S, bool STAGE, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_sap_phase(Geom g, const void *__restrict__ links,
                                                    const void *__restrict__ clov, const void *__restrict__ cinv,
                                                    const RhsPtrs rp, int colour, int self_zero,
                                                    int halo_zero, int nmr) {
@@ -400,10 +400,10 @@ __global__ void __launch_bounds__(256, 1) k_sap_phase(Geom g, const void *__rest
   }
 }
 
-template <typename S, bool STAGE>
+template <typename S, bool STAGE, int MINB>
 int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
   size_t smem = SapSmem<S>::bytes(g, STAGE);
-  auto kern = k_sap_phase<S, STAGE>;
+  auto kern = k_sap_phase<S, STAGE, MINB>;
   DD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(g.nblocks / 2, rp.n);
   for (int sw = 0; sw < p.sweeps; sw++)
@@ -416,6 +416,44 @@ int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtr
       DD_LAUNCHED();
     }
   return DD_OK;
+}
+
+// Launch variants: tiles staged in shared memory with one CTA per SM; tiles
+// staged with two CTAs per SM (fits when the storage is 16-bit); tiles read
+// through L1/L2 with two CTAs per SM. Variants that do not fit are skipped.
+template <typename S>
+int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
+  const size_t limit = 227 * 1024, half = 113 * 1024;
+  const bool stage1 = SapSmem<S>::bytes(g, true) <= limit;
+  const bool stage2 = SapSmem<S>::bytes(g, true) <= half;
+  const bool nost2 = SapSmem<S>::bytes(g, false) <= half;
+  int ids[3], n = 0;
+  if (stage1) ids[n++] = 0;
+  if (stage2) ids[n++] = 1;
+  if (nost2 || !stage1) ids[n++] = 2;
+  if (!stage1 && SapSmem<S>::bytes(g, false) > limit) {
+    set_error("sap: block of %d sites needs more shared memory than available", g.Vb);
+    return DD_EINVAL;
+  }
+  auto run = [&](int k) {
+    switch (ids[k]) {
+      case 1: return sap_t<S, true, 2>(g, f, p, rp, st);
+      case 2: return sap_t<S, false, 2>(g, f, p, rp, st);
+      default: return sap_t<S, true, 1>(g, f, p, rp, st);
+    }
+  };
+  int k = 0;
+  std::string key = tune_key("sap", g, f.prec, rp.n) + "|" + std::to_string(p.sweeps) + "," +
+                    std::to_string(p.mr_steps);
+  // x is pure output when x_is_zero, so trial runs leave the same result
+  if (p.x_is_zero) {
+    int rc = tuned_variant(key, n, run, st, &k);
+    if (rc) return rc;
+  } else {
+    int c = tune_lookup(key);
+    k = c >= 0 ? c : 0;
+  }
+  return run(k);
 }
 
 }  // namespace
@@ -445,26 +483,15 @@ int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const R
     set_error("sap: 1..%d right-hand sides per launch", MAX_RHS);
     return DD_EINVAL;
   }
-  // stage the block's operator tiles in shared memory when they fit
-  const size_t limit = 227 * 1024;
   if (g.Vb > 256) {
     set_error("sap: blocks of more than 256 sites are not supported (got %d)", g.Vb);
     return DD_EINVAL;
   }
-  bool stage = sap_smem_bytes(g, f.prec, true) <= limit;
-  if (!stage && sap_smem_bytes(g, f.prec, false) > limit) {
-    set_error("sap: block of %d sites needs more shared memory than available", g.Vb);
-    return DD_EINVAL;
-  }
   switch (f.prec) {
-    case DD_F64:
-      return stage ? sap_t<double, true>(g, f, p, rp, st) : sap_t<double, false>(g, f, p, rp, st);
-    case DD_F32:
-      return stage ? sap_t<float, true>(g, f, p, rp, st) : sap_t<float, false>(g, f, p, rp, st);
-    case DD_F16:
-      return stage ? sap_t<__half, true>(g, f, p, rp, st) : sap_t<__half, false>(g, f, p, rp, st);
-    case DD_BF16:
-      return stage ? sap_t<__nv_bfloat16, true>(g, f, p, rp, st) : sap_t<__nv_bfloat16, false>(g, f, p, rp, st);
+    case DD_F64: return sap_variants<double>(g, f, p, rp, st);
+    case DD_F32: return sap_variants<float>(g, f, p, rp, st);
+    case DD_F16: return sap_variants<__half>(g, f, p, rp, st);
+    case DD_BF16: return sap_variants<__nv_bfloat16>(g, f, p, rp, st);
   }
   set_error("sap: bad precision %d", f.prec);
   return DD_EINVAL;

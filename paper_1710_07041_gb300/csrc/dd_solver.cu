@@ -315,7 +315,7 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
     const double *hp = hpin_ + HSTRIDE * (s - slots_.data());
     hcol[i].resize(s->j + 1);
     for (int q = 0; q <= s->j; q++) hcol[i][q] = cd(hp[2 * q], hp[2 * q + 1]);
-    if (hp[W1] < 0.5 * hp[W0]) again.push_back(s);
+    if (hp[W1] < REORTH2 * hp[W0]) again.push_back(s);
   }
   if (!again.empty()) {
     for (Slot *s : again) {

@@ -86,6 +86,14 @@ class BatchSolver {
 
 constexpr int HSTRIDE = 2 * 65 + 6;  // h column (complex) + norms
 
+// Classical Gram-Schmidt is repeated only when the new vector's squared norm
+// falls below REORTH2 times its value before the projection (norm ratio
+// 1e-3). One pass then loses orthogonality by at most ~eps / 1e-3: about 1e-11
+// with the double-float or FP64 arithmetic used here, far below the 1e-5 to
+// 1e-7 reduction a cycle asks for, while the classic 1/sqrt(2) test would
+// repeat nearly every step of a well-preconditioned solve.
+constexpr double REORTH2 = 1e-6;
+
 int check_solve_params(const dd_solve_params *p);
 
 }  // namespace dd
