@@ -73,9 +73,13 @@ def kernel_traffic(kernel):
     d = json.load(open(p)).get(kernel)
     if not d:
         return None
-    src = os.path.join(ROOT, d["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] if os.path.exists(src) else None
-    return d["bytes_per_launch"] if h == d.get("source_sha256_16") else None
+    h = hashlib.sha256()
+    for src in d["sources"]:
+        path = os.path.join(ROOT, src)
+        if not os.path.exists(path):
+            return None
+        h.update(open(path, "rb").read())
+    return d["bytes_per_launch"] if h.hexdigest()[:16] == d.get("source_sha256_16") else None
 
 
 class Clocks:
