@@ -85,13 +85,22 @@ __global__ void __launch_bounds__(RED_TPB) k_maxpy_norm(const double2 *__restric
   block_reduce<1>(acc, smem, partial + blockIdx.x);
 }
 
-// out[i] = sum_b partial[b][i], i < nv, fixed order
-__global__ void k_sum_partials(const double *partial, int nblk, int stride, int nv, double *out) {
-  int i = threadIdx.x;
+// out[i] = sum_b partial[b][i]: one CTA per value i, fixed summation order
+// (thread t sums blocks t, t + 256, ..., then a fixed-shape tree)
+__global__ void __launch_bounds__(256) k_sum_partials(const double *partial, int nblk, int stride, int nv,
+                                                      double *out) {
+  __shared__ double red[256];
+  const int i = blockIdx.x;
   if (i >= nv) return;
   double s = 0;
-  for (int b = 0; b < nblk; b++) s += partial[(size_t)b * stride + i];
-  out[i] = s;
+  for (int b = threadIdx.x; b < nblk; b += 256) s += partial[(size_t)b * stride + i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[i] = red[0];
 }
 
 __global__ void k_scale(double2 *y, const double2 *x, double a, size_t n) {
@@ -345,6 +354,47 @@ __global__ void k_field_to_df(Geom g, const void *in, float4 *__restrict__ out) 
   for (int c = 0; c < 12; c++) out[((size_t)b * 12 + c) * g.Vb + s] = make_float4(v.c[c].re, v.c[c].im, 0.f, 0.f);
 }
 
+// x(site) += sum_i y_i Z_i(site) for FP32 Z: the sum is accumulated in
+// double-float (y_i split into hi/lo floats once per CTA), then added to the
+// FP64 x with one FP64 add per real.
+__global__ void __launch_bounds__(128) k_update_x_df(Geom g, double *x, const void *Z, size_t zbytes, int k,
+                                                     const double2 *__restrict__ y) {
+  __shared__ float4 ys[64];
+  if (threadIdx.x < 64 && (int)threadIdx.x < k) {
+    double2 c = y[threadIdx.x];
+    float rh = (float)c.x, ih = (float)c.y;
+    ys[threadIdx.x] = make_float4(rh, ih, (float)(c.x - rh), (float)(c.y - ih));
+  }
+  __syncthreads();
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= g.V) return;
+  int b = (int)(t / g.Vb), s = (int)(t - (long long)b * g.Vb);
+  df re[12], im[12];
+#pragma unroll
+  for (int q = 0; q < 12; q++) re[q] = im[q] = {0.f, 0.f};
+  for (int i = 0; i < k; i++) {
+    Spinor<float> z;
+    load_spinor<float, float>((const char *)Z + i * zbytes, g, b, s, z);
+    const float4 c = ys[i];
+#pragma unroll
+    for (int q = 0; q < 12; q++) {
+      // (cr + i ci)(zr + i zi)
+      df_mac(re[q], c.x, c.z, z.c[q].re, 0.f);
+      df_msub(re[q], c.y, c.w, z.c[q].im, 0.f);
+      df_mac(im[q], c.x, c.z, z.c[q].im, 0.f);
+      df_mac(im[q], c.y, c.w, z.c[q].re, 0.f);
+    }
+  }
+  Spinor<double> acc;
+  load_spinor<double, double>(x, g, b, s, acc);
+#pragma unroll
+  for (int q = 0; q < 12; q++) {
+    acc.c[q].re += df_val(re[q]);
+    acc.c[q].im += df_val(im[q]);
+  }
+  store_spinor<double, double>(x, g, b, s, acc);
+}
+
 }  // namespace
 
 Blas::~Blas() {
@@ -374,7 +424,7 @@ int Blas::mdot(const double *V, size_t ldv, int k, const double *w, size_t n, do
       k_mdot<16><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, (const double2 *)w, n, partial);
     int stride = kk <= 4 ? 9 : 33;
     DD_LAUNCHED();
-    k_sum_partials<<<1, 64, 0, st>>>(partial, nblk, stride, stride, result);
+    k_sum_partials<<<stride, 256, 0, st>>>(partial, nblk, stride, stride, result);
     DD_LAUNCHED();
     if (kk > 0) DD_CUDA(cudaMemcpyAsync(h_dev + 2 * i0, result, sizeof(double) * 2 * kk, cudaMemcpyDeviceToDevice, st));
     if (wnorm2_dev && i0 == 0)
@@ -397,7 +447,7 @@ int Blas::maxpy_norm(const double *V, size_t ldv, int k, const double *h_dev, do
     DD_LAUNCHED();
   }
   if (k == 0) return norm2(w, n, norm2_dev, st);
-  k_sum_partials<<<1, 32, 0, st>>>(partial, nblk, 1, 1, norm2_dev);
+  k_sum_partials<<<1, 256, 0, st>>>(partial, nblk, 1, 1, norm2_dev);
   DD_LAUNCHED();
   return DD_OK;
 }
@@ -405,7 +455,7 @@ int Blas::maxpy_norm(const double *V, size_t ldv, int k, const double *h_dev, do
 int Blas::norm2(const double *w, size_t n, double *norm2_dev, cudaStream_t st) {
   k_mdot<4><<<nblk, RED_TPB, 0, st>>>((const double2 *)w, 0, 0, (const double2 *)w, n, partial);
   DD_LAUNCHED();
-  k_sum_partials<<<1, 32, 0, st>>>(partial, nblk, 9, 9, result);
+  k_sum_partials<<<9, 256, 0, st>>>(partial, nblk, 9, 9, result);
   DD_LAUNCHED();
   DD_CUDA(cudaMemcpyAsync(norm2_dev, result + 8, sizeof(double), cudaMemcpyDeviceToDevice, st));
   return DD_OK;
@@ -433,7 +483,7 @@ int Blas::df_mdot(const float *V, size_t ldv, int k, const float *w, size_t n, d
       k_df_mdot<8><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, (const float4 *)w, n, partial);
     int stride = kk <= 4 ? 9 : 17;
     DD_LAUNCHED();
-    k_sum_partials<<<1, 64, 0, st>>>(partial, nblk, stride, stride, result);
+    k_sum_partials<<<stride, 256, 0, st>>>(partial, nblk, stride, stride, result);
     DD_LAUNCHED();
     if (kk > 0) DD_CUDA(cudaMemcpyAsync(h_dev + 2 * i0, result, sizeof(double) * 2 * kk, cudaMemcpyDeviceToDevice, st));
     if (wnorm2_dev && i0 == 0)
@@ -456,7 +506,7 @@ int Blas::df_maxpy_norm(const float *V, size_t ldv, int k, const double *h_dev, 
       k_df_maxpy_norm<8><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial);
     DD_LAUNCHED();
   }
-  k_sum_partials<<<1, 32, 0, st>>>(partial, nblk, 1, 1, norm2_dev);
+  k_sum_partials<<<1, 256, 0, st>>>(partial, nblk, 1, 1, norm2_dev);
   return launched("k_sum_partials");
 }
 
@@ -496,7 +546,13 @@ int Blas::update_x(const Geom &g, double *x, int zprec, const void *Z, size_t zb
   unsigned grid = (unsigned)((g.V + 127) / 128);
   switch (zprec) {
     case DD_F64: k_update_x<double><<<grid, 128, 0, st>>>(g, x, Z, zbytes, k, (const double2 *)y_dev); break;
-    case DD_F32: k_update_x<float><<<grid, 128, 0, st>>>(g, x, Z, zbytes, k, (const double2 *)y_dev); break;
+    case DD_F32:
+      if (k > 64) {
+        set_error("update_x: at most 64 vectors");
+        return DD_EINVAL;
+      }
+      k_update_x_df<<<grid, 128, 0, st>>>(g, x, Z, zbytes, k, (const double2 *)y_dev);
+      break;
     default: set_error("update_x: bad precision"); return DD_EINVAL;
   }
   return launched("k_update_x");

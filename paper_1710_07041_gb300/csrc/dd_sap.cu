@@ -218,7 +218,7 @@ template <typename S, bool STAGE, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_sap_phase(Geom g, const void *__restrict__ links,
                                                    const void *__restrict__ clov, const void *__restrict__ cinv,
                                                    const RhsPtrs rp, int colour, int self_zero,
-                                                   int halo_zero, int nmr) {
+                                                   int halo_zero, int nmr, int tile) {
   using C = typename Store<S>::comp_t;
   using P = typename Store<S>::pair_t;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -232,8 +232,6 @@ __global__ void __launch_bounds__(256, MINB) k_sap_phase(Geom g, const void *__r
     block_coords(g, b, bc);
     if (((bc[0] + bc[1] + bc[2] + bc[3]) & 1) != colour) b += 1;
   }
-  const void *bf = rp.in[blockIdx.y];
-  void *xf = rp.out[blockIdx.y];
 
   cpx<C> *rho = (cpx<C> *)smem;   // MR residual on odd sites (then e_o)
   cpx<C> *te = rho + 12 * Vh;     // even-site temporary
@@ -261,158 +259,168 @@ __global__ void __launch_bounds__(256, MINB) k_sap_phase(Geom g, const void *__r
 
   const Site se = decode(g, b, j), so = decode(g, b, Vh + j);
   const unsigned nbr_e = inner_neighbours(g, se, h), nbr_o = inner_neighbours(g, so, h);
-  cpx<C> r_e[6], r_o[6];
-
-  // ---- 2. block residual r = b - D x (halves h of the even and odd site)
-  {
-    Spinor<C> bb;
-    load_spinor<S, C>(bf, g, b, j, bb);
-    half_of(bb, h, r_e);
-    load_spinor<S, C>(bf, g, b, Vh + j, bb);
-    half_of(bb, h, r_o);
-  }
-  if (!(self_zero && halo_zero)) {
+  // right-hand sides blockIdx.y * tile ... share the staged tiles
 #pragma unroll 1
-    for (int par = 0; par < 2; par++) {
-      const Site &t = par ? so : se;
-      Spinor<C> part;
-      hops_global<S, C>(g, t, h, links, xf, self_zero, halo_zero, part);
-      cpx<C> hx[6], ax[6] = {}, m[18], xh[6];
-      exchange(xch, Vh, j, h, part, hx);
-      if (!self_zero) {
-        Spinor<C> xs;
-        load_spinor<S, C>(xf, g, b, t.s, xs);
-        half_of(xs, h, xh);
-        load_clover_block<S, C>(clov, Vb, b, t.s, h, m);
-        herm6_mv(m, xh, ax);
+  for (int rr = 0; rr < tile; rr++) {
+    const int r = blockIdx.y * tile + rr;
+    if (r >= rp.n) break;
+    const void *bf = rp.in[r];
+    void *xf = rp.out[r];
+    cpx<C> r_e[6], r_o[6];
+
+    // ---- 2. block residual r = b - D x (halves h of the even and odd site)
+    {
+      Spinor<C> bb;
+      load_spinor<S, C>(bf, g, b, j, bb);
+      half_of(bb, h, r_e);
+      load_spinor<S, C>(bf, g, b, Vh + j, bb);
+      half_of(bb, h, r_o);
+    }
+    if (!(self_zero && halo_zero)) {
+  #pragma unroll 1
+      for (int par = 0; par < 2; par++) {
+        const Site &t = par ? so : se;
+        Spinor<C> part;
+        hops_global<S, C>(g, t, h, links, xf, self_zero, halo_zero, part);
+        cpx<C> hx[6], ax[6] = {}, m[18], xh[6];
+        exchange(xch, Vh, j, h, part, hx);
+        if (!self_zero) {
+          Spinor<C> xs;
+          load_spinor<S, C>(xf, g, b, t.s, xs);
+          half_of(xs, h, xh);
+          load_clover_block<S, C>(clov, Vb, b, t.s, h, m);
+          herm6_mv(m, xh, ax);
+        }
+  #pragma unroll
+        for (int i = 0; i < 6; i++) {
+          cpx<C> d = {ax[i].re + hx[i].re, ax[i].im + hx[i].im};
+          if (par) { r_o[i].re -= d.re; r_o[i].im -= d.im; }
+          else     { r_e[i].re -= d.re; r_e[i].im -= d.im; }
+        }
+        __syncthreads();
       }
-#pragma unroll
-      for (int i = 0; i < 6; i++) {
-        cpx<C> d = {ax[i].re + hx[i].re, ax[i].im + hx[i].im};
-        if (par) { r_o[i].re -= d.re; r_o[i].im -= d.im; }
-        else     { r_e[i].re -= d.re; r_e[i].im -= d.im; }
+    }
+    if constexpr (STAGE) {
+      // each thread waits for its own copies; the barrier publishes everyone's
+      cp_async_wait_all();
+      __syncthreads();
+    }
+
+    // ---- 3.-5. Schur right-hand side, MR steps, reconstruction: one loop of
+    // half-steps, odd steps on the odd site (input te), even steps on the even
+    // site (input rho). Step 0: rho = r_o - D_oe A_ee^-1 r_e. Steps 1..2 n_MR:
+    // te = A_ee^-1 D_eo rho, then p = A_oo rho - D_oe te and the MR update.
+    // Last step: e_e = A_ee^-1 (r_e - D_eo e_o).
+    cpx<C> m[18], tmp[6], rh[6], eo[6], ee[6];
+    tile_block(Ai, j, h, m);
+    herm6_mv(m, r_e, tmp);
+  #pragma unroll
+    for (int i = 0; i < 6; i++) {
+      te[(6 * h + i) * Vh + j] = tmp[i];
+      eo[i] = {0, 0};
+      rh[i] = {0, 0};
+    }
+    __syncthreads();
+    const int last = 2 * nmr + 1;
+  #pragma unroll 1
+    for (int step = 0; step <= last; step++) {
+      const bool odd = (step & 1) == 0;
+      Spinor<C> part;
+      hops_inner(Vh, odd ? Vh + j : j, h, odd ? nbr_o : nbr_e, odd ? 0 : Vh, odd ? te : rho, Lt, part);
+      cpx<C> hv[6], u[6], mu[6];
+      exchange(xch, Vh, j, h, part, hv);
+      // one clover multiply per step: A_oo rho (odd), A_ee^-1 D_eo rho (even),
+      // A_ee^-1 (r_e - D_eo e_o) (last)
+  #pragma unroll
+      for (int i = 0; i < 6; i++)
+        u[i] = odd ? rh[i] : (step == last ? cpx<C>{r_e[i].re - hv[i].re, r_e[i].im - hv[i].im} : hv[i]);
+      tile_block(odd ? Ao : Ai, j, h, m);
+      herm6_mv(m, u, mu);
+      if (odd) {
+        if (step == 0) {
+  #pragma unroll
+          for (int i = 0; i < 6; i++) rh[i] = {r_o[i].re - hv[i].re, r_o[i].im - hv[i].im};
+        } else {
+          cpx<C> p[6];
+          C pr_re = 0, pr_im = 0, pp = 0;
+  #pragma unroll
+          for (int i = 0; i < 6; i++) {
+            p[i] = {mu[i].re - hv[i].re, mu[i].im - hv[i].im};
+            pr_re += p[i].re * rh[i].re + p[i].im * rh[i].im;
+            pr_im += p[i].re * rh[i].im - p[i].im * rh[i].re;
+            pp += p[i].re * p[i].re + p[i].im * p[i].im;
+          }
+          block_sum3(pr_re, pr_im, pp, red);
+          C a_re = 0, a_im = 0;
+          if (pp > (C)0) {
+            a_re = pr_re / pp;
+            a_im = pr_im / pp;
+          }
+  #pragma unroll
+          for (int i = 0; i < 6; i++) {
+            eo[i].re += a_re * rh[i].re - a_im * rh[i].im;
+            eo[i].im += a_re * rh[i].im + a_im * rh[i].re;
+            rh[i].re -= a_re * p[i].re - a_im * p[i].im;
+            rh[i].im -= a_re * p[i].im + a_im * p[i].re;
+          }
+        }
+        // the even half-step after the last MR update reads e_o instead of rho
+        const bool last_odd = step == 2 * nmr;
+  #pragma unroll
+        for (int i = 0; i < 6; i++) rho[(6 * h + i) * Vh + j] = last_odd ? eo[i] : rh[i];
+      } else if (step == last) {
+  #pragma unroll
+        for (int i = 0; i < 6; i++) ee[i] = mu[i];
+      } else {
+  #pragma unroll
+        for (int i = 0; i < 6; i++) te[(6 * h + i) * Vh + j] = mu[i];
       }
       __syncthreads();
     }
-  }
-  if constexpr (STAGE) {
-    // each thread waits for its own copies; the barrier publishes everyone's
-    cp_async_wait_all();
-    __syncthreads();
-  }
 
-  // ---- 3.-5. Schur right-hand side, MR steps, reconstruction: one loop of
-  // half-steps, odd steps on the odd site (input te), even steps on the even
-  // site (input rho). Step 0: rho = r_o - D_oe A_ee^-1 r_e. Steps 1..2 n_MR:
-  // te = A_ee^-1 D_eo rho, then p = A_oo rho - D_oe te and the MR update.
-  // Last step: e_e = A_ee^-1 (r_e - D_eo e_o).
-  cpx<C> m[18], tmp[6], rh[6], eo[6], ee[6];
-  tile_block(Ai, j, h, m);
-  herm6_mv(m, r_e, tmp);
-#pragma unroll
-  for (int i = 0; i < 6; i++) {
-    te[(6 * h + i) * Vh + j] = tmp[i];
-    eo[i] = {0, 0};
-    rh[i] = {0, 0};
-  }
-  __syncthreads();
-  const int last = 2 * nmr + 1;
-#pragma unroll 1
-  for (int step = 0; step <= last; step++) {
-    const bool odd = (step & 1) == 0;
-    Spinor<C> part;
-    hops_inner(Vh, odd ? Vh + j : j, h, odd ? nbr_o : nbr_e, odd ? 0 : Vh, odd ? te : rho, Lt, part);
-    cpx<C> hv[6], u[6], mu[6];
-    exchange(xch, Vh, j, h, part, hv);
-    // one clover multiply per step: A_oo rho (odd), A_ee^-1 D_eo rho (even),
-    // A_ee^-1 (r_e - D_eo e_o) (last)
-#pragma unroll
-    for (int i = 0; i < 6; i++)
-      u[i] = odd ? rh[i] : (step == last ? cpx<C>{r_e[i].re - hv[i].re, r_e[i].im - hv[i].im} : hv[i]);
-    tile_block(odd ? Ao : Ai, j, h, m);
-    herm6_mv(m, u, mu);
-    if (odd) {
-      if (step == 0) {
-#pragma unroll
-        for (int i = 0; i < 6; i++) rh[i] = {r_o[i].re - hv[i].re, r_o[i].im - hv[i].im};
+    // ---- x += e: gather both halves through shared memory, then half 0
+    // writes the even site j and half 1 the odd site j
+  #pragma unroll
+    for (int i = 0; i < 6; i++) {
+      te[(6 * h + i) * Vh + j] = ee[i];
+      xch[(6 * h + i) * Vh + j] = eo[i];
+    }
+    __syncthreads();
+    {
+      const cpx<C> *src = h ? xch : te;
+      const int s = h ? Vh + j : j;
+      Spinor<C> xs, e;
+      vec_load(src, Vh, j, e);
+      if (self_zero) {
+        xs = e;
       } else {
-        cpx<C> p[6];
-        C pr_re = 0, pr_im = 0, pp = 0;
-#pragma unroll
-        for (int i = 0; i < 6; i++) {
-          p[i] = {mu[i].re - hv[i].re, mu[i].im - hv[i].im};
-          pr_re += p[i].re * rh[i].re + p[i].im * rh[i].im;
-          pr_im += p[i].re * rh[i].im - p[i].im * rh[i].re;
-          pp += p[i].re * p[i].re + p[i].im * p[i].im;
-        }
-        block_sum3(pr_re, pr_im, pp, red);
-        C a_re = 0, a_im = 0;
-        if (pp > (C)0) {
-          a_re = pr_re / pp;
-          a_im = pr_im / pp;
-        }
-#pragma unroll
-        for (int i = 0; i < 6; i++) {
-          eo[i].re += a_re * rh[i].re - a_im * rh[i].im;
-          eo[i].im += a_re * rh[i].im + a_im * rh[i].re;
-          rh[i].re -= a_re * p[i].re - a_im * p[i].im;
-          rh[i].im -= a_re * p[i].im + a_im * p[i].re;
+        load_spinor<S, C>(xf, g, b, s, xs);
+  #pragma unroll
+        for (int i = 0; i < 12; i++) {
+          xs.c[i].re += e.c[i].re;
+          xs.c[i].im += e.c[i].im;
         }
       }
-      // the even half-step after the last MR update reads e_o instead of rho
-      const bool last_odd = step == 2 * nmr;
-#pragma unroll
-      for (int i = 0; i < 6; i++) rho[(6 * h + i) * Vh + j] = last_odd ? eo[i] : rh[i];
-    } else if (step == last) {
-#pragma unroll
-      for (int i = 0; i < 6; i++) ee[i] = mu[i];
-    } else {
-#pragma unroll
-      for (int i = 0; i < 6; i++) te[(6 * h + i) * Vh + j] = mu[i];
+      store_spinor<S, C>(xf, g, b, s, xs);
     }
-    __syncthreads();
-  }
-
-  // ---- x += e: gather both halves through shared memory, then half 0
-  // writes the even site j and half 1 the odd site j
-#pragma unroll
-  for (int i = 0; i < 6; i++) {
-    te[(6 * h + i) * Vh + j] = ee[i];
-    xch[(6 * h + i) * Vh + j] = eo[i];
-  }
-  __syncthreads();
-  {
-    const cpx<C> *src = h ? xch : te;
-    const int s = h ? Vh + j : j;
-    Spinor<C> xs, e;
-    vec_load(src, Vh, j, e);
-    if (self_zero) {
-      xs = e;
-    } else {
-      load_spinor<S, C>(xf, g, b, s, xs);
-#pragma unroll
-      for (int i = 0; i < 12; i++) {
-        xs.c[i].re += e.c[i].re;
-        xs.c[i].im += e.c[i].im;
-      }
-    }
-    store_spinor<S, C>(xf, g, b, s, xs);
+    __syncthreads();   // shared vectors are reused by the next right-hand side
   }
 }
 
 template <typename S, bool STAGE, int MINB>
-int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
+int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, int tile, cudaStream_t st) {
   size_t smem = SapSmem<S>::bytes(g, STAGE);
   auto kern = k_sap_phase<S, STAGE, MINB>;
   DD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(g.nblocks / 2, rp.n);
+  dim3 grid(g.nblocks / 2, (rp.n + tile - 1) / tile);
   for (int sw = 0; sw < p.sweeps; sw++)
     for (int colour = 0; colour < 2; colour++) {
       // with x = 0 on entry: the first phase sees x = 0 everywhere, the
       // second still has x = 0 on its own (colour-1) blocks
       int self_zero = (p.x_is_zero && sw == 0) ? 1 : 0;
       int halo_zero = (p.x_is_zero && sw == 0 && colour == 0) ? 1 : 0;
-      kern<<<grid, g.Vb, smem, st>>>(g, f.links, f.clov, f.cinv, rp, colour, self_zero, halo_zero, p.mr_steps);
+      kern<<<grid, g.Vb, smem, st>>>(g, f.links, f.clov, f.cinv, rp, colour, self_zero, halo_zero, p.mr_steps,
+                                     tile);
       DD_LAUNCHED();
     }
   return DD_OK;
@@ -421,33 +429,44 @@ int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtr
 // Launch variants: tiles staged in shared memory with one CTA per SM; tiles
 // staged with two CTAs per SM (fits when the storage is 16-bit); tiles read
 // through L1/L2 with two CTAs per SM. Variants that do not fit are skipped.
+// With several right-hand sides a CTA also solves `tile` of them with one
+// staging of its block's operator (rhs_tile; 0 lets the autotuner choose).
 template <typename S>
 int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
   const size_t limit = 227 * 1024, half = 113 * 1024;
   const bool stage1 = SapSmem<S>::bytes(g, true) <= limit;
   const bool stage2 = SapSmem<S>::bytes(g, true) <= half;
   const bool nost2 = SapSmem<S>::bytes(g, false) <= half;
-  int ids[3], n = 0;
-  if (stage1) ids[n++] = 0;
-  if (stage2) ids[n++] = 1;
-  if (nost2 || !stage1) ids[n++] = 2;
   if (!stage1 && SapSmem<S>::bytes(g, false) > limit) {
     set_error("sap: block of %d sites needs more shared memory than available", g.Vb);
     return DD_EINVAL;
   }
+  int layouts[3], nl = 0;
+  if (stage1) layouts[nl++] = 0;
+  if (stage2) layouts[nl++] = 1;
+  if (nost2 || !stage1) layouts[nl++] = 2;
+  int tiles[6], nt = 0;
+  if (p.rhs_tile > 0) {
+    tiles[nt++] = p.rhs_tile < rp.n ? p.rhs_tile : rp.n;
+  } else {
+    const int cand[5] = {1, 2, 4, 8, 12};
+    for (int c : cand)
+      if (c <= rp.n) tiles[nt++] = c;
+  }
   auto run = [&](int k) {
-    switch (ids[k]) {
-      case 1: return sap_t<S, true, 2>(g, f, p, rp, st);
-      case 2: return sap_t<S, false, 2>(g, f, p, rp, st);
-      default: return sap_t<S, true, 1>(g, f, p, rp, st);
+    const int layout = layouts[k % nl], tile = tiles[k / nl];
+    switch (layout) {
+      case 1: return sap_t<S, true, 2>(g, f, p, rp, tile, st);
+      case 2: return sap_t<S, false, 2>(g, f, p, rp, tile, st);
+      default: return sap_t<S, true, 1>(g, f, p, rp, tile, st);
     }
   };
   int k = 0;
   std::string key = tune_key("sap", g, f.prec, rp.n) + "|" + std::to_string(p.sweeps) + "," +
-                    std::to_string(p.mr_steps);
+                    std::to_string(p.mr_steps) + "," + std::to_string(p.rhs_tile);
   // x is pure output when x_is_zero, so trial runs leave the same result
   if (p.x_is_zero) {
-    int rc = tuned_variant(key, n, run, st, &k);
+    int rc = tuned_variant(key, nl * nt, run, st, &k);
     if (rc) return rc;
   } else {
     int c = tune_lookup(key);
