@@ -58,6 +58,7 @@ def _L():
             "or_block_site": ([pi, pi, l, l], l),
             "or_sap": ([pi, i, pi, pd, pd, pd, pd, pd, i, i], i),
             "or_fgmres": ([pi, i, pi, pd, pd, pd, pd, pd, i, d, i, i, i, pd], i),
+            "or_apply_D_sites": ([pi, i, pd, d, d, pd, P(l), l, pd], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -111,6 +112,21 @@ def site_inverse(A) -> np.ndarray:
     out = np.empty_like(A)
     if _L().or_site_inverse(A.shape[0], _dp(A), _dp(out)) != 0:
         raise ValueError("singular site matrix")
+    return out
+
+
+def apply_D_sites(dims, U, c_sw: float, m0: float, psi, sites, antiperiodic: bool = True) -> np.ndarray:
+    """(D psi)(n) at the given canonical sites, shape (len(sites), 4, 3); the
+    clover term is formed on the fly, so no full-lattice site matrices are
+    held (for sampled checks on large lattices)."""
+    U = _c128(U)
+    psi = _c128(psi)
+    st = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.empty((len(st), 4, 3), dtype=np.complex128)
+    rc = _L().or_apply_D_sites(_dims(dims), int(bool(antiperiodic)), _dp(U), float(c_sw), float(m0), _dp(psi),
+                               st.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), len(st), _dp(out))
+    if rc:
+        raise ValueError("or_apply_D_sites")
     return out
 
 

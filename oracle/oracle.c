@@ -345,6 +345,45 @@ int or_apply_D(const int dims[4], int antiperiodic, const double *U, const doubl
   return 0;
 }
 
+/* (D psi)(n) at the listed sites only, with A(n) = 4 + m0 + C(n) formed from
+ * the links on the fly (same definitions as or_clover_term and or_apply_D).
+ * For checking results on lattices whose full site matrices would not fit in
+ * host memory. out: [nsites][12] complex. */
+int or_apply_D_sites(const int dims[4], int antiperiodic, const double *U, double c_sw, double m0,
+                     const double *in, const long *sites, long nsites, double *out) {
+  lat_t lt;
+  if (lat_init(&lt, dims, antiperiodic) || !U || !in || !sites || !out || nsites < 0) return -1;
+  cd gm[4][4][4];
+  for (int mu = 0; mu < 4; mu++) gamma_mu(mu, gm[mu]);
+  nbr_filter f = {&lt, NULL};
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (long i = 0; i < nsites; i++) {
+    long n = sites[i];
+    if (n < 0 || n >= lt.V) { bad = 1; continue; }
+    cd A[144];
+    for (int k = 0; k < 144; k++) A[k] = (k % 13 == 0) ? (4.0 + m0) : 0.0;
+    for (int mu = 0; mu < 4; mu++)
+      for (int nu = 0; nu < 4; nu++) {
+        if (mu == nu) continue;
+        su3 qmn = clover_leaves(&lt, U, n, mu, nu);
+        su3 qnm = clover_leaves(&lt, U, n, nu, mu);
+        cd gg[4][4];
+        mat4_mul(gm[mu], gm[nu], gg);
+        for (int s = 0; s < 4; s++)
+          for (int t = 0; t < 4; t++)
+            for (int a = 0; a < 3; a++)
+              for (int b = 0; b < 3; b++)
+                A[(3 * s + a) * 12 + 3 * t + b] += -(c_sw / 32.0) * gg[s][t] * (qmn.m[a][b] - qnm.m[a][b]);
+      }
+    cd acc[12];
+    site_mv(A, (const cd *)in + n * 12, acc);
+    hopping_at(&f, U, (const cd *)in, n, acc);
+    memcpy((cd *)out + i * 12, acc, sizeof acc);
+  }
+  return bad ? -1 : 0;
+}
+
 /* ------------------------------------------------------------- blocks */
 typedef struct {
   lat_t lt;

@@ -1,0 +1,114 @@
+"""GPU parity at the workloads' full sizes, in the launch configurations the
+benchmark uses.
+
+* 64 x 32^3, FP32 smoother (the benchmark workload): apply_D against the
+  FP64 oracle on 4096 sampled sites; one full Schwarz sweep against the
+  oracle's sweep over the whole lattice; a solve whose true residual the
+  oracle recomputes over the whole lattice.
+* 96 x 48^3, FP16 and BF16 smoothers (mixed-precision workload): apply_D on
+  sampled sites (the oracle forms the clover term per site, since the full
+  site matrices would need ~70 GB of host memory); solves to 1e-6, 1e-8 and
+  1e-10 whose residual the oracle recomputes on sampled sites (a property of
+  any correct solution: |b - D x| is small at every site), next to the
+  library's FP64 true residual.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1710_07041_gb300 as dd
+import synth
+from gpu_common import relerr
+
+pytestmark = pytest.mark.gpu
+
+W2 = synth.WORKLOADS["sap_fgmres_64x32^3_fp32"]
+W3 = synth.WORKLOADS["sap_fgmres_96x48^3_mixed"]
+
+
+def _sites(V, n, seed):
+    return np.sort(np.unique((synth.uniform(n, seed) * V).astype(np.int64) % V))
+
+
+@pytest.fixture(scope="module")
+def bench_problem():
+    U = synth.gauge(W2["dims"], W2["eps"], W2["n_stout"], W2["rho"], W2["gauge_seed"])
+    b = synth.gaussian_spinor(int(np.prod(W2["dims"])), W2["rhs_seed"])
+    lat = dd.Lattice(W2["dims"], W2["block"])
+    gauge = dd.Gauge(lat, U)
+    op = dd.Op(gauge, W2["c_sw"], W2["m0"], dd.F32)
+    ref = oracle.Operator(W2["dims"], U, W2["c_sw"], W2["m0"])
+    yield U, b, lat, op, ref
+    op.close()
+    gauge.close()
+    lat.close()
+
+
+def test_bench_workload_dslash_sampled(bench_problem):
+    U, b, lat, op, ref = bench_problem
+    fin, fout = lat.to_field(b, dd.F32), lat.new_field(dd.F32)
+    op.apply_D(dd.F32, fin, fout)
+    got = lat.from_field(fout, dd.F32)
+    sites = _sites(lat.V, 4096, 5)
+    want = oracle.apply_D_sites(W2["dims"], U, W2["c_sw"], W2["m0"], b, sites)
+    assert relerr(got[sites], want) <= 1e-6
+
+
+def test_bench_workload_sap_sweep(bench_problem):
+    U, b, lat, op, ref = bench_problem
+    fb, fx = lat.to_field(b, dd.F32), lat.new_field(dd.F32)
+    op.sap_smooth(fb, fx, 1, W2["mr_steps"])
+    got = lat.from_field(fx, dd.F32)
+    want = ref.sap(W2["block"], b, 1, W2["mr_steps"])
+    assert relerr(got, want) <= 1e-5
+
+
+def test_bench_workload_solve_true_residual(bench_problem):
+    U, b, lat, op, ref = bench_problem
+    x, info = op.solve(b, tol=1e-10, restart=W2["restart"], sweeps=W2["sweeps"], mr_steps=W2["mr_steps"],
+                       max_iter=2000)
+    assert info[0]["status"] == 0
+    assert relerr(ref.apply(x), b) <= 1e-10
+
+
+@pytest.fixture(scope="module")
+def mixed_problem():
+    U = synth.gauge(W3["dims"], W3["eps"], W3["n_stout"], W3["rho"], W3["gauge_seed"])
+    b = synth.gaussian_spinor(int(np.prod(W3["dims"])), W3["rhs_seed"])
+    lat = dd.Lattice(W3["dims"], W3["block"])
+    gauge = dd.Gauge(lat, U)
+    yield U, b, lat, gauge
+    gauge.close()
+    lat.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(dd.F16, 1e-3), (dd.BF16, 1e-2)])
+def test_mixed_workload_dslash_sampled(mixed_problem, prec, tol):
+    U, b, lat, gauge = mixed_problem
+    op = dd.Op(gauge, W3["c_sw"], W3["m0"], prec)
+    fin, fout = lat.to_field(b, prec), lat.new_field(prec)
+    op.apply_D(prec, fin, fout)
+    got = lat.from_field(fout, prec)
+    sites = _sites(lat.V, 4096, 6)
+    want = oracle.apply_D_sites(W3["dims"], U, W3["c_sw"], W3["m0"], b, sites)
+    assert relerr(got[sites], want) <= tol
+    op.close()
+
+
+@pytest.mark.parametrize("prec", [dd.F16, dd.BF16])
+def test_mixed_workload_solves(mixed_problem, prec):
+    U, b, lat, gauge = mixed_problem
+    op = dd.Op(gauge, W3["c_sw"], W3["m0"], prec)
+    sites = _sites(lat.V, 4096, 7)
+    bs = b[sites]
+    for tol in (1e-6, 1e-8, 1e-10):
+        x, info = op.solve(b, tol=tol, restart=W3["restart"], sweeps=W3["sweeps"], mr_steps=W3["mr_steps"],
+                           max_iter=3000)
+        r = bs - oracle.apply_D_sites(W3["dims"], U, W3["c_sw"], W3["m0"], x, sites)
+        sampled = float(np.linalg.norm(r) / np.linalg.norm(bs))
+        print(f"96x48^3 prec={prec} tol={tol:g}: iterations {info[0]['iterations']}, "
+              f"FP64 true residual {info[0]['true_rel_residual']:.3e}, oracle residual on "
+              f"{len(sites)} sites {sampled:.3e}")
+        assert info[0]["status"] == 0 and info[0]["true_rel_residual"] <= tol
+        assert sampled <= 3 * tol
+    op.close()

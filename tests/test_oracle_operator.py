@@ -106,3 +106,15 @@ def test_gauge_covariance_of_D():
     lhs = opp.apply(Gpsi)
     rhs = np.einsum("nab,nsb->nsa", G, op.apply(psi))
     assert np.linalg.norm(lhs - rhs) / np.linalg.norm(rhs) < 1e-12
+
+
+def test_sampled_sites_equal_full_operator():
+    """The per-site evaluation used for large lattices equals the full D."""
+    dims = (8, 4, 4, 4)
+    V = int(np.prod(dims))
+    U = synth.gauge(dims, 0.3, 1, 0.1, seed=71)
+    psi = synth.gaussian_spinor(V, 72)
+    full = oracle.Operator(dims, U, c_sw=1.7, m0=-0.03).apply(psi)
+    sites = np.array([0, 1, 17, 100, V - 1, 333])
+    part = oracle.apply_D_sites(dims, U, 1.7, -0.03, psi, sites)
+    assert np.allclose(part, full[sites], atol=1e-14, rtol=0)
