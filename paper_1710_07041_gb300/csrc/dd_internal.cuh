@@ -32,6 +32,7 @@ void set_error(const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *where);
 // Count a kernel launch and report a launch error (if any).
 int launched(const char *where);
+void count_launches(int n);  // kernels launched through a replayed graph
 #define DD_LAUNCHED()                          \
   do {                                         \
     int rc_ = ::dd::launched("kernel launch"); \

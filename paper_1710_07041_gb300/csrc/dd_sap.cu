@@ -19,6 +19,10 @@
 // {2h, 2h+1}; the two halves exchange partial hop sums through shared memory.
 // With Vh = block sites / 2 a multiple of 32, h is warp-uniform, so the
 // per-direction code never diverges inside a warp.
+#include <map>
+#include <mutex>
+#include <string>
+
 #include "dd_tune.cuh"
 
 namespace dd {
@@ -63,36 +67,36 @@ __device__ __forceinline__ void vec_load(const cpx<C> *v, int Vh, int q, Spinor<
 }
 
 // In-block neighbours of one site for the two directions of its thread half:
-// four bytes (dir 2h fwd, dir 2h bwd, dir 2h+1 fwd, dir 2h+1 bwd), each the
-// neighbour's index within the other parity's half-vector, 0xFF if the hop
-// leaves the block.
-__device__ __forceinline__ unsigned inner_neighbours(const Geom &g, const Site &t, int h) {
-  unsigned packed = 0;
+// four 16-bit fields (dir 2h fwd, dir 2h bwd, dir 2h+1 fwd, dir 2h+1 bwd),
+// each the neighbour's index within the other parity's half-vector, NONE if
+// the hop leaves the block.
+constexpr unsigned NONE = 0xFFFFu;
+__device__ __forceinline__ uint2 inner_neighbours(const Geom &g, const Site &t, int h) {
+  unsigned f[4];
   for (int k = 0; k < 4; k++) {
     int nb, ns;
     float sg;
     bool inside;
     neighbour(g, t, 2 * h + (k >> 1), (k & 1) ? -1 : +1, &nb, &ns, &sg, &inside);
-    unsigned idx = inside ? (unsigned)(ns - (t.p ? 0 : g.Vh)) : 0xFFu;
-    packed |= idx << (8 * k);
+    f[k] = inside ? (unsigned)(ns - (t.p ? 0 : g.Vh)) : NONE;
   }
-  return packed;
+  return make_uint2(f[0] | (f[1] << 16), f[2] | (f[3] << 16));
 }
 
 // acc += hop pair in direction MU into the site at tile position s from the
 // shared half-vector v (the other parity), links from tile L. nf/nbk: neighbour
-// indices (0xFF: outside the block); off: tile offset of the other parity.
+// indices (NONE: outside the block); off: tile offset of the other parity.
 template <int MU, typename C, typename P>
 __device__ __forceinline__ void hop_inner_dir(int Vh, int s, unsigned nf, unsigned nbk, int off, const cpx<C> *v,
                                               const Tile<P> &L, Spinor<C> &acc) {
   Link<C> u;
   Spinor<C> psi;
-  if (nf != 0xFFu) {
+  if (nf != NONE) {
     vec_load(v, Vh, (int)nf, psi);
     tile_link(L, s, MU, u);
     hop<MU, true>(acc, u, psi, (C)-0.5);
   }
-  if (nbk != 0xFFu) {
+  if (nbk != NONE) {
     vec_load(v, Vh, (int)nbk, psi);
     tile_link(L, (int)nbk + off, MU, u);
     hop<MU, false>(acc, u, psi, (C)-0.5);
@@ -100,16 +104,16 @@ __device__ __forceinline__ void hop_inner_dir(int Vh, int s, unsigned nf, unsign
 }
 
 template <typename C, typename P>
-__device__ __forceinline__ void hops_inner(int Vh, int s, int h, unsigned nbr, int off, const cpx<C> *v,
+__device__ __forceinline__ void hops_inner(int Vh, int s, int h, uint2 nbr, int off, const cpx<C> *v,
                                            const Tile<P> &L, Spinor<C> &acc) {
 #pragma unroll
   for (int i = 0; i < 12; i++) acc.c[i] = {0, 0};
   if (h == 0) {
-    hop_inner_dir<0>(Vh, s, nbr & 0xFFu, (nbr >> 8) & 0xFFu, off, v, L, acc);
-    hop_inner_dir<1>(Vh, s, (nbr >> 16) & 0xFFu, nbr >> 24, off, v, L, acc);
+    hop_inner_dir<0>(Vh, s, nbr.x & NONE, nbr.x >> 16, off, v, L, acc);
+    hop_inner_dir<1>(Vh, s, nbr.y & NONE, nbr.y >> 16, off, v, L, acc);
   } else {
-    hop_inner_dir<2>(Vh, s, nbr & 0xFFu, (nbr >> 8) & 0xFFu, off, v, L, acc);
-    hop_inner_dir<3>(Vh, s, (nbr >> 16) & 0xFFu, nbr >> 24, off, v, L, acc);
+    hop_inner_dir<2>(Vh, s, nbr.x & NONE, nbr.x >> 16, off, v, L, acc);
+    hop_inner_dir<3>(Vh, s, nbr.y & NONE, nbr.y >> 16, off, v, L, acc);
   }
 }
 
@@ -214,8 +218,8 @@ template <typename S> struct SapSmem {
   }
 };
 
-template <typename S, bool STAGE, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_sap_phase(Geom g, const void *__restrict__ links,
+template <typename S, bool STAGE, int MINB, int NT>
+__global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g, const void *__restrict__ links,
                                                    const void *__restrict__ clov, const void *__restrict__ cinv,
                                                    const RhsPtrs rp, int colour, int self_zero,
                                                    int halo_zero, int nmr, int tile) {
@@ -258,7 +262,7 @@ __global__ void __launch_bounds__(256, MINB) k_sap_phase(Geom g, const void *__r
   }
 
   const Site se = decode(g, b, j), so = decode(g, b, Vh + j);
-  const unsigned nbr_e = inner_neighbours(g, se, h), nbr_o = inner_neighbours(g, so, h);
+  const uint2 nbr_e = inner_neighbours(g, se, h), nbr_o = inner_neighbours(g, so, h);
   // right-hand sides blockIdx.y * tile ... share the staged tiles
 #pragma unroll 1
   for (int rr = 0; rr < tile; rr++) {
@@ -407,11 +411,20 @@ __global__ void __launch_bounds__(256, MINB) k_sap_phase(Geom g, const void *__r
   }
 }
 
-template <typename S, bool STAGE, int MINB>
+template <typename S, bool STAGE, int MINB, int NT = 256>
 int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, int tile, cudaStream_t st) {
   size_t smem = SapSmem<S>::bytes(g, STAGE);
-  auto kern = k_sap_phase<S, STAGE, MINB>;
-  DD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  auto kern = k_sap_phase<S, STAGE, MINB, NT>;
+  // raise the kernel's dynamic shared-memory limit once (never during a capture)
+  static std::mutex mu;
+  static int raised = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (raised < (int)smem) {
+      DD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+      raised = 227 * 1024;
+    }
+  }
   dim3 grid(g.nblocks / 2, (rp.n + tile - 1) / tile);
   for (int sw = 0; sw < p.sweeps; sw++)
     for (int colour = 0; colour < 2; colour++) {
@@ -424,6 +437,57 @@ int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtr
       DD_LAUNCHED();
     }
   return DD_OK;
+}
+
+// The 2 x sweeps phase launches of one smoother application are captured once
+// into a CUDA graph per (operator, parameters, variant, field pointers) and
+// replayed afterwards: one launch per application instead of 2 x sweeps.
+// When the caller's stream is itself being captured the launches go into the
+// caller's graph directly. DD_SAP_GRAPHS=0 disables the graphs.
+struct GraphCache {
+  std::mutex mu;
+  std::map<std::string, cudaGraphExec_t> execs;
+};
+static GraphCache g_graphs;
+
+static int launch_as_graph(const std::string &key, int variant, int nkernels, const OpFields &f, const RhsPtrs &rp,
+                           const std::function<int()> &enqueue, cudaStream_t st) {
+  const char *env = getenv("DD_SAP_GRAPHS");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cap);
+  if ((env && env[0] == '0') || cap != cudaStreamCaptureStatusNone || st == 0) return enqueue();
+  std::string k = key + "|v" + std::to_string(variant) + "|" + std::to_string((uintptr_t)f.links);
+  for (int i = 0; i < rp.n; i++)
+    k += "|" + std::to_string((uintptr_t)rp.in[i]) + ":" + std::to_string((uintptr_t)rp.out[i]);
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_graphs.mu);
+    auto it = g_graphs.execs.find(k);
+    if (it != g_graphs.execs.end()) exec = it->second;
+  }
+  if (!exec) {
+    cudaGraph_t graph = nullptr;
+    DD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue();
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "sap graph capture");
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "sap graph instantiate");
+    std::lock_guard<std::mutex> lk(g_graphs.mu);
+    if (g_graphs.execs.size() >= 256) {   // bounded cache: start over when full
+      for (auto &kv : g_graphs.execs) cudaGraphExecDestroy(kv.second);
+      g_graphs.execs.clear();
+    }
+    g_graphs.execs[k] = exec;
+  } else {
+    count_launches(nkernels);
+  }
+  return cuda_fail(cudaGraphLaunch(exec, st), "sap graph launch");
 }
 
 // Launch variants: tiles staged in shared memory with one CTA per SM; tiles
@@ -442,9 +506,14 @@ int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const
     return DD_EINVAL;
   }
   int layouts[3], nl = 0;
-  if (stage1) layouts[nl++] = 0;
-  if (stage2) layouts[nl++] = 1;
-  if (nost2 || !stage1) layouts[nl++] = 2;
+  if (g.Vb > 256) {
+    // 512-site blocks (e.g. 8 x 4^3): 512 threads, one CTA per SM
+    layouts[nl++] = stage1 ? 3 : 4;
+  } else {
+    if (stage1) layouts[nl++] = 0;
+    if (stage2) layouts[nl++] = 1;
+    if (nost2 || !stage1) layouts[nl++] = 2;
+  }
   int tiles[6], nt = 0;
   if (p.rhs_tile > 0) {
     tiles[nt++] = p.rhs_tile < rp.n ? p.rhs_tile : rp.n;
@@ -458,6 +527,8 @@ int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const
     switch (layout) {
       case 1: return sap_t<S, true, 2>(g, f, p, rp, tile, st);
       case 2: return sap_t<S, false, 2>(g, f, p, rp, tile, st);
+      case 3: return sap_t<S, true, 1, 512>(g, f, p, rp, tile, st);
+      case 4: return sap_t<S, false, 1, 512>(g, f, p, rp, tile, st);
       default: return sap_t<S, true, 1>(g, f, p, rp, tile, st);
     }
   };
@@ -472,7 +543,7 @@ int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const
     int c = tune_lookup(key);
     k = c >= 0 ? c : 0;
   }
-  return run(k);
+  return launch_as_graph(key, k, 2 * p.sweeps, f, rp, [&] { return run(k); }, st);
 }
 
 }  // namespace
@@ -502,8 +573,8 @@ int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const R
     set_error("sap: 1..%d right-hand sides per launch", MAX_RHS);
     return DD_EINVAL;
   }
-  if (g.Vb > 256) {
-    set_error("sap: blocks of more than 256 sites are not supported (got %d)", g.Vb);
+  if (g.Vb > 512) {
+    set_error("sap: blocks of more than 512 sites are not supported (got %d)", g.Vb);
     return DD_EINVAL;
   }
   switch (f.prec) {

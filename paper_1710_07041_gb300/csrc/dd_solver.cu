@@ -52,7 +52,7 @@ size_t BatchSolver::bytes_per_slot(const Geom &g, int prec, int m) {
 }
 
 BatchSolver::BatchSolver(const Op *op, const dd_solve_params &p, int slots, cudaStream_t st)
-    : op_(op), p_(p), st_(st), slots_(slots) {
+    : op_(op), p_(p), st_(st), slots_(slots), caller_(st) {
   const Geom &g = op->lat->g;
   zprec_ = op->prec == DD_F64 ? DD_F64 : DD_F32;
   // mixed precision keeps the Krylov basis in double-float (FP32 hi/lo pairs):
@@ -76,6 +76,7 @@ BatchSolver::~BatchSolver() {
   if (ypin_) cudaFreeHost(ypin_);
   for (auto &e : ev_)
     if (e) cudaEventDestroy(e);
+  if (own_stream_) cudaStreamDestroy(st_);
 }
 
 int BatchSolver::init() {
@@ -108,6 +109,12 @@ int BatchSolver::init() {
   DD_CUDA(cudaMallocHost((void **)&hpin_, sizeof(double) * HSTRIDE * n));
   DD_CUDA(cudaMallocHost((void **)&ypin_, sizeof(double) * 2 * 64 * n));
   for (auto &e : ev_) DD_CUDA(cudaEventCreate(&e));
+  // work on a stream of our own when given the legacy default stream, so the
+  // smoother's launches can be captured into CUDA graphs
+  if (caller_ == nullptr) {
+    DD_CUDA(cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking));
+    own_stream_ = true;
+  }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -384,6 +391,10 @@ int BatchSolver::run(const std::function<bool(RhsJob &)> &next) {
   failed_ = 0;
   bool more = true;
   int rc;
+  if (own_stream_) {   // order our stream after the caller's prior work
+    DD_CUDA(cudaEventRecord(ev_[0], caller_));
+    DD_CUDA(cudaStreamWaitEvent(st_, ev_[0], 0));
+  }
   for (;;) {
     for (auto &s : slots_) {
       if (s.busy || !more) continue;
@@ -408,6 +419,10 @@ int BatchSolver::run(const std::function<bool(RhsJob &)> &next) {
       continue;
     }
     if ((rc = arnoldi_step(A))) return rc;
+  }
+  if (own_stream_) {   // and the caller's later work after ours
+    DD_CUDA(cudaEventRecord(ev_[0], st_));
+    DD_CUDA(cudaStreamWaitEvent(caller_, ev_[0], 0));
   }
   return failed_ ? DD_ENOTCONV : DD_OK;
 }

@@ -81,6 +81,8 @@ class BatchSolver {
   double *ydev_ = nullptr;   // [slots][2*64]
   double *ypin_ = nullptr;
   cudaEvent_t ev_[4] = {};
+  cudaStream_t caller_ = nullptr;  // the caller's stream
+  bool own_stream_ = false;        // st_ created here (the caller passed the legacy stream)
   int failed_ = 0;
 };
 

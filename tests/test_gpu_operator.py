@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {dd.F64: 1e-13, dd.F32: 1e-6, dd.F16: 1e-3, dd.BF16: 1e-2}
 SHAPES = [((4, 4, 4, 4), (2, 2, 2, 2)), ((8, 4, 4, 12), (2, 2, 2, 2)), ((8, 8, 8, 8), (4, 4, 4, 4)),
-          ((16, 8, 8, 8), (4, 4, 2, 4))]
+          ((16, 8, 8, 8), (4, 4, 2, 4)), ((16, 8, 8, 8), (8, 4, 4, 4))]
 
 
 @pytest.mark.parametrize("dims,block", SHAPES)
