@@ -384,6 +384,161 @@ def run_kernels(args):
     print(json.dumps(res), flush=True)
 
 
+def _solve_rate(op, b, kw, reps=1):
+    t0 = time.perf_counter()
+    infos = []
+    for _ in range(reps):
+        _, info = op.solve(b, **kw)
+        infos += info
+    return (time.perf_counter() - t0) / (reps * max(1, b.shape[0] if b.ndim == 4 else 1)), infos
+
+
+def run_batched(args):
+    """Batched multi-RHS workload: 48^3 x 96, 12 point sources (one per spin-colour
+    at the origin) + 12 complex Z2-noise sources, FP16 storage. Autotunes the
+    Schwarz block over {4^4, 8x4^3} and the RHS tile over {4, 8, 12} by timing
+    one smoother application on all 24 sources, then solves all 24 to 1e-10 in
+    as many concurrent slots as device memory allows, and times one plain FP64
+    GPU SAP-FGMRES solve for the speedup."""
+    import torch
+
+    import paper_1710_07041_gb300 as dd
+
+    wl = synth.WORKLOADS["batched_48^3x96_24rhs"]
+    dims = wl["dims"]
+    V = int(np.prod(dims))
+    U = synth.gauge(dims, wl["eps"], wl["n_stout"], wl["rho"], wl["gauge_seed"])
+    srcs = [synth.point_source(V, s, c) for s in range(4) for c in range(3)]
+    srcs += [synth.z2_spinor(V, wl["rhs_seed"] + k) for k in range(12)]
+    B = np.stack(srcs)
+    stream = torch.cuda.current_stream()
+    out = {"mode": "batched", "workload": "batched_48^3x96_24rhs", "nrhs": 24, "sap": {}}
+    best = None
+    for block in ((4, 4, 4, 4), (8, 4, 4, 4)):
+        lat = dd.Lattice(dims, block)
+        gauge = dd.Gauge(lat, U)
+        op = dd.Op(gauge, wl["c_sw"], wl["m0"], dd.F16)
+        fb = lat.to_field(B, dd.F16, scale=1.0)
+        fx = lat.new_field(dd.F16, 24)
+        for tile in (4, 8, 12):
+            op.sap_smooth(fb, fx, wl["sweeps"], wl["mr_steps"], nrhs=24, rhs_tile=tile)
+            ms = ev_time(lambda: op.sap_smooth(fb, fx, wl["sweeps"], wl["mr_steps"], nrhs=24, rhs_tile=tile), 3,
+                         stream)
+            key = f"block {'x'.join(map(str, block))} tile {tile}"
+            out["sap"][key] = {"ms_per_application_24rhs": ms, "ms_per_rhs": ms / 24}
+            if best is None or ms < best[0]:
+                best = (ms, block, tile)
+        del fb, fx
+        op.close(); gauge.close(); lat.close()
+        torch.cuda.empty_cache()
+    out["chosen"] = {"block": list(best[1]), "rhs_tile": best[2]}
+    lat = dd.Lattice(dims, best[1])
+    gauge = dd.Gauge(lat, U)
+    op = dd.Op(gauge, wl["c_sw"], wl["m0"], dd.F16)
+    kw = dict(tol=1e-10, restart=wl["restart"], sweeps=wl["sweeps"], mr_steps=wl["mr_steps"], max_iter=3000)
+    t0 = time.perf_counter()
+    x, infos = op.solve(B, **kw)
+    t = time.perf_counter() - t0
+    out["solve_all_24"] = {"seconds": t, "rhs_per_s": 24 / t,
+                           "max_true_rel_residual": max(i["true_rel_residual"] for i in infos),
+                           "iterations": [int(i["iterations"]) for i in infos]}
+    op.close()
+    op64 = dd.Op(gauge, wl["c_sw"], wl["m0"], dd.F64)
+    t64, info64 = _solve_rate(op64, B[12], dict(kw, inner_reduction=0.0))
+    out["plain_fp64_one_rhs"] = {"seconds": t64, "iterations": int(info64[0]["iterations"]),
+                                 "true_rel_residual": info64[0]["true_rel_residual"]}
+    out["speedup_vs_plain_fp64"] = (24 / t) / (1 / t64)
+    op64.close(); gauge.close(); lat.close()
+    print(json.dumps(out), flush=True)
+
+
+def run_serve(args):
+    """Served stream: Poisson arrivals at 200 req/s over lattices 16^3x32,
+    24^3x48 and 32^3x64 (equal mix), 1-12 right-hand sides each, on 8 resident
+    gauge fields (3 + 3 + 2; exp(i 0.25 H) + 2 stout, seeds 500..507), m0 drawn
+    from {-0.03, -0.0033, 0.0233, 0.05} (uniform grid over [-0.03, 0.05]),
+    mixed-precision (FP16) solves to 1e-10 through the continuous-batching
+    server. Reports p50/p99 latency and solves/s next to the plain FP64 GPU
+    solve of the same request mix (estimated from one timed FP64 solve per
+    lattice size)."""
+    import torch
+
+    import paper_1710_07041_gb300 as dd
+
+    sizes = [(32, 16, 16, 16), (48, 24, 24, 24), (64, 32, 32, 32)]
+    fields = [(sizes[0], 500), (sizes[0], 501), (sizes[0], 502), (sizes[1], 503), (sizes[1], 504), (sizes[1], 505),
+              (sizes[2], 506), (sizes[2], 507)]
+    m0s = [-0.03, -0.0033, 0.0233, 0.05]
+    lats = {d: dd.Lattice(d, (4, 4, 4, 4)) for d in sizes}
+    gauges = [dd.Gauge(lats[d], synth.gauge(d, 0.25, 2, 0.1, seed)) for d, seed in fields]
+    ops = {}
+
+    def op_for(fi, mi, prec=dd.F16):
+        k = (fi, mi, prec)
+        if k not in ops:
+            ops[k] = dd.Op(gauges[fi], 1.7, m0s[mi], prec)
+        return ops[k]
+
+    nreq = args.requests
+    rate = 200.0
+    u = synth.uniform(4 * nreq, 51)
+    arrivals = np.cumsum(-np.log(u[:nreq]) / rate)
+    reqs = []
+    for k in range(nreq):
+        size = int(u[nreq + k] * 3) % 3
+        fi = [i for i, (d, _) in enumerate(fields) if d == sizes[size]][int(u[2 * nreq + k] * 8) % (3 if size < 2 else 2)]
+        nrhs = 1 + int(u[3 * nreq + k] * 12) % 12
+        mi = k % len(m0s)
+        V = int(np.prod(fields[fi][0]))
+        b = synth.gaussian(12 * V * nrhs, 1000 + k).reshape(nrhs, V, 4, 3)
+        reqs.append((arrivals[k], fi, mi, nrhs, b))
+    for _, fi, mi, _, _ in reqs:   # resident operators before the stream starts
+        op_for(fi, mi)
+    srv = dd.Server(max_slots=8, max_batch_rhs=12)
+    # warm-up: one small request per lattice size (autotuning, graphs)
+    for d in sizes:
+        fi = [i for i, (dd_, _) in enumerate(fields) if dd_ == d][0]
+        t = srv.submit(op_for(fi, 0), synth.gaussian_spinor(int(np.prod(d)), 7))
+        srv.wait(t)
+    srv.close()
+    srv = dd.Server(max_slots=8, max_batch_rhs=12)
+    tickets = []
+    t0 = time.perf_counter()
+    for at, fi, mi, nrhs, b in reqs:
+        now = time.perf_counter() - t0
+        if at > now:
+            time.sleep(at - now)
+        tickets.append((srv.submit(op_for(fi, mi), b if nrhs > 1 else b[0]), nrhs))
+    worst, nrhs_done = 0.0, 0
+    for t, nrhs in tickets:
+        st, x, info = srv.wait(t, timeout=3600)
+        if st != dd.DONE:
+            raise RuntimeError(f"request {t} ended in state {st}")
+        worst = max(worst, max(i["true_rel_residual"] for i in info))
+        nrhs_done += nrhs
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    # plain FP64 GPU solves: one per lattice size, scaled to the mix
+    kw = dict(tol=1e-10, restart=16, sweeps=4, mr_steps=4, max_iter=3000, inner_reduction=0.0)
+    t64 = {}
+    for si, d in enumerate(sizes):
+        fi = [i for i, (dd_, _) in enumerate(fields) if dd_ == d][0]
+        op64 = op_for(fi, 1, dd.F64)
+        t64[si], _ = _solve_rate(op64, synth.gaussian_spinor(int(np.prod(d)), 9), kw)
+    fp64_seconds = sum(t64[[s for s, dd_ in enumerate(sizes) if dd_ == fields[fi][0]][0]] * nrhs
+                       for _, fi, _, nrhs, _ in reqs)
+    out = {"mode": "serve", "requests": nreq, "offered_req_per_s": rate, "rhs": nrhs_done,
+           "wall_s": wall, "achieved_req_per_s": nreq / wall, "rhs_per_s": nrhs_done / wall,
+           "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "max_true_rel_residual": worst,
+           "plain_fp64_seconds_per_rhs": {f"{'x'.join(map(str, d))}": t64[i] for i, d in enumerate(sizes)},
+           "plain_fp64_rhs_per_s_same_mix": nrhs_done / fp64_seconds,
+           "speedup_vs_plain_fp64": (nrhs_done / wall) / (nrhs_done / fp64_seconds)}
+    print(json.dumps(out), flush=True)
+    for o in ops.values():
+        o.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,8 +548,10 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],
-                    help="kernels: short kernel loop for profiler captures (no contract line)")
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "batched", "serve"],
+                    help="kernels: short kernel loop for profiler captures; batched: the 24-source "
+                         "48^3x96 workload; serve: the Poisson request stream (no contract line)")
+    ap.add_argument("--requests", type=int, default=40, help="requests in --mode serve")
     ap.add_argument("--solve-iters", type=int, default=20, help="iteration cap of the solve in --mode kernels")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -403,6 +560,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.mode == "kernels":
         run_kernels(args)
+    elif args.mode == "batched":
+        run_batched(args)
+    elif args.mode == "serve":
+        run_serve(args)
     elif args.impl == "reference":
         run_reference(args, rank)
     else:
