@@ -207,6 +207,22 @@ def config_of(wl):
             "l2": "inputs larger than L2 (operator fields 1.8 GB, each vector 0.2-0.4 GB)"}
 
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput: all ranks' units over the slowest rank's time
+    (each rank solves its own replica; there is no exchange between GPUs)."""
+    return world * units_per_rank / seconds_max
+
+
 def ev_time(fn, reps, stream):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -281,13 +297,10 @@ def run_ours(args, rank, world):
         e1.record(stream)
         e1.synchronize()
     launches = L.dd_kernel_launches() - l0
-    total_ms = e0.elapsed_time(e1)
+    total_ms = max_over_ranks(e0.elapsed_time(e1), dist)
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
-    value = world * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(args.steps, world, total_ms / 1e3)
 
     # end to end through dd_solve with pinned host buffers
     bh = torch.from_numpy(b.view(np.float64).reshape(-1).copy()).pin_memory()
@@ -299,11 +312,7 @@ def run_ours(args, rank, world):
     t0 = time.perf_counter()
     for _ in range(max(1, args.steps // 2)):
         op.solve(bh_np, xh_np, **kw)
-    e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / max(1, args.steps // 2), dist)
 
     peaks = measured_peaks()
     real_b = {dd.F64: 8, dd.F32: 4, dd.F16: 2, dd.BF16: 2}
@@ -340,7 +349,7 @@ def run_ours(args, rank, world):
                    "hbm_peak_gbs": peaks["hbm_gbs"], "peak_source": peaks["src"]},
         "roofline": dominant,
         "roofline_other": roofline_dslash if dominant is roofline_sap else roofline_sap,
-        "e2e": {"value": world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": V * 24 * 8,
+        "e2e": {"value": whole_job_rate(1, world, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": V * 24 * 8,
                 "d2h_bytes_per_step": V * 24 * 8},
         "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
         "clocks": clocks,

@@ -19,6 +19,7 @@
 // {2h, 2h+1}; the two halves exchange partial hop sums through shared memory.
 // With Vh = block sites / 2 a multiple of 32, h is warp-uniform, so the
 // per-direction code never diverges inside a warp.
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -34,6 +35,11 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// bulk prefetch of `bytes` (multiple of 16, 16-byte aligned) into L2
+__device__ __forceinline__ void prefetch_l2(const void *gmem, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
 }
 
 // cooperative async copy of `bytes` (multiple of 16) from global to shared
@@ -229,18 +235,39 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g, const void *__re
   const int Vh = g.Vh, Vb = g.Vb;
   const int h = threadIdx.x / Vh, j = threadIdx.x - h * Vh;
 
-  // the blockIdx.x-th block of this colour: blocks 2i and 2i+1 differ in colour
-  int b = 2 * blockIdx.x;
-  {
-    int bc[4];
-    block_coords(g, b, bc);
-    if (((bc[0] + bc[1] + bc[2] + bc[3]) & 1) != colour) b += 1;
-  }
-
   cpx<C> *rho = (cpx<C> *)smem;   // MR residual on odd sites (then e_o)
   cpx<C> *te = rho + 12 * Vh;     // even-site temporary
   cpx<C> *xch = te + 12 * Vh;     // partial-sum exchange between thread halves
   C *red = (C *)(xch + 12 * Vh);
+
+  // Work items: (block of this colour, right-hand-side tile), block fastest.
+  // A CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...; while it works
+  // on one, the next one's operator tiles and fields are prefetched into L2.
+  const int nbc = g.nblocks / 2;
+  const int nitems = nbc * ((rp.n + tile - 1) / tile);
+  // the i-th block of this colour: blocks 2i and 2i+1 differ in colour
+  auto block_of = [&](int bi) {
+    int bb = 2 * bi, bc[4];
+    block_coords(g, bb, bc);
+    return (((bc[0] + bc[1] + bc[2] + bc[3]) & 1) != colour) ? bb + 1 : bb;
+  };
+#pragma unroll 1
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+  const int b = block_of(item % nbc), rt = item / nbc;
+  if (threadIdx.x == 0 && item + (int)gridDim.x < nitems) {
+    const int nitem = item + gridDim.x, nb = block_of(nitem % nbc), nrt = nitem / nbc;
+    prefetch_l2((const P *)links + (size_t)nb * 36 * Vb, 36u * Vb * sizeof(P));
+    prefetch_l2((const P *)clov + (size_t)nb * 36 * Vb, 36u * Vb * sizeof(P));
+    prefetch_l2((const P *)cinv + (size_t)nb * 36 * Vh, 36u * Vh * sizeof(P));
+    constexpr int NC = spinor_chunks<S>();
+    for (int q = 0; q < tile; q++) {
+      const int r = nrt * tile + q;
+      if (r >= rp.n) break;
+      const size_t off = (size_t)nb * NC * Vb * 16;
+      prefetch_l2((const char *)rp.in[r] + off, NC * Vb * 16u);
+      if (!self_zero) prefetch_l2((const char *)rp.out[r] + off, NC * Vb * 16u);
+    }
+  }
 
   Tile<P> Lt, Ao, Ai;
   if constexpr (STAGE) {
@@ -266,7 +293,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g, const void *__re
   // right-hand sides blockIdx.y * tile ... share the staged tiles
 #pragma unroll 1
   for (int rr = 0; rr < tile; rr++) {
-    const int r = blockIdx.y * tile + rr;
+    const int r = rt * tile + rr;
     if (r >= rp.n) break;
     const void *bf = rp.in[r];
     void *xf = rp.out[r];
@@ -409,10 +436,12 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g, const void *__re
     }
     __syncthreads();   // shared vectors are reused by the next right-hand side
   }
+  }  // work items
 }
 
 template <typename S, bool STAGE, int MINB, int NT = 256>
-int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, int tile, cudaStream_t st) {
+int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, int tile, bool persistent,
+          cudaStream_t st) {
   size_t smem = SapSmem<S>::bytes(g, STAGE);
   auto kern = k_sap_phase<S, STAGE, MINB, NT>;
   // raise the kernel's dynamic shared-memory limit once (never during a capture)
@@ -425,7 +454,16 @@ int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtr
       raised = 227 * 1024;
     }
   }
-  dim3 grid(g.nblocks / 2, (rp.n + tile - 1) / tile);
+  const int nitems = g.nblocks / 2 * ((rp.n + tile - 1) / tile);
+  int grid = nitems;
+  if (persistent) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, g.Vb, smem);
+    if (occ < 1) occ = 1;
+    grid = std::min(nitems, sms * occ);
+  }
   for (int sw = 0; sw < p.sweeps; sw++)
     for (int colour = 0; colour < 2; colour++) {
       // with x = 0 on entry: the first phase sees x = 0 everywhere, the
@@ -522,14 +560,16 @@ int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const
     for (int c : cand)
       if (c <= rp.n) tiles[nt++] = c;
   }
+  // variant k: layout k % nl, RHS tile (k / nl) % nt, persistent grid if k >= nl * nt
   auto run = [&](int k) {
-    const int layout = layouts[k % nl], tile = tiles[k / nl];
+    const int layout = layouts[k % nl], tile = tiles[(k / nl) % nt];
+    const bool pers = k >= nl * nt;
     switch (layout) {
-      case 1: return sap_t<S, true, 2>(g, f, p, rp, tile, st);
-      case 2: return sap_t<S, false, 2>(g, f, p, rp, tile, st);
-      case 3: return sap_t<S, true, 1, 512>(g, f, p, rp, tile, st);
-      case 4: return sap_t<S, false, 1, 512>(g, f, p, rp, tile, st);
-      default: return sap_t<S, true, 1>(g, f, p, rp, tile, st);
+      case 1: return sap_t<S, true, 2>(g, f, p, rp, tile, pers, st);
+      case 2: return sap_t<S, false, 2>(g, f, p, rp, tile, pers, st);
+      case 3: return sap_t<S, true, 1, 512>(g, f, p, rp, tile, pers, st);
+      case 4: return sap_t<S, false, 1, 512>(g, f, p, rp, tile, pers, st);
+      default: return sap_t<S, true, 1>(g, f, p, rp, tile, pers, st);
     }
   };
   int k = 0;
@@ -537,7 +577,7 @@ int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const
                     std::to_string(p.mr_steps) + "," + std::to_string(p.rhs_tile);
   // x is pure output when x_is_zero, so trial runs leave the same result
   if (p.x_is_zero) {
-    int rc = tuned_variant(key, nl * nt, run, st, &k);
+    int rc = tuned_variant(key, 2 * nl * nt, run, st, &k);
     if (rc) return rc;
   } else {
     int c = tune_lookup(key);

@@ -4,7 +4,8 @@
 // caller's stream) and caches the fastest; later calls reuse the choice.
 // Tuning synchronises the stream, so it is skipped (variant 0 is used) while
 // the stream is being captured into a CUDA graph. DD_TUNE=0 in the
-// environment disables tuning; DD_TUNE_VARIANT=<k> forces variant k.
+// environment disables tuning; DD_TUNE_VARIANT=<k> forces variant k;
+// DD_TUNE_VERBOSE=1 prints every variant's time to stderr.
 #include <cstdlib>
 #include <map>
 #include <mutex>
@@ -56,6 +57,8 @@ int tuned_variant(const std::string &key, int nvariants, const std::function<int
   DD_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_v = 0, rc = DD_OK;
+  const char *verbose = getenv("DD_TUNE_VERBOSE");
+  std::string report;
   for (int v = 0; v < nvariants && rc == DD_OK; v++) {
     if ((rc = run(v))) break;
     cudaEventRecord(e0, st);
@@ -65,6 +68,7 @@ int tuned_variant(const std::string &key, int nvariants, const std::function<int
     rc = cuda_fail(cudaEventSynchronize(e1), "tune");
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
+    if (verbose) report += " v" + std::to_string(v) + "=" + std::to_string(ms / 3) + "ms";
     if (ms < best) {
       best = ms;
       best_v = v;
@@ -73,6 +77,7 @@ int tuned_variant(const std::string &key, int nvariants, const std::function<int
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
+  if (verbose) fprintf(stderr, "dd tune %s:%s -> v%d\n", key.c_str(), report.c_str(), best_v);
   std::lock_guard<std::mutex> lk(g_mu);
   g_cache[key] = best_v;
   *chosen = best_v;
