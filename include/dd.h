@@ -77,6 +77,7 @@ typedef struct dd_lattice_s *dd_lattice_t;
 typedef struct dd_gauge_s *dd_gauge_t;
 typedef struct dd_op_s *dd_op_t;
 typedef struct dd_server_s *dd_server_t;
+typedef struct dd_mg_s *dd_mg_t;
 
 /* Library version string, never NULL. */
 const char *dd_version(void);
@@ -164,6 +165,8 @@ typedef struct {
                              (0: run to tol; mixed precision uses ~1e-5)            */
   int where;            /* DD_HOST or DD_DEVICE for b and x                          */
   int use_x0;           /* 1: x holds the initial guess; 0: start from x = 0         */
+  dd_mg_t mg;           /* NULL: precondition with `sap`; else the two-level
+                           preconditioner of dd_create_mg (same operator)          */
 } dd_solve_params;
 
 typedef struct {
@@ -185,6 +188,40 @@ typedef struct {
  * respect to the host; work runs on `stream`. */
 int dd_solve(dd_op_t op, const dd_solve_params *p, const double *b, double *x, int nrhs,
              dd_solve_info *info, void *stream);
+
+/* ------------------------------------------------------- two-level multigrid */
+
+typedef struct {
+  int n_vectors;        /* test vectors N (1..32); coarse sites carry 2N unknowns          */
+  int setup_iters;      /* smoother applications to each test vector before P is formed    */
+  int coarse_max_iter;  /* coarse GMRES steps per application (1..64, one cycle from 0)    */
+  double coarse_tol;    /* coarse GMRES stops once its residual estimate falls by this     */
+  dd_sap_params smoother; /* Schwarz post-smoother (and the setup's smoother)              */
+} dd_mg_params;
+
+/* Two-level preconditioner of the paper's DD-alpha-AMG (Sec. 1; its
+ * fine-level smoother is the Schwarz method of Sec. 3.1): aggregates are the
+ * lattice's Schwarz blocks; the test vectors (host, N canonical FP64 spinor
+ * fields [N][V][4][3][2], e.g. seeded random fields) are each smoothed by
+ * `setup_iters` Schwarz applications, then orthonormalised per aggregate and
+ * chirality (spins {0,1} / {2,3}) by modified Gram-Schmidt in vector order to
+ * form the interpolation P; the coarse operator is D_c = P^dagger D P (FP32,
+ * nearest-neighbour stencil on the block grid with 2N x 2N blocks). One
+ * application is M r = P e_c + SAP(r - D P e_c) with e_c from GMRES on D_c.
+ * Synchronous; the object keeps a reference on `op`. Blocks of at most 256
+ * sites. */
+int dd_create_mg(dd_op_t op, const dd_mg_params *p, const double *test_vectors_host, dd_mg_t *out);
+
+/* Coarse vectors are [aggregate][chirality h][k] complex FP32 (2 floats),
+ * aggregates in block order (x fastest); dd_mg_coarse_length gives their
+ * number of complex entries. Fine fields are FP32 internal-layout fields. The
+ * calls below use the object's own workspace: one stream at a time.
+ * Asynchronous on `stream`. */
+size_t dd_mg_coarse_length(dd_mg_t mg);
+int dd_mg_restrict(dd_mg_t mg, const void *fine_f32, void *coarse, void *stream);   /* P^dagger r */
+int dd_mg_prolong(dd_mg_t mg, const void *coarse, void *fine_f32, void *stream);    /* P c */
+int dd_mg_coarse_apply(dd_mg_t mg, const void *coarse_in, void *coarse_out, void *stream); /* D_c c */
+int dd_mg_precondition(dd_mg_t mg, const void *r_f32, void *x_f32, void *stream);   /* x = M r */
 
 /* Size of the fixed device scratch array behind dd_solve_noalloc: 64 MiB. */
 #define DD_NOALLOC_SCRATCH_BYTES (64u << 20)

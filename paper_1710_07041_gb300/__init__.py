@@ -41,7 +41,12 @@ class SapParams(ctypes.Structure):
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("sap", SapParams), ("inner_reduction", ctypes.c_double), ("where", ctypes.c_int),
-                ("use_x0", ctypes.c_int)]
+                ("use_x0", ctypes.c_int), ("mg", ctypes.c_void_p)]
+
+
+class MgParams(ctypes.Structure):
+    _fields_ = [("n_vectors", ctypes.c_int), ("setup_iters", ctypes.c_int), ("coarse_max_iter", ctypes.c_int),
+                ("coarse_tol", ctypes.c_double), ("smoother", SapParams)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -95,6 +100,13 @@ EXPORTS = {
                   ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "dd_solve_noalloc": ([ctypes.c_void_p, ctypes.POINTER(SolveParams), ctypes.c_void_p, ctypes.c_void_p,
                           ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "dd_create_mg": ([ctypes.c_void_p, ctypes.POINTER(MgParams), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
+                     ctypes.c_int),
+    "dd_mg_coarse_length": ([ctypes.c_void_p], ctypes.c_size_t),
+    "dd_mg_restrict": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "dd_mg_prolong": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "dd_mg_coarse_apply": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "dd_mg_precondition": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "dd_server_create": ([ctypes.POINTER(ServerParams), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "dd_submit": ([ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "dd_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
@@ -250,7 +262,7 @@ class Op(Handle):
                "dd_sap_smooth")
 
     def solve(self, b, x=None, tol=1e-10, restart=16, max_iter=1000, sweeps=4, mr_steps=4,
-              inner_reduction=None, use_x0=False, stream=None, raise_on_notconv=True):
+              inner_reduction=None, use_x0=False, stream=None, raise_on_notconv=True, mg=None):
         """Solve D x = b. b: numpy (host) or torch (device) canonical spinors
         (nrhs, V, 4, 3) complex128 or their float64 view. Returns (x, infos)."""
         if inner_reduction is None:
@@ -265,7 +277,7 @@ class Op(Handle):
             if _count_rhs(x, self.lat.V) != nrhs:
                 raise ValueError("x and b hold different numbers of right-hand sides")
         p = SolveParams(tol, restart, max_iter, SapParams(sweeps, mr_steps, 1, 0), inner_reduction,
-                        DEVICE if on_dev else HOST, int(bool(use_x0)))
+                        DEVICE if on_dev else HOST, int(bool(use_x0)), mg.handle if mg is not None else None)
         infos = (SolveInfo * nrhs)()
         rc = lib().dd_solve(self._h, ctypes.byref(p), _ptr(b), _ptr(x), nrhs, infos, _stream_ptr(stream))
         if rc != 0 and not (rc == -4 and not raise_on_notconv):
@@ -317,6 +329,51 @@ def _count_rhs(a, V: int) -> int:
     if reals % (24 * V):
         raise ValueError("spinor array size is not a whole number of lattice fields")
     return reals // (24 * V)
+
+
+class Multigrid(Handle):
+    """Two-level preconditioner (dd_create_mg) built from host test vectors
+    (N, V, 4, 3) complex128 on the lattice's Schwarz blocks as aggregates."""
+
+    def __init__(self, op: Op, test_vectors, setup_iters=3, coarse_max_iter=24, coarse_tol=0.05, sweeps=4,
+                 mr_steps=4):
+        tv = np.ascontiguousarray(test_vectors, dtype=np.complex128)
+        n = tv.size // (12 * op.lat.V)
+        p = MgParams(n, setup_iters, coarse_max_iter, coarse_tol, SapParams(sweeps, mr_steps, 1, 0))
+        h = ctypes.c_void_p()
+        _check(lib().dd_create_mg(op.handle, ctypes.byref(p), _ptr(tv), ctypes.byref(h)), "dd_create_mg")
+        self._h = h.value
+        self.op, self.N = op, n
+        self.coarse_length = int(lib().dd_mg_coarse_length(self._h))
+
+    def new_coarse(self, device="cuda"):
+        import torch
+        return torch.zeros(2 * self.coarse_length, dtype=torch.float32, device=device)
+
+    def restrict(self, fine_f32, coarse, stream=None):
+        _check(lib().dd_mg_restrict(self._h, _ptr(fine_f32), _ptr(coarse), _stream_ptr(stream)), "dd_mg_restrict")
+
+    def prolong(self, coarse, fine_f32, stream=None):
+        _check(lib().dd_mg_prolong(self._h, _ptr(coarse), _ptr(fine_f32), _stream_ptr(stream)), "dd_mg_prolong")
+
+    def coarse_apply(self, cin, cout, stream=None):
+        _check(lib().dd_mg_coarse_apply(self._h, _ptr(cin), _ptr(cout), _stream_ptr(stream)), "dd_mg_coarse_apply")
+
+    def precondition(self, r_f32, x_f32, stream=None):
+        _check(lib().dd_mg_precondition(self._h, _ptr(r_f32), _ptr(x_f32), _stream_ptr(stream)),
+               "dd_mg_precondition")
+
+    @staticmethod
+    def coarse_to_numpy(t, nagg: int, N: int) -> np.ndarray:
+        import torch
+        torch.cuda.synchronize()
+        return t.cpu().numpy().view(np.complex64).astype(np.complex128).reshape(nagg, 2, N)
+
+    @staticmethod
+    def coarse_from_numpy(c: np.ndarray):
+        import torch
+        a = np.ascontiguousarray(c, dtype=np.complex64).reshape(-1)
+        return torch.from_numpy(a.view(np.float32).copy()).cuda()
 
 
 class Server(Handle):

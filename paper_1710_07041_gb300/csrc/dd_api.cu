@@ -40,7 +40,8 @@ int launched(const char *where) {
   return cuda_fail(cudaGetLastError(), where);
 }
 
-enum : int { MAGIC_LAT = 0x4c415431, MAGIC_GAUGE = 0x47415531, MAGIC_OP = 0x4f505231, MAGIC_SERVER = 0x53525631 };
+enum : int { MAGIC_LAT = 0x4c415431, MAGIC_GAUGE = 0x47415531, MAGIC_OP = 0x4f505231, MAGIC_SERVER = 0x53525631,
+             MAGIC_MG = 0x4d475231 };
 
 static bool pow2(int v) { return v >= 2 && (v & (v - 1)) == 0; }
 static int ilog2(int v) {
@@ -78,7 +79,18 @@ static void release_gauge(Gauge *g) {
   }
 }
 
+void release_op(Op *op) {
+  if (!op || --op->refs > 0) return;
+  free_fields(op->f64);
+  free_fields(op->f32);
+  if (op->prec == DD_F16 || op->prec == DD_BF16) free_fields(op->fp);
+  release_gauge(op->gauge);
+  op->magic = 0;
+  delete op;
+}
+
 void destroy_server(void *s);  // dd_server.cu
+void destroy_mg(void *h);      // dd_mg.cu
 int server_magic_ok(void *s);
 
 }  // namespace dd
@@ -234,6 +246,7 @@ int dd_create_op(dd_gauge_t gauge, double c_sw, double m0, int prec, dd_op_t *ou
   }
   if (prec == DD_F64) op->fp = op->f64;
   if (prec == DD_F32) op->fp = op->f32;
+  op->refs = 1;
   ga->refs++;
   *out = (dd_op_t)op;
   return DD_OK;
@@ -282,15 +295,11 @@ void dd_destroy(void *h) {
   } else if (m == MAGIC_GAUGE) {
     release_gauge((Gauge *)h);
   } else if (m == MAGIC_OP) {
-    Op *op = (Op *)h;
-    free_fields(op->f64);
-    free_fields(op->f32);
-    if (op->prec == DD_F16 || op->prec == DD_BF16) free_fields(op->fp);
-    release_gauge(op->gauge);
-    op->magic = 0;
-    delete op;
+    release_op((Op *)h);
   } else if (m == MAGIC_SERVER) {
     destroy_server(h);
+  } else if (m == MAGIC_MG) {
+    destroy_mg(h);
   }
 }
 

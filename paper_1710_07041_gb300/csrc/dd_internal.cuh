@@ -468,7 +468,9 @@ struct Op {
   double c_sw, m0;
   int prec;             // smoother precision
   OpFields f64, f32, fp;  // fp = smoother precision fields (aliases f64/f32 when equal)
+  int refs;             // the caller's handle plus multigrid objects built on it
 };
+void release_op(Op *op);
 
 const OpFields *fields_for(const Op *op, int prec);
 

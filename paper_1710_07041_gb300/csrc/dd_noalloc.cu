@@ -97,6 +97,10 @@ extern "C" int dd_solve_noalloc(dd_op_t opp, const dd_solve_params *p, const dou
   }
   int rc = check_solve_params(p);
   if (rc) return rc;
+  if (p->mg) {
+    set_error("dd_solve_noalloc: the multigrid preconditioner needs workspace; use dd_solve");
+    return DD_EINVAL;
+  }
   const Geom &g = op->lat->g;
   const int m = p->restart;
   cudaStream_t st = (cudaStream_t)stream;

@@ -82,7 +82,7 @@ struct Server {
 
 static bool same_params(const dd_solve_params &a, const dd_solve_params &b) {
   return a.tol == b.tol && a.restart == b.restart && a.max_iter == b.max_iter && a.sap.sweeps == b.sap.sweeps &&
-         a.sap.mr_steps == b.sap.mr_steps && a.inner_reduction == b.inner_reduction;
+         a.sap.mr_steps == b.sap.mr_steps && a.inner_reduction == b.inner_reduction && a.mg == b.mg;
 }
 
 // Called with srv->mu held: a right-hand side of r finished with `status`.
@@ -209,6 +209,8 @@ static void scheduler_main(Server *srv) {
       if (!target && (int)srv->workers.size() < srv->p.max_slots) {
         const Geom &g = r->op->lat->g;
         size_t per = BatchSolver::bytes_per_slot(g, r->op->prec, r->params.restart);
+        if (r->params.mg)
+          per += MgWork::bytes(g, r->op->prec, ((Mg *)r->params.mg)->N, ((Mg *)r->params.mg)->p.coarse_max_iter);
         size_t room = srv->budget > srv->in_use ? srv->budget - srv->in_use : 0;
         int slots = (int)std::min<size_t>((size_t)srv->p.max_batch_rhs, room / per);
         if (slots >= 1) {
@@ -295,6 +297,11 @@ int dd_submit(dd_server_t sh, const dd_request *req, uint64_t *ticket) {
   }
   int rc = check_solve_params(&req->params);
   if (rc) return rc;
+  if (req->params.mg && (((Mg *)req->params.mg)->magic != MAGIC_MG || ((Mg *)req->params.mg)->op != op ||
+                         op->prec == DD_F64)) {
+    set_error("dd_submit: the multigrid object must belong to the request's operator (not FP64)");
+    return DD_EINVAL;
+  }
   const Geom &g = op->lat->g;
   size_t per = BatchSolver::bytes_per_slot(g, op->prec, req->params.restart);
   if (per > srv->budget) {

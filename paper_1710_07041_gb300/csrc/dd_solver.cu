@@ -17,6 +17,7 @@
 // side gets bit-identical results alone or in any mix.
 #include <cmath>
 #include <complex>
+#include <new>
 #include <vector>
 
 #include "dd_solver.cuh"
@@ -69,6 +70,7 @@ BatchSolver::~BatchSolver() {
     void *ptrs[] = {s.Vb, s.Z, s.x, s.b, s.w, s.canon, s.tin, s.tout, s.zt};
     for (void *q : ptrs)
       if (q) cudaFree(q);
+    delete s.mgw;
   }
   if (hdev_) cudaFree(hdev_);
   if (ydev_) cudaFree(ydev_);
@@ -97,6 +99,11 @@ int BatchSolver::init() {
       set_error("solver: out of device memory for %d FGMRES(%d) slots (%zu bytes each)", n, m,
                 bytes_per_slot(op_->lat->g, op_->prec, m));
       return DD_ENOMEM;
+    }
+    if (p_.mg) {
+      s.mgw = new (std::nothrow) MgWork;
+      int rc = s.mgw ? s.mgw->init((const Mg *)p_.mg) : DD_ENOMEM;
+      if (rc) return rc;
     }
     s.H.assign((size_t)(m + 1) * m, 0);
     s.g.assign(m + 1, 0);
@@ -282,23 +289,36 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
   cudaEventRecord(ev_[0], st_);
   RhsPtrs sp_ptrs, d_ptrs;
   sp_ptrs.n = d_ptrs.n = (int)A.size();
-  for (int i = 0; i < (int)A.size(); i++) {
-    Slot *s = A[i];
-    if (df_) rc = blas_.df_to_field(g, (const float *)(s->Vb + 2 * n * s->j), op_->prec, s->tin, sigma_, st_);
-    else rc = launch_convert_field(g, DD_F64, s->Vb + 2 * n * s->j, op_->prec, s->tin, 1, sigma_, st_);
-    if (rc) return rc;
-    sp_ptrs.in[i] = s->tin;
-    sp_ptrs.out[i] = s->tout;
-  }
-  dd_sap_params sp = p_.sap;
-  sp.x_is_zero = 1;
-  if ((rc = launch_sap(g, op_->fp, sp, sp_ptrs, st_))) return rc;
-  for (int i = 0; i < (int)A.size(); i++) {
-    Slot *s = A[i];
-    char *zj = s->Z + (size_t)s->j * fz_;
-    if ((rc = launch_convert_field(g, op_->prec, s->tout, zprec_, zj, 1, 1.0 / sigma_, st_))) return rc;
-    d_ptrs.in[i] = zj;
-    d_ptrs.out[i] = zprec_ == DD_F64 ? (void *)s->w : s->zt;
+  if (p_.mg) {
+    // two-level preconditioner per slot (FP32): z_j = M (sigma v_j) / sigma
+    for (int i = 0; i < (int)A.size(); i++) {
+      Slot *s = A[i];
+      char *zj = s->Z + (size_t)s->j * fz_;
+      if ((rc = blas_.df_to_field(g, (const float *)(s->Vb + 2 * n * s->j), DD_F32, s->zt, sigma_, st_))) return rc;
+      if ((rc = mg_apply((const Mg *)p_.mg, *s->mgw, (const float *)s->zt, (float *)zj, st_, (float)(1.0 / sigma_))))
+        return rc;
+      d_ptrs.in[i] = zj;
+      d_ptrs.out[i] = s->zt;
+    }
+  } else {
+    for (int i = 0; i < (int)A.size(); i++) {
+      Slot *s = A[i];
+      if (df_) rc = blas_.df_to_field(g, (const float *)(s->Vb + 2 * n * s->j), op_->prec, s->tin, sigma_, st_);
+      else rc = launch_convert_field(g, DD_F64, s->Vb + 2 * n * s->j, op_->prec, s->tin, 1, sigma_, st_);
+      if (rc) return rc;
+      sp_ptrs.in[i] = s->tin;
+      sp_ptrs.out[i] = s->tout;
+    }
+    dd_sap_params sp = p_.sap;
+    sp.x_is_zero = 1;
+    if ((rc = launch_sap(g, op_->fp, sp, sp_ptrs, st_))) return rc;
+    for (int i = 0; i < (int)A.size(); i++) {
+      Slot *s = A[i];
+      char *zj = s->Z + (size_t)s->j * fz_;
+      if ((rc = launch_convert_field(g, op_->prec, s->tout, zprec_, zj, 1, 1.0 / sigma_, st_))) return rc;
+      d_ptrs.in[i] = zj;
+      d_ptrs.out[i] = zprec_ == DD_F64 ? (void *)s->w : s->zt;
+    }
   }
   cudaEventRecord(ev_[1], st_);
   // w = D z_j in zprec
@@ -440,11 +460,16 @@ extern "C" int dd_solve(dd_op_t opp, const dd_solve_params *p, const double *b, 
   }
   int rc = check_solve_params(p);
   if (rc) return rc;
+  if (p->mg && (((Mg *)p->mg)->magic != MAGIC_MG || ((Mg *)p->mg)->op != op || op->prec == DD_F64)) {
+    set_error("dd_solve: the multigrid object must belong to this operator (FP32/FP16/BF16 smoother)");
+    return DD_EINVAL;
+  }
   const Geom &g = op->lat->g;
   // as many slots as right-hand sides, bounded by free device memory
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   size_t per = BatchSolver::bytes_per_slot(g, op->prec, p->restart);
+  if (p->mg) per += MgWork::bytes(g, op->prec, ((Mg *)p->mg)->N, ((Mg *)p->mg)->p.coarse_max_iter);
   int slots = nrhs < MAX_RHS ? nrhs : MAX_RHS;
   while (slots > 1 && (size_t)slots * per > free_b / 10 * 9) slots--;
   BatchSolver bs(op, *p, slots, (cudaStream_t)stream);

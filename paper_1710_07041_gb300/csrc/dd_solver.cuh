@@ -5,7 +5,7 @@
 #include <functional>
 #include <vector>
 
-#include "dd_blas.cuh"
+#include "dd_mg.cuh"
 
 namespace dd {
 
@@ -36,6 +36,7 @@ struct Slot {
   char *Z = nullptr;     // m preconditioned fields (zprec)
   double *x = nullptr, *b = nullptr, *w = nullptr, *canon = nullptr;
   void *tin = nullptr, *tout = nullptr, *zt = nullptr;
+  MgWork *mgw = nullptr;   // coarse-solve workspace when preconditioning with multigrid
 };
 
 // FGMRES(m) right-preconditioned by SAP over a batch of right-hand sides that
