@@ -461,6 +461,69 @@ def run_batched(args):
     print(json.dumps(out), flush=True)
 
 
+# two-level configuration (DD-alpha-AMG style, Sec. 1): test vectors, their
+# smoothing iterations, coarse GMRES steps and tolerance, Schwarz post-smoother
+MG = {"n_vectors": 16, "setup_iters": 6, "coarse_max_iter": 24, "coarse_tol": 0.05, "sweeps": 3, "mr_steps": 4,
+      "tv_seed": 7000}
+
+
+def run_mg(args):
+    """Two-level preconditioner on the benchmark workload: SAP-FGMRES against
+    FGMRES preconditioned by the aggregation coarse-grid correction plus
+    Schwarz post-smoothing, both to 1e-10 (FP64 true residual). Reports the
+    setup time, solve times and iterations, and after how many solves the
+    setup has paid for itself."""
+    import torch
+
+    import paper_1710_07041_gb300 as dd
+
+    wl = synth.WORKLOADS[args.workload]
+    prec = {"f32": dd.F32, "f16": dd.F16, "bf16": dd.BF16, "f64": dd.F64}[args.prec]
+    U, b = setup_problem(wl)
+    lat = dd.Lattice(wl["dims"], wl["block"])
+    gauge = dd.Gauge(lat, U)
+    op = dd.Op(gauge, wl["c_sw"], wl["m0"], prec)
+    V = lat.V
+    bd = torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda()
+    xd = torch.zeros_like(bd)
+    kw = dict(tol=1e-10, restart=wl["restart"], sweeps=wl["sweeps"], mr_steps=wl["mr_steps"], max_iter=3000)
+    reps = max(1, args.steps)
+
+    def timed(fn):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            info = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps, info
+
+    t_sap, (_, info_sap) = timed(lambda: op.solve(bd, xd, **kw))
+    tv = np.stack([synth.gaussian_spinor(V, MG["tv_seed"] + k) for k in range(MG["n_vectors"])])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mg = dd.Multigrid(op, tv, setup_iters=MG["setup_iters"], coarse_max_iter=MG["coarse_max_iter"],
+                      coarse_tol=MG["coarse_tol"], sweeps=MG["sweeps"], mr_steps=MG["mr_steps"])
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    t_mg, (_, info_mg) = timed(lambda: op.solve(bd, xd, mg=mg, **kw))
+    mg.close()
+    op.close()
+    gauge.close()
+    lat.close()
+    i0, i1 = info_sap[0], info_mg[0]
+    out = {"mode": "mg", "workload": args.workload, "smoother_dtype": args.prec, "tol": 1e-10, "mg": MG,
+           "sap_fgmres": {"ms_per_solve": t_sap * 1e3, "solves_per_s": 1 / t_sap, "iterations": int(i0["iterations"]),
+                          "true_rel_residual": i0["true_rel_residual"]},
+           "two_level": {"ms_per_solve": t_mg * 1e3, "solves_per_s": 1 / t_mg, "iterations": int(i1["iterations"]),
+                         "true_rel_residual": i1["true_rel_residual"], "setup_s": t_setup,
+                         "ms_preconditioner": i1["ms_sap"], "ms_orth": i1["ms_orth"], "ms_dirac": i1["ms_dirac"]},
+           "speedup_per_solve": t_sap / t_mg,
+           "break_even_solves": (t_setup / (t_sap - t_mg)) if t_sap > t_mg else None}
+    print(json.dumps(out), flush=True)
+
+
 def run_serve(args):
     """Served stream: Poisson arrivals at 200 req/s over lattices 16^3x32,
     24^3x48 and 32^3x64 (equal mix), 1-12 right-hand sides each, on 8 resident
@@ -557,9 +620,10 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "batched", "serve"],
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "batched", "serve", "mg"],
                     help="kernels: short kernel loop for profiler captures; batched: the 24-source "
-                         "48^3x96 workload; serve: the Poisson request stream (no contract line)")
+                         "48^3x96 workload; serve: the Poisson request stream; mg: two-level "
+                         "preconditioner against SAP alone (no contract line)")
     ap.add_argument("--requests", type=int, default=40, help="requests in --mode serve")
     ap.add_argument("--solve-iters", type=int, default=20, help="iteration cap of the solve in --mode kernels")
     args = ap.parse_args()
@@ -573,6 +637,8 @@ def main():
         run_batched(args)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "mg":
+        run_mg(args)
     elif args.impl == "reference":
         run_reference(args, rank)
     else:

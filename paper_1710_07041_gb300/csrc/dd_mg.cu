@@ -29,16 +29,23 @@ __device__ __forceinline__ int colour16(const Geom &g, int b) {
   return (bc[0] & 1) | ((bc[1] & 1) << 1) | ((bc[2] & 1) << 2) | ((bc[3] & 1) << 3);
 }
 
-// coarse neighbour of block a in stencil direction d (0 self, 1+2mu +mu, 2+2mu -mu)
+// coarse neighbour of block a in stencil direction d (0 self, 1+2mu +mu, 2+2mu -mu);
+// the direction is selected by an unrolled loop so that no Geom array is
+// indexed at run time (which would copy the kernel parameter to local memory)
 __device__ __forceinline__ int coarse_nbr(const Geom &g, int a, int d) {
   if (d == 0) return a;
   const int mu = (d - 1) >> 1, dir = (d & 1) ? +1 : -1;
-  int bc[4];
-  block_coords(g, a, bc);
-  int v = bc[mu] + dir;
-  if (v < 0) v += g.nb[mu];
-  if (v >= g.nb[mu]) v -= g.nb[mu];
-  return a + (v - bc[mu]) * g.bstride[mu];
+  int res = a;
+#pragma unroll
+  for (int m = 0; m < 4; m++)
+    if (m == mu) {
+      const int bcm = (a / g.bstride[m]) % g.nb[m];
+      int v = bcm + dir;
+      if (v < 0) v += g.nb[m];
+      if (v >= g.nb[m]) v -= g.nb[m];
+      res = a + (v - bcm) * g.bstride[m];
+    }
+  return res;
 }
 
 __device__ __forceinline__ float2 cfma_c(float2 a, float2 b, float2 acc) {  // acc += conj(a) b
@@ -56,8 +63,8 @@ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {  // acc
 // fields V: out[(h * N + k)] of this CTA's aggregate, optionally only over the
 // sites of one face (face = 2 mu + side, side 1 = upper; -1 = all sites).
 // Returns through smem; thread t < 2N writes result t to dst[t * dst_stride].
-template <int NMAX>
-__device__ void restrict_block(const Geom &g, int b, const float *V, size_t fstride, int N, const float *in, int face,
+template <int NMAX, typename SV>
+__device__ void restrict_block(const Geom &g, int b, const void *V, size_t fbytes, int N, const float *in, int face,
                                float2 *dst, int dst_stride) {
   __shared__ float2 red[MG_TPB / 32][2 * NMAX];
   const int s = threadIdx.x;
@@ -79,7 +86,7 @@ __device__ void restrict_block(const Geom &g, int b, const float *V, size_t fstr
       for (int k = 0; k < NMAX; k++) {
         if (k < N) {
           Spinor<float> v;
-          load_spinor<float, float>(V + k * fstride, g, b, s, v);
+          load_spinor<SV, float>((const char *)V + k * fbytes, g, b, s, v);
           float2 up = make_float2(0.f, 0.f), dn = make_float2(0.f, 0.f);
 #pragma unroll
           for (int c = 0; c < 6; c++) {
@@ -118,10 +125,11 @@ __device__ void restrict_block(const Geom &g, int b, const float *V, size_t fstr
   __syncthreads();
 }
 
+// restriction with the FP16 interpolation fields
 template <int NMAX>
-__global__ void __launch_bounds__(MG_TPB) k_restrict(Geom g, const float *V, size_t fstride, int N, const float *in,
+__global__ void __launch_bounds__(MG_TPB) k_restrict(Geom g, const __half *V, size_t fbytes, int N, const float *in,
                                                     float2 *out) {
-  restrict_block<NMAX>(g, blockIdx.x, V, fstride, N, in, -1, out + (size_t)blockIdx.x * 2 * N, 1);
+  restrict_block<NMAX, __half>(g, blockIdx.x, V, fbytes, N, in, -1, out + (size_t)blockIdx.x * 2 * N, 1);
 }
 
 // Column (h', j) of D_c for aggregates coupled to colour class c16: w = D u
@@ -136,11 +144,12 @@ __global__ void __launch_bounds__(MG_TPB) k_restrict_dc(Geom g, const float *V, 
   const int n2 = 2 * N;
   float2 *base = Dc + (size_t)a * 9 * n2 * n2;
   if (diff == 0) {
-    restrict_block<NMAX>(g, a, V, fstride, N, w, -1, base + (size_t)col * n2, 1);
+    restrict_block<NMAX, float>(g, a, V, fstride * 4, N, w, -1, base + (size_t)col * n2, 1);
   } else if ((diff & (diff - 1)) == 0) {
     const int mu = __ffs(diff) - 1;
-    restrict_block<NMAX>(g, a, V, fstride, N, w, 2 * mu + 1, base + ((size_t)(1 + 2 * mu) * n2 + col) * n2, 1);
-    restrict_block<NMAX>(g, a, V, fstride, N, w, 2 * mu, base + ((size_t)(2 + 2 * mu) * n2 + col) * n2, 1);
+    restrict_block<NMAX, float>(g, a, V, fstride * 4, N, w, 2 * mu + 1,
+                                base + ((size_t)(1 + 2 * mu) * n2 + col) * n2, 1);
+    restrict_block<NMAX, float>(g, a, V, fstride * 4, N, w, 2 * mu, base + ((size_t)(2 + 2 * mu) * n2 + col) * n2, 1);
   }
 }
 
@@ -159,7 +168,7 @@ __global__ void k_column(Geom g, const float *vj, int hp, int c16, float *u) {
 }
 
 // x(site) = sum_k v_k(site) c[a][h(spin)][k]  (+ x when accumulate)
-__global__ void k_prolong(Geom g, const float *V, size_t fstride, int N, const float2 *c, float *x) {
+__global__ void k_prolong(Geom g, const __half *V, size_t fbytes, int N, const float2 *c, float *x) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= g.V) return;
   int b = (int)(t / g.Vb), s = (int)(t - (long long)b * g.Vb);
@@ -169,7 +178,7 @@ __global__ void k_prolong(Geom g, const float *V, size_t fstride, int N, const f
   for (int q = 0; q < 12; q++) o[q] = make_float2(0.f, 0.f);
   for (int k = 0; k < N; k++) {
     Spinor<float> v;
-    load_spinor<float, float>(V + k * fstride, g, b, s, v);
+    load_spinor<__half, float>((const char *)V + k * fbytes, g, b, s, v);
     const float2 cu = cb[k], cd = cb[N + k];
 #pragma unroll
     for (int q = 0; q < 12; q++) o[q] = cfma(make_float2(v.c[q].re, v.c[q].im), q < 6 ? cu : cd, o[q]);
@@ -241,229 +250,388 @@ __global__ void __launch_bounds__(MG_TPB) k_orthonormalise(Geom g, float *V, siz
   }
 }
 
-// y = D_c x: one CTA per aggregate, thread per row (2N <= 64)
-__global__ void k_coarse_apply(Geom g, const float2 *__restrict__ Dc, int N, const float2 *__restrict__ x, float2 *y) {
-  extern __shared__ float2 xs[];   // [9][2N]
-  const int a = blockIdx.x, n2 = 2 * N, row = threadIdx.x;
-  for (int q = threadIdx.x; q < 9 * n2; q += blockDim.x) {
+// Rows of a stored coarse column, padded to a multiple of 4 so that a column
+// is a whole number of 16-byte chunks (4 complex FP16 entries each).
+__host__ __device__ __forceinline__ int dc_rows(int N) { return (2 * N + 3) & ~3; }
+
+// Launch shape of the coarse apply: R = rows/4 chunk lanes times Q column
+// groups, at most 256 threads.
+static inline void coarse_shape(int N, int *R, int *Q) {
+  *R = dc_rows(N) / 4;
+  const int q = 256 / *R;
+  *Q = q < 18 * N ? q : 18 * N;
+}
+
+// y = D_c (s x), s = 1 / *scale (or 1). D_c is stored as complex FP16
+// [a][q = d * 2N + col][row (padded)], summed in FP32. One CTA per aggregate;
+// thread t owns rows 4r..4r+3 (r = t mod R) of the columns q = t / R + k Q and
+// loads them as one 16-byte chunk per column; the Q column groups' partial
+// sums are added in shared memory in a fixed order. With NPRE > 0 a thread
+// issues all its (at most NPRE) chunk loads before gathering x, so the
+// operator stream overlaps the gather. With vnext != null the CTA also stores
+// its own part of s x there (the next Krylov basis vector).
+template <int NPRE>
+__global__ void __launch_bounds__(256) k_coarse_apply(Geom g, const __half2 *__restrict__ Dc, int N, int R, int Q,
+                                                      const float2 *__restrict__ x, float2 *y, const float *scale,
+                                                      float2 *vnext, const int *done) {
+  if (done && *done) return;
+  extern __shared__ float2 sm[];   // xs[9 * 2N], then red[Q][rows]
+  const int a = blockIdx.x, n2 = 2 * N, np = 4 * R, ncol = 9 * n2;
+  const int r = threadIdx.x % R, qg = threadIdx.x / R;
+  const uint4 *D = reinterpret_cast<const uint4 *>(Dc + (size_t)a * ncol * np);
+  uint4 pre[NPRE > 0 ? NPRE : 1];
+#pragma unroll
+  for (int k = 0; k < NPRE; k++) {
+    const int q = qg + k * Q;
+    pre[k] = q < ncol ? __ldcs(D + (size_t)q * R + r) : make_uint4(0, 0, 0, 0);
+  }
+  float2 *xs = sm, *red = sm + ncol;
+  const float sc = scale ? 1.f / *scale : 1.f;
+  for (int q = threadIdx.x; q < ncol; q += blockDim.x) {
     const int d = q / n2, c = q - d * n2;
-    xs[q] = x[(size_t)coarse_nbr(g, a, d) * n2 + c];
+    const float2 v = x[(size_t)coarse_nbr(g, a, d) * n2 + c];
+    xs[q] = make_float2(v.x * sc, v.y * sc);
   }
   __syncthreads();
-  if (row >= n2) return;
-  float2 acc = make_float2(0.f, 0.f);
-  const float2 *D = Dc + (size_t)a * 9 * n2 * n2;
-  for (int d = 0; d < 9; d++)
-    for (int c = 0; c < n2; c++) acc = cfma(D[((size_t)d * n2 + c) * n2 + row], xs[d * n2 + c], acc);
-  y[(size_t)a * n2 + row] = acc;
+  if (vnext)
+    for (int row = threadIdx.x; row < n2; row += blockDim.x) vnext[(size_t)a * n2 + row] = xs[row];
+  float2 acc[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) acc[k] = make_float2(0.f, 0.f);
+  if (NPRE > 0) {
+#pragma unroll
+    for (int k = 0; k < NPRE; k++) {
+      const int q = qg + k * Q;
+      if (q < ncol) {
+        const float2 xq = xs[q];
+        const __half2 *h = reinterpret_cast<const __half2 *>(&pre[k]);
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[c] = cfma(__half22float2(h[c]), xq, acc[c]);
+      }
+    }
+  } else {
+#pragma unroll 4
+    for (int q = qg; q < ncol; q += Q) {
+      const uint4 c4 = __ldcs(D + (size_t)q * R + r);
+      const float2 xq = xs[q];
+      const __half2 *h = reinterpret_cast<const __half2 *>(&c4);
+#pragma unroll
+      for (int c = 0; c < 4; c++) acc[c] = cfma(__half22float2(h[c]), xq, acc[c]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; k++) red[qg * np + 4 * r + k] = acc[k];
+  __syncthreads();
+  for (int row = threadIdx.x; row < n2; row += blockDim.x) {
+    float2 t = make_float2(0.f, 0.f);
+    for (int q = 0; q < Q; q++) {
+      t.x += red[q * np + row].x;
+      t.y += red[q * np + row].y;
+    }
+    y[(size_t)a * n2 + row] = t;
+  }
+}
+
+// FP32 [a][q][2N] -> FP16 [a][q][rows], padding rows zero
+__global__ void k_dc_to_half(const float2 *in, __half2 *out, size_t ncols, int n2, int np) {
+  const size_t n = ncols * np;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t col = e / np;
+    const int row = (int)(e - col * np);
+    const float2 v = row < n2 ? in[col * n2 + row] : make_float2(0.f, 0.f);
+    out[e] = __floats2half2_rn(v.x, v.y);
+  }
 }
 
 // ---------------------------------------------------------- coarse GMRES
 // GMRES(k) on D_c with one cycle of at most `kmax` steps from x = 0 and the
 // control (Givens rotations, convergence test) on the device, so a coarse
 // solve needs no host synchronisation and can be captured in a CUDA graph.
+// Three launches per step: (1) w' = D_c v_j, v_j = w / h_{j,j-1} formed on
+// the fly; (2) the projections H[i][j] = <v_i, w'>; (3) w' -= sum_i H[i][j]
+// v_i with its norm, then the Givens update. Kernels (2) and (3) finish with
+// the last CTA summing all CTAs' partials in a fixed order (deterministic).
 struct CgState {
   int j, done, steps;
-  double bnorm, tol;
-  double2 H[65 * 64];
-  double2 g[65];
-  double cs[64];
-  double2 sn[64];
-  double2 y[64];
-  double hn;
+  unsigned count;          // CTAs finished in the current reduction
+  float bnorm, tol, hn;
+  float2 H[65 * 64];       // H[i * 64 + j]
+  float2 g[65];
+  float cs[64];
+  float2 sn[64];
+  float2 y[64];
 };
 
-constexpr int CG_BLK = 128;   // reduction CTAs for coarse vector norms / updates
-constexpr int CG_CHUNKS = 32; // CTAs per coarse dot product
+constexpr int CG_GRID = 1024;   // maximum CTAs of the start and final update
+constexpr int CG_EPT = 4;       // float4 per thread in a projection
+constexpr int CG_ROWS = 4;      // basis vectors per projection CTA
 
-// partial[i][chunk] = this CTA's part of <v_i, w>, i = blockIdx.y < k
-__global__ void __launch_bounds__(256) k_cg_dots(const float2 *Vc, size_t n, const float2 *w, double2 *partial,
-                                                 const CgState *st) {
-  if (st->done) return;
-  __shared__ double2 red[8];
-  const int i = blockIdx.y;
-  double2 acc = make_double2(0, 0);
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const float2 we = w[e], v = Vc[i * n + e];
-    acc.x += (double)(v.x * we.x + v.y * we.y);
-    acc.y += (double)(v.x * we.y - v.y * we.x);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-  }
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+static inline int cg_grid(size_t n) {
+  const size_t b = (n + 255) / 256;
+  return (int)(b < CG_GRID ? (b ? b : 1) : CG_GRID);
+}
+// CTAs per projection row; CTAs of the update (one float4 per thread)
+static inline int cg_chunks(size_t n) { return (int)((n / 2 + 256 * CG_EPT - 1) / (256 * CG_EPT)); }
+static inline int cg_upd_grid(size_t n) { return (int)((n / 2 + 255) / 256); }
+static inline int cg_partials(size_t n) { return cg_upd_grid(n) > CG_GRID ? cg_upd_grid(n) : CG_GRID; }
+
+// is this CTA the last of the grid to arrive? (after its partial is stored)
+__device__ __forceinline__ bool last_cta(unsigned *count, unsigned total) {
+  __shared__ bool last;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double2 t = make_double2(0, 0);
-    for (int q = 0; q < (int)(blockDim.x >> 5); q++) {
-      t.x += red[q].x;
-      t.y += red[q].y;
-    }
-    partial[(size_t)i * CG_CHUNKS + blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(count, 1u) == total - 1;
   }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
 }
 
-// H[.., j] = sum of partials (fixed order); k = j + 1 projections
-__global__ void k_cg_hcol(const double2 *partial, int k, CgState *st) {
+// sum over a 256-thread CTA in a fixed order; every thread gets the result.
+// The coarse solve reduces in FP32 throughout: FP64 instructions issue at a
+// small fraction of the FP32 rate here, and the coarse solve is an FP32
+// inner solve of a flexible outer method.
+__device__ __forceinline__ float cta_sum(float v) {
+  __shared__ float red[8];
+  __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; q++) t += red[q];
+  return t;
+}
+
+// sum of partial[0 .. P) by a 256-thread CTA, fixed order
+__device__ __forceinline__ float cta_sum_partials(const float *partial, int P) {
+  float t = 0.f;
+  for (int b = threadIdx.x; b < P; b += 256) t += __ldcg(partial + b);
+  return cta_sum(t);
+}
+
+// H[i][j] = <v_i, w> for i <= j. CTA (c, y) covers the rows i = CG_ROWS y ..
+// CG_ROWS y + CG_ROWS - 1 on float4 (two complex) indices
+// c * 256 * CG_EPT + t + 256 u, u < CG_EPT; all its loads are issued together.
+__global__ void __launch_bounds__(256) k_cg_proj(const float2 *Vc, size_t n, const float2 *w, float2 *partial,
+                                                 int chunks, CgState *st) {
   if (st->done) return;
-  const int i = threadIdx.x;
-  if (i >= k) return;
-  double2 t = make_double2(0, 0);
-  for (int b = 0; b < CG_CHUNKS; b++) {
-    t.x += partial[(size_t)i * CG_CHUNKS + b].x;
-    t.y += partial[(size_t)i * CG_CHUNKS + b].y;
+  __shared__ float2 red[8][CG_ROWS];
+  const int k = st->j + 1, i0 = blockIdx.y * CG_ROWS;
+  const size_t n4 = n / 2;
+  const float4 *w4 = reinterpret_cast<const float4 *>(w);
+  const size_t e0 = (size_t)blockIdx.x * 256 * CG_EPT + threadIdx.x;
+  float4 ww[CG_EPT], vv[CG_ROWS][CG_EPT];
+#pragma unroll
+  for (int u = 0; u < CG_EPT; u++) {
+    const size_t e = e0 + 256 * u;
+    ww[u] = e < n4 ? w4[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < CG_ROWS; q++)
+      vv[q][u] = (e < n4 && i0 + q < k) ? reinterpret_cast<const float4 *>(Vc + (size_t)(i0 + q) * n)[e]
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  st->H[i * 64 + st->j] = t;
+#pragma unroll
+  for (int q = 0; q < CG_ROWS; q++) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < CG_EPT; u++) {
+      acc = cfma_c(make_float2(vv[q][u].x, vv[q][u].y), make_float2(ww[u].x, ww[u].y), acc);
+      acc = cfma_c(make_float2(vv[q][u].z, vv[q][u].w), make_float2(ww[u].z, ww[u].w), acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < CG_ROWS && i0 + (int)threadIdx.x < k) {
+    float2 t = make_float2(0.f, 0.f);
+    for (int wq = 0; wq < 8; wq++) {
+      t.x += red[wq][threadIdx.x].x;
+      t.y += red[wq][threadIdx.x].y;
+    }
+    partial[(size_t)(i0 + threadIdx.x) * chunks + blockIdx.x] = t;
+  }
+  if (last_cta(&st->count, gridDim.x * gridDim.y)) {
+    // warp w sums rows i = w, w + 8, ...; lane l the partials l, l + 32, ...
+    const int lane = threadIdx.x & 31, j = st->j;
+    for (int q = threadIdx.x >> 5; q < k; q += 8) {
+      float2 t = make_float2(0.f, 0.f);
+      for (int b = lane; b < chunks; b += 32) {
+        const float2 pv = __ldcg(&partial[(size_t)q * chunks + b]);
+        t.x += pv.x;
+        t.y += pv.y;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+        t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+      }
+      if (lane == 0) st->H[q * 64 + j] = t;
+    }
+    if (threadIdx.x == 0) st->count = 0;
+  }
 }
 
-// w -= sum_i H[i][j] v_i ; partial[blk] = |w|^2
-__global__ void __launch_bounds__(256) k_cg_axpy(const float2 *Vc, size_t n, int k, float2 *w, double *partial,
-                                                 const CgState *st) {
+// finish step j: apply the earlier rotations to column j of H, form the new
+// one, update g and test convergence. Run by one CTA (the last to arrive);
+// the column and the rotations are staged in shared memory. The rotations
+// are FP32 like the coarse vectors (FP64 runs at a small fraction of the
+// FP32 rate here and this chain is serial).
+__device__ void cg_givens(float n2, CgState *st, int kmax) {
+  __shared__ float2 col[65], sn[64];
+  __shared__ float cs[64];
+  const int j = st->j;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = st->H[i * 64 + j];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    cs[i] = st->cs[i];
+    sn[i] = st->sn[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const float hn = sqrtf(n2 > 0.f ? n2 : 0.f);
+    for (int i = 0; i < j; i++) {
+      const float2 a = col[i], c = col[i + 1], s = sn[i];
+      const float ci = cs[i];
+      // a' = cs a + sn c ; c' = -conj(sn) a + cs c
+      col[i] = make_float2(ci * a.x + s.x * c.x - s.y * c.y, ci * a.y + s.x * c.y + s.y * c.x);
+      col[i + 1] = make_float2(-(s.x * a.x + s.y * a.y) + ci * c.x, -(s.x * a.y - s.y * a.x) + ci * c.y);
+    }
+    const float2 a = col[j];
+    const float aa = sqrtf(a.x * a.x + a.y * a.y), rr = sqrtf(aa * aa + hn * hn);
+    float c;
+    float2 s;
+    if (aa == 0.f) {
+      c = 0.f;
+      s = make_float2(1.f, 0.f);
+    } else {
+      const float inv = 1.f / (aa * rr);
+      c = aa * aa * inv;
+      s = make_float2(a.x * hn * inv, a.y * hn * inv);
+    }
+    st->cs[j] = c;
+    st->sn[j] = s;
+    col[j] = make_float2(c * a.x + s.x * hn, c * a.y + s.y * hn);
+    const float2 gj = st->g[j];
+    const float2 g1 = make_float2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+    st->g[j + 1] = g1;
+    st->g[j] = make_float2(c * gj.x, c * gj.y);
+    st->hn = hn;
+    st->steps = j + 1;
+    const float est = sqrtf(g1.x * g1.x + g1.y * g1.y);
+    if (est <= st->tol * st->bnorm || hn == 0.f || j + 1 >= kmax) st->done = 1;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) st->H[i * 64 + j] = col[i];
+  __syncthreads();
+  if (threadIdx.x == 0) st->j = j + 1;
+}
+
+// w -= sum_{i<=j} H[i][j] v_i, then |w|^2 and the Givens step (last CTA).
+// Thread t of CTA c owns float4 (two complex numbers) c * 256 + t.
+__global__ void __launch_bounds__(256) k_cg_update_w(const float2 *Vc, size_t n, float2 *w, float *partial,
+                                                     CgState *st, int kmax) {
   if (st->done) return;
   __shared__ float2 hs[64];
-  __shared__ double red[8];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    const double2 h = st->H[i * 64 + st->j];
-    hs[i] = make_float2((float)h.x, (float)h.y);
-  }
+  const int k = st->j + 1;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) hs[i] = st->H[i * 64 + st->j];
   __syncthreads();
-  double nrm = 0;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    float2 we = w[e];
+  const size_t n4 = n / 2, e = (size_t)blockIdx.x * 256 + threadIdx.x;
+  float nrm = 0.f;
+  if (e < n4) {
+    float4 *w4 = reinterpret_cast<float4 *>(w);
+    float4 we = w4[e];
+#pragma unroll 8
     for (int i = 0; i < k; i++) {
-      const float2 v = Vc[i * n + e], h = hs[i];
+      const float4 v = reinterpret_cast<const float4 *>(Vc + (size_t)i * n)[e];
+      const float2 h = hs[i];
       we.x -= h.x * v.x - h.y * v.y;
       we.y -= h.x * v.y + h.y * v.x;
+      we.z -= h.x * v.z - h.y * v.w;
+      we.w -= h.x * v.w + h.y * v.z;
     }
-    w[e] = we;
-    nrm += (double)(we.x * we.x + we.y * we.y);
+    w4[e] = we;
+    nrm = we.x * we.x + we.y * we.y + we.z * we.z + we.w * we.w;
   }
-  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += red[q];
-    partial[blockIdx.x] = t;
-  }
-}
-
-// one thread: finish step j (Givens, convergence); set hn for the next basis vector
-__global__ void k_cg_givens(const double *partial, int nblk, CgState *st, int kmax) {
-  if (st->done) return;
-  double n2 = 0;
-  for (int b = 0; b < nblk; b++) n2 += partial[b];
-  const int j = st->j;
-  const double hn = sqrt(n2 > 0 ? n2 : 0);
-  for (int i = 0; i < j; i++) {
-    double2 a = st->H[i * 64 + j], c = st->H[(i + 1) * 64 + j];
-    const double cs = st->cs[i];
-    const double2 sn = st->sn[i];
-    // a' = cs a + sn c ; c' = -conj(sn) a + cs c
-    double2 a2 = make_double2(cs * a.x + sn.x * c.x - sn.y * c.y, cs * a.y + sn.x * c.y + sn.y * c.x);
-    double2 c2 = make_double2(-(sn.x * a.x + sn.y * a.y) + cs * c.x, -(sn.x * a.y - sn.y * a.x) + cs * c.y);
-    st->H[i * 64 + j] = a2;
-    st->H[(i + 1) * 64 + j] = c2;
-  }
-  const double2 a = st->H[j * 64 + j];
-  const double aa = sqrt(a.x * a.x + a.y * a.y), rr = sqrt(aa * aa + hn * hn);
-  double cs;
-  double2 sn;
-  if (aa == 0) {
-    cs = 0;
-    sn = make_double2(1, 0);
-  } else {
-    cs = aa / rr;
-    sn = make_double2(a.x / aa * hn / rr, a.y / aa * hn / rr);
-  }
-  st->cs[j] = cs;
-  st->sn[j] = sn;
-  st->H[j * 64 + j] = make_double2(cs * a.x + sn.x * hn, cs * a.y + sn.y * hn);
-  const double2 gj = st->g[j];
-  st->g[j + 1] = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));
-  st->g[j] = make_double2(cs * gj.x, cs * gj.y);
-  st->hn = hn;
-  st->steps = j + 1;
-  const double est = sqrt(st->g[j + 1].x * st->g[j + 1].x + st->g[j + 1].y * st->g[j + 1].y);
-  if (est <= st->tol * st->bnorm || hn == 0 || j + 1 >= kmax) st->done = 1;
-  st->j = j + 1;
-}
-
-// v_{j} = w / hn (the new basis vector), skipped once done
-__global__ void k_cg_next(float2 *Vc, size_t n, const float2 *w, const CgState *st) {
-  if (st->done) return;
-  const float inv = (float)(1.0 / st->hn);
-  float2 *v = Vc + (size_t)st->j * n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const float2 we = w[e];
-    v[e] = make_float2(we.x * inv, we.y * inv);
+  const float tot = cta_sum(nrm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+  if (last_cta(&st->count, gridDim.x)) {
+    const float t = cta_sum_partials(partial, gridDim.x);
+    if (threadIdx.x == 0) st->count = 0;
+    cg_givens(t, st, kmax);
   }
 }
 
-// start: bnorm from partial[0..nblk) (|b|^2), v_0 = b / |b|, g = |b| e_1
-__global__ void k_cg_start(const double *partial, int nblk, CgState *st, double tol) {
-  double n2 = 0;
-  for (int b = 0; b < nblk; b++) n2 += partial[b];
-  st->bnorm = sqrt(n2 > 0 ? n2 : 0);
-  st->tol = tol;
-  st->j = 0;
-  st->steps = 0;
-  st->done = st->bnorm == 0;
-  for (int i = 0; i < 65; i++) st->g[i] = make_double2(0, 0);
-  st->g[0] = make_double2(st->bnorm, 0);
-  st->hn = st->bnorm;
-}
-
-__global__ void k_cg_first(float2 *Vc, size_t n, const float2 *b, const CgState *st) {
-  const float inv = st->bnorm > 0 ? (float)(1.0 / st->bnorm) : 0.f;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const float2 be = b[e];
-    Vc[e] = make_float2(be.x * inv, be.y * inv);
-  }
-}
-
-// |b|^2 partials
-__global__ void __launch_bounds__(256) k_cg_norm(const float2 *b, size_t n, double *partial) {
-  __shared__ double red[8];
-  double nrm = 0;
+// start: |b|^2 partials, then (last CTA) the state; v_0 = b / |b| is formed
+// by the first apply
+__global__ void __launch_bounds__(256) k_cg_start(const float2 *b, size_t n, float *partial, CgState *st, float tol) {
+  float nrm = 0.f;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-    nrm += (double)(b[e].x * b[e].x + b[e].y * b[e].y);
-  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += red[q];
-    partial[blockIdx.x] = t;
+    nrm = fmaf(b[e].x, b[e].x, fmaf(b[e].y, b[e].y, nrm));
+  nrm = cta_sum(nrm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
+  if (last_cta(&st->count, gridDim.x)) {
+    const float t = cta_sum_partials(partial, gridDim.x);
+    for (int i = threadIdx.x; i < 65; i += blockDim.x) st->g[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const float bn = sqrtf(t > 0.f ? t : 0.f);
+      st->count = 0;
+      st->bnorm = bn;
+      st->tol = tol;
+      st->j = 0;
+      st->steps = 0;
+      st->done = bn == 0.f;
+      st->g[0] = make_float2(bn, 0.f);
+      st->hn = bn;
+    }
   }
 }
 
-// back substitution R y = g (one thread)
-__global__ void k_cg_solve(CgState *st) {
-  const int k = st->steps;
-  for (int i = k - 1; i >= 0; i--) {
-    double2 t = st->g[i];
-    for (int l = i + 1; l < k; l++) {
-      const double2 h = st->H[i * 64 + l], yl = st->y[l];
-      t.x -= h.x * yl.x - h.y * yl.y;
-      t.y -= h.x * yl.y + h.y * yl.x;
+// back substitution R y = g, column by column, R staged in shared memory as a
+// packed upper triangle (column l holds rows 0..l at l (l + 1) / 2) and the
+// reciprocals of its diagonal formed in parallel first
+__global__ void __launch_bounds__(64) k_cg_solve(CgState *st) {
+  __shared__ float2 R[64 * 65 / 2], t[64], rd[64];
+  const int k = st->steps, tri = k * (k + 1) / 2;
+  for (int p = threadIdx.x; p < tri; p += blockDim.x) {
+    int l = (int)((sqrtf(8.f * p + 1.f) - 1.f) * 0.5f);   // column of packed index p
+    while (l * (l + 1) / 2 > p) l--;
+    while ((l + 1) * (l + 2) / 2 <= p) l++;
+    R[p] = st->H[(p - l * (l + 1) / 2) * 64 + l];
+  }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    t[i] = st->g[i];
+    const float2 d = st->H[i * 64 + i];
+    const float dd = d.x * d.x + d.y * d.y;
+    rd[i] = dd > 0.f ? make_float2(d.x / dd, -d.y / dd) : make_float2(0.f, 0.f);   // 1 / d
+  }
+  __syncthreads();
+  for (int l = k - 1; l >= 0; l--) {
+    const float2 tl = t[l], r = rd[l];
+    const float2 yl = make_float2(tl.x * r.x - tl.y * r.y, tl.x * r.y + tl.y * r.x);
+    if (threadIdx.x == 0) st->y[l] = yl;
+    for (int i = threadIdx.x; i < l; i += blockDim.x) {
+      const float2 h = R[l * (l + 1) / 2 + i];
+      t[i].x -= h.x * yl.x - h.y * yl.y;
+      t[i].y -= h.x * yl.y + h.y * yl.x;
     }
-    const double2 d = st->H[i * 64 + i];
-    const double dd = d.x * d.x + d.y * d.y;
-    st->y[i] = dd > 0 ? make_double2((t.x * d.x + t.y * d.y) / dd, (t.y * d.x - t.x * d.y) / dd) : make_double2(0, 0);
+    __syncthreads();
   }
 }
 
 // x = sum_i y_i v_i
-__global__ void k_cg_update(const float2 *Vc, size_t n, float2 *x, const CgState *st) {
+__global__ void __launch_bounds__(256) k_cg_update(const float2 *Vc, size_t n, float2 *x, const CgState *st) {
+  __shared__ float2 ys[64];
   const int k = st->steps;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = st->y[i];
+  __syncthreads();
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     float2 acc = make_float2(0.f, 0.f);
-    for (int i = 0; i < k; i++) {
-      const double2 y = st->y[i];
-      acc = cfma(make_float2((float)y.x, (float)y.y), Vc[i * n + e], acc);
-    }
+#pragma unroll 8
+    for (int i = 0; i < k; i++) acc = cfma(ys[i], Vc[i * n + e], acc);
     x[e] = acc;
   }
 }
@@ -487,7 +655,8 @@ __global__ void k_add_scale(const float4 *a, const float4 *b, float4 *y, float s
 
 // ---------------------------------------------------------------- MgWork
 MgWork::~MgWork() {
-  void *p[] = {Vc, w, cb, ce, xf, rf, tf, tin, tout, partial, pnorm, st};
+  for (auto &kv : graphs) cudaGraphExecDestroy(kv.second.first);
+  void *p[] = {Vc, w, w2, cb, ce, xf, rf, tf, tin, tout, partial, pnorm, st};
   for (void *q : p)
     if (q) cudaFree(q);
 }
@@ -498,25 +667,26 @@ int MgWork::init(const Mg *mg) {
   const size_t f32 = (size_t)g.V * 24 * 4, fp = (size_t)g.V * 24 * real_bytes(mg->op->prec);
   const int kmax = mg->p.coarse_max_iter;
   bool ok = cudaMalloc(&Vc, sizeof(float2) * nc * (kmax + 1)) == cudaSuccess &&
-            cudaMalloc(&w, sizeof(float2) * nc) == cudaSuccess && cudaMalloc(&cb, sizeof(float2) * nc) == cudaSuccess &&
+            cudaMalloc(&w, sizeof(float2) * nc) == cudaSuccess && cudaMalloc(&w2, sizeof(float2) * nc) == cudaSuccess &&
+            cudaMalloc(&cb, sizeof(float2) * nc) == cudaSuccess &&
             cudaMalloc(&ce, sizeof(float2) * nc) == cudaSuccess && cudaMalloc(&xf, f32) == cudaSuccess &&
             cudaMalloc(&rf, f32) == cudaSuccess && cudaMalloc(&tf, f32) == cudaSuccess &&
             cudaMalloc(&tin, fp) == cudaSuccess && cudaMalloc(&tout, fp) == cudaSuccess &&
-            cudaMalloc(&partial, sizeof(double2) * CG_CHUNKS * 65) == cudaSuccess &&
-            cudaMalloc(&pnorm, sizeof(double) * CG_BLK) == cudaSuccess &&
+            cudaMalloc(&partial, sizeof(float2) * cg_chunks(nc) * 65) == cudaSuccess &&
+            cudaMalloc(&pnorm, sizeof(float) * cg_partials(nc)) == cudaSuccess &&
             cudaMalloc(&st, sizeof(CgState)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     set_error("mg: out of device memory for the coarse-solve workspace");
     return DD_ENOMEM;
   }
-  return DD_OK;
+  return cuda_fail(cudaMemset(st, 0, sizeof(CgState)), "mg workspace");   // reduction counter = 0
 }
 
 size_t MgWork::bytes(const Geom &g, int prec, int N, int kmax) {
   const size_t nc = (size_t)g.nblocks * 2 * N;
-  return sizeof(float2) * nc * (kmax + 4) + (size_t)g.V * 24 * (4 * 3 + 2 * real_bytes(prec)) +
-         sizeof(double2) * CG_CHUNKS * 65 + sizeof(double) * CG_BLK + sizeof(CgState);
+  return sizeof(float2) * nc * (kmax + 5) + (size_t)g.V * 24 * (4 * 3 + 2 * real_bytes(prec)) +
+         sizeof(float2) * cg_chunks(nc) * 65 + sizeof(float) * cg_partials(nc) + sizeof(CgState);
 }
 
 // ------------------------------------------------------------- operations
@@ -528,9 +698,10 @@ static int restrict_launch(const Mg *mg, const float *in, float2 *out, cudaStrea
     set_error("mg: aggregates of more than %d sites are not supported", MG_TPB);
     return DD_EINVAL;
   }
-  if (mg->N <= 8) k_restrict<8><<<g.nblocks, MG_TPB, 0, st>>>(g, mg->V, fs, mg->N, in, out);
-  else if (mg->N <= 16) k_restrict<16><<<g.nblocks, MG_TPB, 0, st>>>(g, mg->V, fs, mg->N, in, out);
-  else k_restrict<32><<<g.nblocks, MG_TPB, 0, st>>>(g, mg->V, fs, mg->N, in, out);
+  const size_t fb = fs * sizeof(__half);
+  if (mg->N <= 8) k_restrict<8><<<g.nblocks, MG_TPB, 0, st>>>(g, mg->Vh, fb, mg->N, in, out);
+  else if (mg->N <= 16) k_restrict<16><<<g.nblocks, MG_TPB, 0, st>>>(g, mg->Vh, fb, mg->N, in, out);
+  else k_restrict<32><<<g.nblocks, MG_TPB, 0, st>>>(g, mg->Vh, fb, mg->N, in, out);
   return launched("k_restrict");
 }
 
@@ -538,46 +709,52 @@ int mg_restrict(const Mg *mg, const float *in, float2 *out, cudaStream_t st) { r
 
 int mg_prolong(const Mg *mg, const float2 *c, float *out, cudaStream_t st) {
   const Geom &g = mg->op->lat->g;
-  k_prolong<<<(unsigned)((g.V + 127) / 128), 128, 0, st>>>(g, mg->V, (size_t)g.V * 24, mg->N, c, out);
+  k_prolong<<<(unsigned)((g.V + 127) / 128), 128, 0, st>>>(g, mg->Vh, (size_t)g.V * 24 * sizeof(__half), mg->N, c,
+                                                            out);
   return launched("k_prolong");
 }
 
-int mg_coarse_apply(const Mg *mg, const float2 *x, float2 *y, cudaStream_t st) {
+static int coarse_apply_launch(const Mg *mg, const float2 *x, float2 *y, const float *scale, float2 *vnext,
+                               const int *done, cudaStream_t st) {
   const Geom &g = mg->op->lat->g;
-  const int n2 = 2 * mg->N;
-  k_coarse_apply<<<g.nblocks, n2 < 32 ? 32 : n2, sizeof(float2) * 9 * n2, st>>>(g, mg->Dc, mg->N, x, y);
+  int R, Q;
+  coarse_shape(mg->N, &R, &Q);
+  const size_t shm = sizeof(float2) * (18 * (size_t)mg->N + (size_t)Q * 4 * R);
+  const int per = (18 * mg->N + Q - 1) / Q;   // chunks per thread
+  const dim3 grid(g.nblocks), blk(R * Q);
+  if (per <= 4) k_coarse_apply<4><<<grid, blk, shm, st>>>(g, mg->Dc, mg->N, R, Q, x, y, scale, vnext, done);
+  else if (per <= 8) k_coarse_apply<8><<<grid, blk, shm, st>>>(g, mg->Dc, mg->N, R, Q, x, y, scale, vnext, done);
+  else if (per <= 12) k_coarse_apply<12><<<grid, blk, shm, st>>>(g, mg->Dc, mg->N, R, Q, x, y, scale, vnext, done);
+  else k_coarse_apply<0><<<grid, blk, shm, st>>>(g, mg->Dc, mg->N, R, Q, x, y, scale, vnext, done);
   return launched("k_coarse_apply");
 }
 
-// e = GMRES_kmax(D_c, b) from 0 (device-side control)
+int mg_coarse_apply(const Mg *mg, const float2 *x, float2 *y, cudaStream_t st) {
+  return coarse_apply_launch(mg, x, y, nullptr, nullptr, nullptr, st);
+}
+
+// e = GMRES_kmax(D_c, b) from 0 (device-side control, 3 launches per step)
 int mg_coarse_solve(const Mg *mg, MgWork &W, const float2 *b, float2 *e, cudaStream_t st) {
   const size_t n = W.nc;
-  const int kmax = mg->p.coarse_max_iter;
+  const int kmax = mg->p.coarse_max_iter, grid = cg_grid(n);
   CgState *cs = (CgState *)W.st;
-  double *pd = W.pnorm;
-  k_cg_norm<<<CG_BLK, 256, 0, st>>>(b, n, pd);
+  k_cg_start<<<grid, 256, 0, st>>>(b, n, W.pnorm, cs, (float)mg->p.coarse_tol);
   DD_LAUNCHED();
-  k_cg_start<<<1, 1, 0, st>>>(pd, CG_BLK, cs, mg->p.coarse_tol);
-  DD_LAUNCHED();
-  k_cg_first<<<CG_BLK, 256, 0, st>>>(W.Vc, n, b, cs);
-  DD_LAUNCHED();
+  const float2 *src = b;      // v_j = src / hn
+  float2 *wbuf[2] = {W.w, W.w2};
+  int rc;
   for (int j = 0; j < kmax; j++) {
-    int rc = mg_coarse_apply(mg, W.Vc + (size_t)j * n, W.w, st);
-    if (rc) return rc;
-    k_cg_dots<<<dim3(CG_CHUNKS, j + 1), 256, 0, st>>>(W.Vc, n, W.w, W.partial, cs);
+    float2 *wj = wbuf[j & 1];
+    if ((rc = coarse_apply_launch(mg, src, wj, &cs->hn, W.Vc + (size_t)j * n, &cs->done, st))) return rc;
+    k_cg_proj<<<dim3(cg_chunks(n), (j + CG_ROWS) / CG_ROWS), 256, 0, st>>>(W.Vc, n, wj, W.partial, cg_chunks(n), cs);
     DD_LAUNCHED();
-    k_cg_hcol<<<1, 64, 0, st>>>(W.partial, j + 1, cs);
+    k_cg_update_w<<<cg_upd_grid(n), 256, 0, st>>>(W.Vc, n, wj, W.pnorm, cs, kmax);
     DD_LAUNCHED();
-    k_cg_axpy<<<CG_BLK, 256, 0, st>>>(W.Vc, n, j + 1, W.w, pd, cs);
-    DD_LAUNCHED();
-    k_cg_givens<<<1, 1, 0, st>>>(pd, CG_BLK, cs, kmax);
-    DD_LAUNCHED();
-    k_cg_next<<<CG_BLK, 256, 0, st>>>(W.Vc, n, W.w, cs);
-    DD_LAUNCHED();
+    src = wj;
   }
-  k_cg_solve<<<1, 1, 0, st>>>(cs);
+  k_cg_solve<<<1, 64, 0, st>>>(cs);
   DD_LAUNCHED();
-  k_cg_update<<<CG_BLK, 256, 0, st>>>(W.Vc, n, e, cs);
+  k_cg_update<<<grid, 256, 0, st>>>(W.Vc, n, e, cs);
   return launched("k_cg_update");
 }
 
@@ -591,7 +768,7 @@ int mg_add_scale(const float *a, const float *b, float *y, float s, size_t n_flo
 }
 
 // M r: x = scale * (P e_c + SAP(r - D P e_c)), e_c ~ D_c^-1 P^dagger r. r and x: FP32 fields.
-int mg_apply(const Mg *mg, MgWork &W, const float *r, float *x, cudaStream_t st, float scale) {
+static int mg_enqueue(const Mg *mg, MgWork &W, const float *r, float *x, cudaStream_t st, float scale) {
   const Op *op = mg->op;
   const Geom &g = op->lat->g;
   const size_t nf = (size_t)g.V * 24;
@@ -613,6 +790,53 @@ int mg_apply(const Mg *mg, MgWork &W, const float *r, float *x, cudaStream_t st,
   return mg_add_scale(W.xf, W.tf, x, scale, nf, st);
 }
 
+// A preconditioner application is about 3 kmax + 10 launches, most of them
+// small (coarse vectors of 2N complex numbers per aggregate), so from the
+// second application on with the same (r, x, scale) it runs as one CUDA graph
+// captured on that call. The first application of a workspace runs eagerly,
+// so that the autotuner has chosen the fine-grid kernels' variants before any
+// capture. DD_MG_GRAPHS=0 disables the graphs; a stream under capture by the
+// caller, or the legacy stream, gets the launches directly.
+int mg_apply(const Mg *mg, MgWork &W, const float *r, float *x, cudaStream_t st, float scale) {
+  const char *env = getenv("DD_MG_GRAPHS");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cap);
+  if ((env && env[0] == '0') || cap != cudaStreamCaptureStatusNone || st == 0 || !W.warm) {
+    W.warm = true;
+    return mg_enqueue(mg, W, r, x, st, scale);
+  }
+  uint32_t sbits;
+  memcpy(&sbits, &scale, 4);
+  const std::string key = std::to_string((uintptr_t)r) + ":" + std::to_string((uintptr_t)x) + ":" +
+                          std::to_string(sbits);
+  auto it = W.graphs.find(key);
+  if (it != W.graphs.end()) {
+    count_launches((int)it->second.second);
+    return cuda_fail(cudaGraphLaunch(it->second.first, st), "mg graph launch");
+  }
+  cudaGraph_t graph = nullptr;
+  DD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int rc = mg_enqueue(mg, W, r, x, st, scale);
+  cudaError_t e = cudaStreamEndCapture(st, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "mg graph capture");
+  size_t nodes = 0;
+  cudaGraphGetNodes(graph, nullptr, &nodes);
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "mg graph instantiate");
+  if (W.graphs.size() >= 128) {   // bounded: start over when full
+    for (auto &kv : W.graphs) cudaGraphExecDestroy(kv.second.first);
+    W.graphs.clear();
+  }
+  W.graphs[key] = {exec, nodes};
+  return cuda_fail(cudaGraphLaunch(exec, st), "mg graph launch");
+}
+
 // ------------------------------------------------------------------ setup
 static int build_coarse(Mg *mg, cudaStream_t st) {
   const Op *op = mg->op;
@@ -620,27 +844,36 @@ static int build_coarse(Mg *mg, cudaStream_t st) {
   const size_t fs = (size_t)g.V * 24;
   const int N = mg->N, n2 = 2 * N;
   float *u = nullptr, *wv = nullptr;
+  float2 *dcf = nullptr;   // FP32 coarse operator while it is assembled
+  const size_t ndc = (size_t)g.nblocks * 9 * n2 * n2;
   DD_CUDA(cudaMalloc(&u, fs * 4));
-  if (cudaMalloc(&wv, fs * 4) != cudaSuccess) {
+  if (cudaMalloc(&wv, fs * 4) != cudaSuccess || cudaMalloc(&dcf, sizeof(float2) * ndc) != cudaSuccess) {
+    cudaGetLastError();
     cudaFree(u);
+    cudaFree(wv);
     set_error("mg: out of device memory");
     return DD_ENOMEM;
   }
-  int rc = cuda_fail(cudaMemsetAsync(mg->Dc, 0, sizeof(float2) * (size_t)g.nblocks * 9 * n2 * n2, st), "memset");
+  int rc = cuda_fail(cudaMemsetAsync(dcf, 0, sizeof(float2) * ndc, st), "memset");
   for (int c16 = 0; c16 < 16 && rc == DD_OK; c16++)
     for (int col = 0; col < n2 && rc == DD_OK; col++) {
       const int hp = col / N, j = col - hp * N;
       k_column<<<(unsigned)((g.V + 127) / 128), 128, 0, st>>>(g, mg->V + j * fs, hp, c16, u);
       if ((rc = launched("k_column"))) break;
       if ((rc = launch_dirac(g, op->f32, u, wv, 1, st))) break;
-      if (N <= 8) k_restrict_dc<8><<<g.nblocks, MG_TPB, 0, st>>>(g, mg->V, fs, N, wv, mg->Dc, c16, col);
-      else if (N <= 16) k_restrict_dc<16><<<g.nblocks, MG_TPB, 0, st>>>(g, mg->V, fs, N, wv, mg->Dc, c16, col);
-      else k_restrict_dc<32><<<g.nblocks, MG_TPB, 0, st>>>(g, mg->V, fs, N, wv, mg->Dc, c16, col);
+      if (N <= 8) k_restrict_dc<8><<<g.nblocks, MG_TPB, 0, st>>>(g, mg->V, fs, N, wv, dcf, c16, col);
+      else if (N <= 16) k_restrict_dc<16><<<g.nblocks, MG_TPB, 0, st>>>(g, mg->V, fs, N, wv, dcf, c16, col);
+      else k_restrict_dc<32><<<g.nblocks, MG_TPB, 0, st>>>(g, mg->V, fs, N, wv, dcf, c16, col);
       rc = launched("k_restrict_dc");
     }
+  if (rc == DD_OK) {
+    k_dc_to_half<<<1024, 256, 0, st>>>(dcf, mg->Dc, (size_t)g.nblocks * 9 * n2, n2, dc_rows(N));
+    rc = launched("k_dc_to_half");
+  }
   if (rc == DD_OK) rc = cuda_fail(cudaStreamSynchronize(st), "mg setup");
   cudaFree(u);
   cudaFree(wv);
+  cudaFree(dcf);
   return rc;
 }
 
@@ -694,7 +927,22 @@ int mg_setup(Mg *mg, const double *tv_host, cudaStream_t st) {
   if (rc) return rc;
   k_orthonormalise<<<2 * g.nblocks, MG_TPB, 0, st>>>(g, mg->V, fs, N);
   if ((rc = launched("k_orthonormalise"))) return rc;
-  return build_coarse(mg, st);
+  // The interpolation is kept in FP16 (restriction and prolongation read all
+  // N fields per application). The FP32 copy is rounded the same way before
+  // the coarse operator is assembled from it, so D_c = P^dagger D P holds
+  // for the stored P.
+  for (int k = 0; k < N && rc == DD_OK; k++) {
+    float *vk = mg->V + k * fs;
+    __half *hk = mg->Vh + k * fs;
+    if ((rc = launch_convert_field(g, DD_F32, vk, DD_F16, hk, 1, 1.0, st))) break;
+    rc = launch_convert_field(g, DD_F16, hk, DD_F32, vk, 1, 1.0, st);
+  }
+  if (rc == DD_OK) rc = build_coarse(mg, st);
+  if (rc == DD_OK) {   // the FP32 copy is needed by the set-up only
+    cudaFree(mg->V);
+    mg->V = nullptr;
+  }
+  return rc;
 }
 
 }  // namespace dd
@@ -724,9 +972,11 @@ int dd_create_mg(dd_op_t opp, const dd_mg_params *p, const double *tv_host, dd_m
   mg->N = p->n_vectors;
   const size_t n2 = 2 * (size_t)mg->N;
   if (cudaMalloc(&mg->V, (size_t)g.V * 24 * 4 * mg->N) != cudaSuccess ||
-      cudaMalloc(&mg->Dc, sizeof(float2) * (size_t)g.nblocks * 9 * n2 * n2) != cudaSuccess) {
+      cudaMalloc(&mg->Vh, (size_t)g.V * 24 * 2 * mg->N) != cudaSuccess ||
+      cudaMalloc(&mg->Dc, sizeof(__half2) * (size_t)g.nblocks * 9 * n2 * dc_rows(mg->N)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(mg->V);
+    cudaFree(mg->Vh);
     delete mg;
     set_error("dd_create_mg: out of device memory");
     return DD_ENOMEM;
@@ -735,6 +985,7 @@ int dd_create_mg(dd_op_t opp, const dd_mg_params *p, const double *tv_host, dd_m
   if (rc == DD_OK) rc = mg_setup(mg, tv_host, 0);
   if (rc) {
     cudaFree(mg->V);
+    cudaFree(mg->Vh);
     cudaFree(mg->Dc);
     delete mg;
     return rc;
@@ -796,6 +1047,7 @@ namespace dd {
 void destroy_mg(void *h) {
   Mg *mg = (Mg *)h;
   cudaFree(mg->V);
+  cudaFree(mg->Vh);
   cudaFree(mg->Dc);
   mg->magic = 0;
   Op *op = mg->op;

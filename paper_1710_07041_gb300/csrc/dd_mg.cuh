@@ -1,5 +1,9 @@
 // Two-level aggregation multigrid internals (see dd_mg.cu).
 #pragma once
+#include <map>
+#include <string>
+#include <utility>
+
 #include "dd_blas.cuh"
 
 namespace dd {
@@ -11,12 +15,14 @@ struct Mg;
 struct MgWork {
   size_t nc = 0;               // coarse vector length (complex)
   float2 *Vc = nullptr;        // coarse Krylov basis (kmax + 1 vectors)
-  float2 *w = nullptr, *cb = nullptr, *ce = nullptr;
+  float2 *w = nullptr, *w2 = nullptr, *cb = nullptr, *ce = nullptr;
   float *xf = nullptr, *rf = nullptr, *tf = nullptr;   // fine FP32 fields
   void *tin = nullptr, *tout = nullptr;                // smoother-precision fields
-  double2 *partial = nullptr;  // coarse reduction partials
-  double *pnorm = nullptr;
+  float2 *partial = nullptr;   // coarse reduction partials
+  float *pnorm = nullptr;
   void *st = nullptr;          // coarse GMRES control state (device)
+  bool warm = false;           // one eager application done (variants tuned)
+  std::map<std::string, std::pair<cudaGraphExec_t, size_t>> graphs;   // (r, x, scale) -> graph, nodes
   ~MgWork();
   int init(const Mg *mg);
   static size_t bytes(const Geom &g, int prec, int N, int kmax);
@@ -27,8 +33,9 @@ struct Mg {
   Op *op;
   dd_mg_params p;
   int N;                 // test vectors
-  float *V = nullptr;    // N FP32 fields: orthonormal per (aggregate, chirality)
-  float2 *Dc = nullptr;  // coarse operator [aggregate][9][col][row], 2N x 2N blocks
+  float *V = nullptr;    // N FP32 fields: orthonormal per (aggregate, chirality); set-up only
+  __half *Vh = nullptr;  // the same N fields rounded to FP16: the interpolation P
+  __half2 *Dc = nullptr; // coarse operator [aggregate][9][col][row padded to 4], complex FP16
   MgWork work;           // for the dd_mg_* entry points
 };
 

@@ -48,6 +48,7 @@ int tuned_variant(const std::string &key, int nvariants, const std::function<int
   const char *off = getenv("DD_TUNE");
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cap);
+  // under capture the cached choice (looked up above) or variant 0 is used
   if ((off && off[0] == '0') || cap != cudaStreamCaptureStatusNone || nvariants == 1) {
     *chosen = 0;
     return DD_OK;

@@ -1,9 +1,16 @@
 """GPU parity of the two-level multigrid against the FP64 oracle
 (oracle/twolevel.py) on the same seeded test vectors, and the two-level
 SAP-FGMRES solve (true residual by the oracle's operator, fewer iterations
-than the Schwarz preconditioner alone). FP32 bounds: 1e-5 for restriction,
-prolongation and the Galerkin coarse operator, 1e-3 for a whole
-preconditioner application (coarse GMRES in FP32 against FP64)."""
+than the Schwarz preconditioner alone).
+
+The library keeps the interpolation P and the coarse operator D_c in FP16
+(each entry rounded to a relative 2^-11 = 4.9e-4, RMS about 2.8e-4) with FP32
+sums, and assembles D_c from the rounded P. Bounds, as relative L2 errors
+against the oracle's unrounded FP64 P: 2e-3 for restriction and
+prolongation (one factor of P: ~2.8e-4 expected) and for the coarse operator
+(two factors of P plus the rounding of D_c: ~6e-4 expected); 5e-3 for a
+whole preconditioner application, whose 12 coarse GMRES steps run on the
+rounded operator."""
 import numpy as np
 import pytest
 
@@ -36,12 +43,16 @@ def test_restrict_prolong_match_oracle(mgsetup):
     mg.restrict(rf, c)
     got = dd.Multigrid.coarse_to_numpy(c, tl.nagg, tl.N)
     r32 = s.lat.from_field(rf, dd.F32)
-    assert relerr(got, tl.restrict(r32)) <= 1e-5
+    err = relerr(got, tl.restrict(r32))
+    print(f"restrict relerr {err:.3e}")
+    assert err <= 2e-3
     cc = synth.gaussian(tl.nagg * 2 * tl.N, 902).reshape(tl.nagg, 2, tl.N)
     xf = s.lat.new_field(dd.F32)
     mg.prolong(dd.Multigrid.coarse_from_numpy(cc), xf)
     x = s.lat.from_field(xf, dd.F32)
-    assert relerr(x, tl.prolong(cc.astype(np.complex64))) <= 1e-5
+    err = relerr(x, tl.prolong(cc.astype(np.complex64)))
+    print(f"prolong relerr {err:.3e}")
+    assert err <= 2e-3
 
 
 def test_coarse_operator_matches_galerkin(mgsetup):
@@ -50,7 +61,9 @@ def test_coarse_operator_matches_galerkin(mgsetup):
     out = mg.new_coarse()
     mg.coarse_apply(dd.Multigrid.coarse_from_numpy(cc), out)
     got = dd.Multigrid.coarse_to_numpy(out, tl.nagg, tl.N)
-    assert relerr(got, tl.coarse_apply(cc)) <= 1e-5
+    err = relerr(got, tl.coarse_apply(cc))
+    print(f"coarse apply relerr {err:.3e}")
+    assert err <= 2e-3
 
 
 def test_preconditioner_matches_oracle(mgsetup):
@@ -62,7 +75,9 @@ def test_preconditioner_matches_oracle(mgsetup):
     got = s.lat.from_field(xf, dd.F32)
     want = tl.precondition(s.lat.from_field(rf, dd.F32), BLOCK, sweeps=2, nmr=3, coarse_restart=12,
                            coarse_iter=12, coarse_tol=0.0)
-    assert relerr(got, want) <= 1e-3
+    err = relerr(got, want)
+    print(f"preconditioner relerr {err:.3e}")
+    assert err <= 5e-3
 
 
 @pytest.mark.parametrize("prec", [dd.F32, dd.F16])
