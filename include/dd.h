@@ -89,6 +89,22 @@ const char *dd_last_error(void);
  * this process (all threads). */
 uint64_t dd_kernel_launches(void);
 
+/* Diagnostics (no counterpart in the paper): waits for all work on the
+ * current device, then returns DD_OK, or DD_ETIMEOUT if any bounded wait
+ * inside a kernel (the Schwarz kernel's wait for its staged tiles, about one
+ * second of SM clock) has expired since the previous call; a kernel whose
+ * wait expired leaves the blocks it had not finished unsmoothed. Clears the
+ * count. DD_ECUDA if the device reports an error. */
+int dd_device_status(void);
+
+/* Self-test of the kernels' bounded wait (no counterpart in the paper): one
+ * CTA stages 16 bytes by a bulk copy and waits on its barrier. expire == 0:
+ * the copy completes, DD_OK. expire != 0: the barrier is told to expect more
+ * bytes than are copied, the wait expires after about one second, the kernel
+ * raises the flag that dd_device_status reports and returns; DD_OK means the
+ * expiry was observed and the context is still usable. Synchronous. */
+int dd_selftest_wait(int expire);
+
 /* ------------------------------------------------------------------ setup */
 
 /* Lattice geometry and storage tiling. dims {T,Z,Y,X} >= 2 each; block as in

@@ -79,6 +79,8 @@ EXPORTS = {
     "dd_version": ([], ctypes.c_char_p),
     "dd_last_error": ([], ctypes.c_char_p),
     "dd_kernel_launches": ([], ctypes.c_uint64),
+    "dd_device_status": ([], ctypes.c_int),
+    "dd_selftest_wait": ([ctypes.c_int], ctypes.c_int),
     "dd_create_lattice": ([ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                            ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "dd_lattice_volume": ([ctypes.c_void_p], ctypes.c_long),
@@ -433,3 +435,18 @@ class Server(Handle):
 
 def version() -> str:
     return lib().dd_version().decode()
+
+
+def kernel_launches() -> int:
+    return int(lib().dd_kernel_launches())
+
+
+def device_status():
+    """Wait for the device; raise DDError if a bounded in-kernel wait expired
+    since the previous call (dd_device_status)."""
+    _check(lib().dd_device_status(), "dd_device_status")
+
+
+def selftest_wait(expire: bool):
+    """dd_selftest_wait: the bounded in-kernel wait, completing or expiring."""
+    _check(lib().dd_selftest_wait(int(bool(expire))), "dd_selftest_wait")

@@ -105,6 +105,10 @@ const char *dd_last_error(void) { return g_err.c_str(); }
 
 uint64_t dd_kernel_launches(void) { return g_launches.load(); }
 
+int dd_device_status(void) { return device_wait_status(); }
+
+int dd_selftest_wait(int expire) { return wait_selftest(expire); }
+
 int dd_create_lattice(const int dims[4], const int block[4], int antiperiodic_t, dd_lattice_t *out) {
   if (!dims || !block || !out) {
     set_error("dd_create_lattice: null argument");

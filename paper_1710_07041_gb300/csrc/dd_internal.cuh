@@ -498,6 +498,11 @@ int launch_dirac(const Geom &g, const OpFields &f, const void *in, void *out, in
 int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &sp, const RhsPtrs &p, cudaStream_t st);
 int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &sp, const void *b, void *x, int nrhs,
                cudaStream_t st);
+// DD_OK, or DD_ETIMEOUT if a bounded device wait has expired since the last
+// call (waits for the device first; clears the count)
+int device_wait_status();
+// staging-handshake self-test (see dd_selftest_wait)
+int wait_selftest(int expire);
 // spinor precision conversion between two internal layouts, y = scale * x
 int launch_convert_field(const Geom &g, int prec_in, const void *in, int prec_out, void *out, int nrhs, double scale,
                          cudaStream_t st);

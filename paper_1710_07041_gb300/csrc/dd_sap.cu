@@ -27,25 +27,104 @@
 #include "dd_tune.cuh"
 
 namespace dd {
+
+// Number of bounded device waits that expired (read and cleared by
+// dd_device_status).
+__device__ unsigned g_wait_timeouts = 0;
+
+int device_wait_status() {
+  int rc = cuda_fail(cudaDeviceSynchronize(), "device status");
+  if (rc) return rc;
+  unsigned n = 0, zero = 0;
+  if ((rc = cuda_fail(cudaMemcpyFromSymbol(&n, g_wait_timeouts, sizeof(n)), "device status"))) return rc;
+  if (n) {
+    if ((rc = cuda_fail(cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof(zero)), "device status"))) return rc;
+    set_error("%u bounded device wait(s) expired", n);
+    return DD_ETIMEOUT;
+  }
+  return DD_OK;
+}
+
 namespace {
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
 
 // bulk prefetch of `bytes` (multiple of 16, 16-byte aligned) into L2
 __device__ __forceinline__ void prefetch_l2(const void *gmem, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
 }
 
-// cooperative async copy of `bytes` (multiple of 16) from global to shared
-__device__ __forceinline__ void stage(void *dst, const void *src, size_t bytes) {
-  for (size_t o = (size_t)threadIdx.x * 16; o < bytes; o += (size_t)blockDim.x * 16)
-    cp_async16((char *)dst + o, (const char *)src + o);
+// ---- bulk (TMA) staging into shared memory, completion on an mbarrier
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
+}
+// the issuing thread's arrival, announcing `bytes` of bulk copies
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *mbar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+// one bulk copy global -> shared (addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned mbar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// generic-proxy accesses of shared memory before later bulk copies into it
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Bounded wait for phase `parity` of the staging barrier (shared address
+// mbar): about one second of SM clock at most, then false.
+constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;
+__device__ __noinline__ bool mbar_wait_slow(unsigned mbar, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(mbar, parity))
+    if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+  return true;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
+  return mbar_test(mbar, parity) || mbar_wait_slow(mbar, parity);
+}
+// the CTA's wait expired: count it, let thread 0's copies land (bounded)
+__device__ __noinline__ void wait_expired(unsigned mbar, unsigned parity) {
+  if (threadIdx.x == 0) {
+    atomicAdd(&g_wait_timeouts, 1u);
+    mbar_wait_slow(mbar, parity);
+  }
+}
+
+// Self-test of the staging handshake: one 16-byte bulk copy tracked by an
+// mbarrier; with `expire` the barrier is told to expect 16 more bytes than
+// are copied, so its phase never completes and the bounded wait must expire.
+// result: 0 copy landed, 1 wait expired, 2 copy landed with wrong data.
+__global__ void k_wait_selftest(const uint4 *src, int expire, int *result) {
+  __shared__ __align__(16) uint4 buf;
+  __shared__ __align__(8) uint64_t mbar;
+  const unsigned m = smem_u32(&mbar);
+  if (threadIdx.x == 0) mbar_init(&mbar);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    fence_proxy_async();
+    mbar_arrive_expect(&mbar, expire ? 32u : 16u);
+    bulk_g2s(&buf, src, 16u, &mbar);
+  }
+  const bool ok = mbar_wait(m, 0);
+  if (__syncthreads_or(!ok)) {
+    wait_expired(m, 0);
+    if (threadIdx.x == 0) *result = 1;
+    return;
+  }
+  if (threadIdx.x == 0) *result = (buf.x == src->x && buf.w == src->w) ? 0 : 2;
 }
 
 // Strided view of one block's pair tile: element (i, site) at p[i * stride + site].
@@ -77,16 +156,22 @@ __device__ __forceinline__ void vec_load(const cpx<C> *v, int Vh, int q, Spinor<
 // each the neighbour's index within the other parity's half-vector, NONE if
 // the hop leaves the block.
 constexpr unsigned NONE = 0xFFFFu;
+template <int MU, int DIR>
+__device__ __forceinline__ unsigned inner_index(const Geom &g, const Site &t) {
+  int nb, ns;
+  float sg;
+  bool inside;
+  neighbour(g, t, MU, DIR, &nb, &ns, &sg, &inside);
+  return inside ? (unsigned)(ns - (t.p ? 0 : g.Vh)) : NONE;
+}
+// (the directions are compile-time constants in each branch, so no Geom or
+// Site array is indexed at run time)
 __device__ __forceinline__ uint2 inner_neighbours(const Geom &g, const Site &t, int h) {
-  unsigned f[4];
-  for (int k = 0; k < 4; k++) {
-    int nb, ns;
-    float sg;
-    bool inside;
-    neighbour(g, t, 2 * h + (k >> 1), (k & 1) ? -1 : +1, &nb, &ns, &sg, &inside);
-    f[k] = inside ? (unsigned)(ns - (t.p ? 0 : g.Vh)) : NONE;
-  }
-  return make_uint2(f[0] | (f[1] << 16), f[2] | (f[3] << 16));
+  if (h == 0)
+    return make_uint2(inner_index<0, +1>(g, t) | (inner_index<0, -1>(g, t) << 16),
+                      inner_index<1, +1>(g, t) | (inner_index<1, -1>(g, t) << 16));
+  return make_uint2(inner_index<2, +1>(g, t) | (inner_index<2, -1>(g, t) << 16),
+                    inner_index<3, +1>(g, t) | (inner_index<3, -1>(g, t) << 16));
 }
 
 // acc += hop pair in direction MU into the site at tile position s from the
@@ -217,14 +302,19 @@ template <typename S> struct SapSmem {
   using C = typename Store<S>::comp_t;
   using P = typename Store<S>::pair_t;
   static size_t vec_bytes(const Geom &g) { return (size_t)12 * g.Vh * sizeof(cpx<C>); }
-  static size_t bytes(const Geom &g, bool stage) {
-    size_t b = 3 * vec_bytes(g) + 96 * sizeof(C);
-    if (stage) b += (size_t)36 * (g.Vb + 2 * g.Vh) * sizeof(P);
+  // stage: 0 nothing staged, 1 links + A_oo + A_ee^-1, 2 links only
+  static size_t bytes(const Geom &g, int stage) {
+    size_t b = 3 * vec_bytes(g) + 96 * sizeof(C) + 16;   // + staging mbarrier
+    if (stage == 1) b += (size_t)36 * (g.Vb + 2 * g.Vh) * sizeof(P);
+    if (stage == 2) b += (size_t)36 * g.Vb * sizeof(P);
     return b;
   }
 };
 
-template <typename S, bool STAGE, int MINB, int NT>
+// STAGE: 0 operator tiles read through L1/L2; 1 links, A_oo and A_ee^-1 staged
+// in shared memory; 2 links staged, the clover blocks (each read by one
+// thread only) through L1/L2, which halves the footprint.
+template <typename S, int STAGE, int MINB, int NT>
 __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g, const void *__restrict__ links,
                                                    const void *__restrict__ clov, const void *__restrict__ cinv,
                                                    const RhsPtrs rp, int colour, int self_zero,
@@ -239,6 +329,14 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g, const void *__re
   cpx<C> *te = rho + 12 * Vh;     // even-site temporary
   cpx<C> *xch = te + 12 * Vh;     // partial-sum exchange between thread halves
   C *red = (C *)(xch + 12 * Vh);
+  uint64_t *mbar = (uint64_t *)(red + 96);   // staging barrier (16 bytes reserved)
+  unsigned char *tiles = (unsigned char *)(red + 96) + 16;
+  unsigned phase = 0;                        // parity of the staging barrier's current phase
+  if constexpr (STAGE != 0) {
+    if (threadIdx.x == 0) mbar_init(mbar);
+    __syncthreads();
+  }
+  const unsigned mbar_s = smem_u32(mbar);
 
   // Work items: (block of this colour, right-hand-side tile), block fastest.
   // A CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...; while it works
@@ -269,19 +367,40 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g, const void *__re
     }
   }
 
+  // Staging by bulk copies (the TMA engine), issued by thread 0 and tracked
+  // by the mbarrier: the links tile (36 x Vb pairs, contiguous per block),
+  // and for STAGE 1 the odd half of every clover row (36 pieces of Vh pairs)
+  // and the even-site inverse tile (36 x Vh, contiguous). Every size is a
+  // multiple of 16 bytes (Vh is even) and every address 16-byte aligned.
   Tile<P> Lt, Ao, Ai;
-  if constexpr (STAGE) {
-    P *sl = (P *)(red + 96);
+  if constexpr (STAGE == 1) {
+    P *sl = (P *)tiles;
     P *sa = sl + (size_t)36 * Vb;
     P *si = sa + (size_t)36 * Vh;
-    const P *gl = (const P *)links + (size_t)b * 36 * Vb;
-    const P *ga = (const P *)clov + (size_t)b * 36 * Vb;
-    stage(sl, gl, (size_t)36 * Vb * sizeof(P));
-    for (int i = 0; i < 36; i++) stage(sa + (size_t)i * Vh, ga + (size_t)i * Vb + Vh, (size_t)Vh * sizeof(P));
-    stage(si, (const P *)cinv + (size_t)b * 36 * Vh, (size_t)36 * Vh * sizeof(P));
+    if (threadIdx.x == 0) {
+      const P *gl = (const P *)links + (size_t)b * 36 * Vb;
+      const P *ga = (const P *)clov + (size_t)b * 36 * Vb;
+      const unsigned lb = 36u * Vb * sizeof(P), rb = (unsigned)(Vh * sizeof(P));
+      fence_proxy_async();
+      mbar_arrive_expect(mbar, lb + 72u * rb);
+      bulk_g2s(sl, gl, lb, mbar);
+      for (int i = 0; i < 36; i++) bulk_g2s(sa + (size_t)i * Vh, ga + (size_t)i * Vb + Vh, rb, mbar);
+      bulk_g2s(si, (const P *)cinv + (size_t)b * 36 * Vh, 36u * rb, mbar);
+    }
     Lt = {sl, Vb};
     Ao = {sa, Vh};
     Ai = {si, Vh};
+  } else if constexpr (STAGE == 2) {
+    P *sl = (P *)tiles;
+    if (threadIdx.x == 0) {
+      const unsigned lb = 36u * Vb * sizeof(P);
+      fence_proxy_async();
+      mbar_arrive_expect(mbar, lb);
+      bulk_g2s(sl, (const P *)links + (size_t)b * 36 * Vb, lb, mbar);
+    }
+    Lt = {sl, Vb};
+    Ao = {(const P *)clov + (size_t)b * 36 * Vb + Vh, Vb};
+    Ai = {(const P *)cinv + (size_t)b * 36 * Vh, Vh};
   } else {
     Lt = {(const P *)links + (size_t)b * 36 * Vb, Vb};
     Ao = {(const P *)clov + (size_t)b * 36 * Vb + Vh, Vb};
@@ -331,10 +450,17 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g, const void *__re
         __syncthreads();
       }
     }
-    if constexpr (STAGE) {
-      // each thread waits for its own copies; the barrier publishes everyone's
-      cp_async_wait_all();
-      __syncthreads();
+    if constexpr (STAGE != 0) {
+      // the staging of this item completes phase `phase` of the barrier;
+      // a CTA whose wait expired leaves as a whole (the flag is raised)
+      if (rr == 0) {
+        const bool ok = mbar_wait(mbar_s, phase);
+        if (__syncthreads_or(!ok)) {
+          wait_expired(mbar_s, phase);
+          return;
+        }
+        phase ^= 1u;
+      }
     }
 
     // ---- 3.-5. Schur right-hand side, MR steps, reconstruction: one loop of
@@ -439,7 +565,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g, const void *__re
   }  // work items
 }
 
-template <typename S, bool STAGE, int MINB, int NT = 256>
+template <typename S, int STAGE, int MINB, int NT = 256>
 int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, int tile, bool persistent,
           cudaStream_t st) {
   size_t smem = SapSmem<S>::bytes(g, STAGE);
@@ -529,27 +655,31 @@ static int launch_as_graph(const std::string &key, int variant, int nkernels, co
 }
 
 // Launch variants: tiles staged in shared memory with one CTA per SM; tiles
-// staged with two CTAs per SM (fits when the storage is 16-bit); tiles read
-// through L1/L2 with two CTAs per SM. Variants that do not fit are skipped.
+// staged with two CTAs per SM (fits when the storage is 16-bit); only the
+// links staged, with two CTAs per SM (when the full staging does not fit
+// twice); tiles read through L1/L2 with two CTAs per SM. Variants that do not
+// fit are skipped.
 // With several right-hand sides a CTA also solves `tile` of them with one
 // staging of its block's operator (rhs_tile; 0 lets the autotuner choose).
 template <typename S>
 int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
   const size_t limit = 227 * 1024, half = 113 * 1024;
-  const bool stage1 = SapSmem<S>::bytes(g, true) <= limit;
-  const bool stage2 = SapSmem<S>::bytes(g, true) <= half;
-  const bool nost2 = SapSmem<S>::bytes(g, false) <= half;
-  if (!stage1 && SapSmem<S>::bytes(g, false) > limit) {
+  const bool stage1 = SapSmem<S>::bytes(g, 1) <= limit;
+  const bool stage2 = SapSmem<S>::bytes(g, 1) <= half;
+  const bool links2 = !stage2 && SapSmem<S>::bytes(g, 2) <= half;
+  const bool nost2 = SapSmem<S>::bytes(g, 0) <= half;
+  if (!stage1 && SapSmem<S>::bytes(g, 0) > limit) {
     set_error("sap: block of %d sites needs more shared memory than available", g.Vb);
     return DD_EINVAL;
   }
-  int layouts[3], nl = 0;
+  int layouts[4], nl = 0;
   if (g.Vb > 256) {
     // 512-site blocks (e.g. 8 x 4^3): 512 threads, one CTA per SM
     layouts[nl++] = stage1 ? 3 : 4;
   } else {
     if (stage1) layouts[nl++] = 0;
     if (stage2) layouts[nl++] = 1;
+    if (links2) layouts[nl++] = 5;
     if (nost2 || !stage1) layouts[nl++] = 2;
   }
   int tiles[6], nt = 0;
@@ -565,11 +695,12 @@ int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const
     const int layout = layouts[k % nl], tile = tiles[(k / nl) % nt];
     const bool pers = k >= nl * nt;
     switch (layout) {
-      case 1: return sap_t<S, true, 2>(g, f, p, rp, tile, pers, st);
-      case 2: return sap_t<S, false, 2>(g, f, p, rp, tile, pers, st);
-      case 3: return sap_t<S, true, 1, 512>(g, f, p, rp, tile, pers, st);
-      case 4: return sap_t<S, false, 1, 512>(g, f, p, rp, tile, pers, st);
-      default: return sap_t<S, true, 1>(g, f, p, rp, tile, pers, st);
+      case 1: return sap_t<S, 1, 2>(g, f, p, rp, tile, pers, st);
+      case 2: return sap_t<S, 0, 2>(g, f, p, rp, tile, pers, st);
+      case 3: return sap_t<S, 1, 1, 512>(g, f, p, rp, tile, pers, st);
+      case 4: return sap_t<S, 0, 1, 512>(g, f, p, rp, tile, pers, st);
+      case 5: return sap_t<S, 2, 2>(g, f, p, rp, tile, pers, st);
+      default: return sap_t<S, 1, 1>(g, f, p, rp, tile, pers, st);
     }
   };
   int k = 0;
@@ -588,12 +719,33 @@ int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const
 
 }  // namespace
 
+int wait_selftest(int expire) {
+  uint4 *src = nullptr;
+  int *res = nullptr;
+  DD_CUDA(cudaMalloc(&src, sizeof(uint4) + sizeof(int)));
+  res = (int *)(src + 1);
+  const uint4 pat = make_uint4(0x01234567u, 0x89abcdefu, 0x0f1e2d3cu, 0x4b5a6978u);
+  int got = -1, rc = cuda_fail(cudaMemcpy(src, &pat, sizeof(pat), cudaMemcpyHostToDevice), "wait selftest");
+  if (rc == DD_OK) {
+    k_wait_selftest<<<1, 32>>>(src, expire, res);
+    rc = launched("k_wait_selftest");
+  }
+  if (rc == DD_OK) rc = cuda_fail(cudaMemcpy(&got, res, sizeof(int), cudaMemcpyDeviceToHost), "wait selftest");
+  cudaFree(src);
+  if (rc) return rc;
+  if (got != (expire ? 1 : 0)) {
+    set_error("wait selftest: result %d (expected %d)", got, expire ? 1 : 0);
+    return DD_ECUDA;
+  }
+  return DD_OK;
+}
+
 size_t sap_smem_bytes(const Geom &g, int prec, bool stage) {
   switch (prec) {
-    case DD_F64: return SapSmem<double>::bytes(g, stage);
-    case DD_F32: return SapSmem<float>::bytes(g, stage);
-    case DD_F16: return SapSmem<__half>::bytes(g, stage);
-    default: return SapSmem<__nv_bfloat16>::bytes(g, stage);
+    case DD_F64: return SapSmem<double>::bytes(g, stage ? 1 : 0);
+    case DD_F32: return SapSmem<float>::bytes(g, stage ? 1 : 0);
+    case DD_F16: return SapSmem<__half>::bytes(g, stage ? 1 : 0);
+    default: return SapSmem<__nv_bfloat16>::bytes(g, stage ? 1 : 0);
   }
 }
 
