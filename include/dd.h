@@ -128,6 +128,16 @@ int dd_create_gauge(dd_lattice_t lat, const double *links_host, dd_gauge_t *out)
  * Returns DD_EINVAL if a 6x6 block is singular. Synchronous. */
 int dd_create_op(dd_gauge_t gauge, double c_sw, double m0, int prec, dd_op_t *out);
 
+/* Wilson-clover operator on `gauge` with caller-supplied site blocks
+ * A(n) = 4 + m0 + C(n) (the clover term computed elsewhere, e.g. by the
+ * calling application), host FP64 [V][2][6][6][2] in the layout of
+ * dd_op_get_clover (chirality block h = spins {2h, 2h+1}; row/column index
+ * 3*(spin - 2h) + colour; canonical site order). Each block's Hermitian
+ * part is used. The even-site inverses are formed on the device; storage as
+ * for dd_create_op. DD_EINVAL if an even-site block is singular. The caller
+ * keeps ownership of clover_host. Synchronous. */
+int dd_create_op_clover(dd_gauge_t gauge, const double *clover_host, int prec, dd_op_t *out);
+
 /* Copy the clover site blocks A(n) of `op` (FP64) to host memory as
  * [V][2][6][6][2] (chirality block h = spins {2h, 2h+1}; row/column index
  * 3*(spin - 2h) + colour), canonical site order. Synchronous. */

@@ -88,6 +88,8 @@ EXPORTS = {
     "dd_create_gauge": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "dd_create_op": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                       ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "dd_create_op_clover": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)],
+                            ctypes.c_int),
     "dd_op_get_clover": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "dd_destroy": ([ctypes.c_void_p], None),
     "dd_pack": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
@@ -241,10 +243,20 @@ class Gauge(Handle):
 class Op(Handle):
     """Wilson-clover operator; ``prec`` is the Schwarz smoother's storage precision."""
 
-    def __init__(self, gauge: Gauge, c_sw: float, m0: float, prec: int = F32):
+    def __init__(self, gauge: Gauge, c_sw: float = None, m0: float = None, prec: int = F32, clover=None):
+        """Either (c_sw, m0): the clover term is built from the gauge field; or
+        clover: caller-supplied site blocks A(n) = 4 + m0 + C(n), (V, 2, 6, 6)
+        complex (the layout of ``Op.clover()``)."""
         h = ctypes.c_void_p()
-        _check(lib().dd_create_op(gauge.handle, float(c_sw), float(m0), int(prec), ctypes.byref(h)),
-               "dd_create_op")
+        if clover is not None:
+            A = np.ascontiguousarray(clover, dtype=np.complex128)
+            if A.size != gauge.lat.V * 72:
+                raise ValueError("clover must hold V x 2 x 6 x 6 complex entries")
+            _check(lib().dd_create_op_clover(gauge.handle, _ptr(A), int(prec), ctypes.byref(h)),
+                   "dd_create_op_clover")
+        else:
+            _check(lib().dd_create_op(gauge.handle, float(c_sw), float(m0), int(prec), ctypes.byref(h)),
+                   "dd_create_op")
         self._h = h.value
         self.gauge, self.lat, self.prec = gauge, gauge.lat, prec
 
@@ -389,12 +401,15 @@ class Server(Handle):
         self._keep = {}
 
     def submit(self, op: Op, b: np.ndarray, tol=1e-10, restart=16, max_iter=1000, sweeps=4, mr_steps=4,
-               inner_reduction=None) -> int:
+               inner_reduction=None, mg=None) -> int:
+        """Queue a solve; ``mg``: a Multigrid of ``op`` to precondition with
+        the two-level method instead of SAP."""
         b = _as_canonical(np.ascontiguousarray(b), op.lat.V)
         nrhs = _count_rhs(b, op.lat.V)
         if inner_reduction is None:
             inner_reduction = 0.0 if op.prec == F64 else 1e-5
-        sp = SolveParams(tol, restart, max_iter, SapParams(sweeps, mr_steps, 1, 0), inner_reduction, HOST, 0)
+        sp = SolveParams(tol, restart, max_iter, SapParams(sweeps, mr_steps, 1, 0), inner_reduction, HOST, 0,
+                         mg.handle if mg is not None else None)
         req = Request(op.handle, b.ctypes.data, nrhs, sp)
         t = ctypes.c_uint64()
         _check(lib().dd_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "dd_submit")

@@ -198,13 +198,13 @@ static int alloc_fields(const Geom &g, int prec, OpFields &f) {
   return DD_OK;
 }
 
-int dd_create_op(dd_gauge_t gauge, double c_sw, double m0, int prec, dd_op_t *out) {
-  Gauge *ga = (Gauge *)gauge;
-  if (!ga || ga->magic != MAGIC_GAUGE || !out || prec < DD_F64 || prec > DD_BF16 || !std::isfinite(c_sw) ||
-      !std::isfinite(m0)) {
-    set_error("dd_create_op: bad argument");
-    return DD_EINVAL;
-  }
+}  // extern "C"
+
+// Shared tail of the two operator constructors: `fill` writes the FP64 site
+// blocks and even-site inverses (and may flag a singular block in *bad); the
+// links and the lower-precision copies follow.
+template <typename Fill>
+static int create_op(Gauge *ga, double c_sw, double m0, int prec, Fill fill, dd_op_t *out) {
   const Geom &g = ga->lat->g;
   Op *op = new (std::nothrow) Op;
   if (!op) return DD_ENOMEM;
@@ -221,8 +221,7 @@ int dd_create_op(dd_gauge_t gauge, double c_sw, double m0, int prec, dd_op_t *ou
   if (rc == DD_OK && cudaMalloc(&bad, sizeof(int)) != cudaSuccess) rc = DD_ENOMEM;
   cudaStream_t st = 0;
   if (rc == DD_OK) rc = cuda_fail(cudaMemsetAsync(bad, 0, sizeof(int), st), "memset");
-  if (rc == DD_OK)
-    rc = launch_build_clover(g, ga->links_canon, c_sw, m0, (double *)op->f64.clov, (double *)op->f64.cinv, bad, st);
+  if (rc == DD_OK) rc = fill(g, (double *)op->f64.clov, (double *)op->f64.cinv, bad, st);
   if (rc == DD_OK) rc = launch_pack_links(g, DD_F64, ga->links_canon, op->f64.links, st);
   if (rc == DD_OK) rc = launch_pack_links(g, DD_F32, ga->links_canon, op->f32.links, st);
   if (rc == DD_OK) rc = launch_convert_pairs(DD_F32, (const double *)op->f64.clov, op->f32.clov, (size_t)g.V * 36, st);
@@ -238,7 +237,7 @@ int dd_create_op(dd_gauge_t gauge, double c_sw, double m0, int prec, dd_op_t *ou
   if (rc == DD_OK) rc = cuda_fail(cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost), "dd_create_op");
   cudaFree(bad);
   if (rc == DD_OK && hbad) {
-    set_error("dd_create_op: a clover block A = 4 + m0 + C is singular");
+    set_error("dd_create_op: an even-site clover block A = 4 + m0 + C is singular");
     rc = DD_EINVAL;
   }
   if (rc != DD_OK) {
@@ -254,6 +253,48 @@ int dd_create_op(dd_gauge_t gauge, double c_sw, double m0, int prec, dd_op_t *ou
   ga->refs++;
   *out = (dd_op_t)op;
   return DD_OK;
+}
+
+extern "C" {
+
+int dd_create_op(dd_gauge_t gauge, double c_sw, double m0, int prec, dd_op_t *out) {
+  Gauge *ga = (Gauge *)gauge;
+  if (!ga || ga->magic != MAGIC_GAUGE || !out || prec < DD_F64 || prec > DD_BF16 || !std::isfinite(c_sw) ||
+      !std::isfinite(m0)) {
+    set_error("dd_create_op: bad argument");
+    return DD_EINVAL;
+  }
+  return create_op(
+      ga, c_sw, m0, prec,
+      [&](const Geom &g, double *clov, double *cinv, int *bad, cudaStream_t st) {
+        return launch_build_clover(g, ga->links_canon, c_sw, m0, clov, cinv, bad, st);
+      },
+      out);
+}
+
+int dd_create_op_clover(dd_gauge_t gauge, const double *clover_host, int prec, dd_op_t *out) {
+  Gauge *ga = (Gauge *)gauge;
+  if (!ga || ga->magic != MAGIC_GAUGE || !clover_host || !out || prec < DD_F64 || prec > DD_BF16) {
+    set_error("dd_create_op_clover: bad argument");
+    return DD_EINVAL;
+  }
+  const size_t bytes = (size_t)ga->lat->g.V * 144 * sizeof(double);
+  double *dev = nullptr;
+  if (cudaMalloc(&dev, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("dd_create_op_clover: out of device memory (%zu bytes)", bytes);
+    return DD_ENOMEM;
+  }
+  int rc = cuda_fail(cudaMemcpy(dev, clover_host, bytes, cudaMemcpyHostToDevice), "dd_create_op_clover: copy");
+  if (rc == DD_OK)
+    rc = create_op(
+        ga, NAN, NAN, prec,
+        [&](const Geom &g, double *clov, double *cinv, int *bad, cudaStream_t st) {
+          return launch_load_clover(g, dev, clov, cinv, bad, st);
+        },
+        out);
+  cudaFree(dev);
+  return rc;
 }
 
 int dd_op_get_clover(dd_op_t opp, double *host_out) {

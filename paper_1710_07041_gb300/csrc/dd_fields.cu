@@ -267,6 +267,39 @@ __global__ void k_build_clover(Geom g, const double2 *__restrict__ U, double c_s
   }
 }
 
+// Caller-supplied site blocks A(n), canonical order [V][2][6][6] complex:
+// packed (Hermitian part, as pack_herm) into the tile layout, and the
+// even-site blocks inverted.
+__global__ void k_load_clover(Geom g, const double2 *__restrict__ A_canon, double2 *clov, double2 *cinv, int *bad) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= g.V) return;
+  int b = (int)(t / g.Vb), s = (int)(t - (long long)b * g.Vb);
+  const long long n = canonical_index(g, b, s);
+  const bool even = s < g.Vh;
+  for (int h = 0; h < 2; h++) {
+    cpx<double> M[36];
+    for (int i = 0; i < 36; i++) {
+      const double2 v = A_canon[(n * 2 + h) * 36 + i];
+      M[i] = {v.x, v.y};
+    }
+    pack_herm(M, clov + ((size_t)b * 36 + 18 * h) * g.Vb + s, g.Vb);
+    if (even) {
+      // invert the stored (exactly Hermitian) block
+      cpx<double> A[36], Ai[36];
+      for (int i = 0; i < 6; i++) {
+        A[7 * i] = {M[7 * i].re, 0.0};
+        for (int j = i + 1; j < 6; j++) {
+          const cpx<double> a = M[6 * i + j], c = M[6 * j + i];
+          A[6 * i + j] = {0.5 * (a.re + c.re), 0.5 * (a.im - c.im)};
+          A[6 * j + i] = {A[6 * i + j].re, -A[6 * i + j].im};
+        }
+      }
+      if (!inv6(A, Ai)) atomicExch(bad, 1);
+      pack_herm(Ai, cinv + ((size_t)b * 36 + 18 * h) * g.Vh + s, g.Vh);
+    }
+  }
+}
+
 template <typename S> int pack_t(const Geom &g, const double *canon, void *field, int nrhs, double scale, cudaStream_t st) {
   size_t fb = (size_t)g.V * 24 * sizeof(S);
   k_pack<S><<<grid_for(g.V * nrhs), TPB, 0, st>>>(g, (const double2 *)canon, field, nrhs, scale, fb);
@@ -355,6 +388,13 @@ int launch_convert_pairs(int prec, const double *in, void *out, size_t n, cudaSt
     default: set_error("bad precision %d", prec); return DD_EINVAL;
   }
   return launched("k_convert_pairs");
+}
+
+int launch_load_clover(const Geom &g, const double *A_canon, double *clov64, double *cinv64, int *bad,
+                       cudaStream_t st) {
+  k_load_clover<<<grid_for(g.V, 128), 128, 0, st>>>(g, (const double2 *)A_canon, (double2 *)clov64,
+                                                   (double2 *)cinv64, bad);
+  return launched("k_load_clover");
 }
 
 int launch_build_clover(const Geom &g, const double *links_canon, double c_sw, double m0, double *clov64,

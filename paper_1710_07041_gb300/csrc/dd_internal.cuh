@@ -489,6 +489,9 @@ RhsPtrs contiguous(const void *in, void *out, int nrhs, size_t field_bytes);
 int launch_pack(const Geom &g, int prec, const double *canon, void *field, int nrhs, double scale, cudaStream_t st);
 int launch_unpack(const Geom &g, int prec, const void *field, double *canon, int nrhs, double scale, cudaStream_t st);
 int launch_pack_links(const Geom &g, int prec, const double *links_canon, void *out, cudaStream_t st);
+// caller-supplied site blocks A(n) [V][2][6][6] complex (canonical order), packed and inverted like the build
+int launch_load_clover(const Geom &g, const double *A_canon, double *clov64, double *cinv64, int *bad,
+                       cudaStream_t st);
 int launch_build_clover(const Geom &g, const double *links_canon, double c_sw, double m0, double *clov64,
                         double *cinv64, int *bad, cudaStream_t st);
 int launch_convert_pairs(int prec, const double *in, void *out, size_t npairs, cudaStream_t st);

@@ -93,3 +93,43 @@ def test_two_level_solve(prec):
     assert info[0]["iterations"] < info_sap[0]["iterations"], (info[0]["iterations"], info_sap[0]["iterations"])
     mg.close()
     s.close()
+
+
+def test_two_level_batched_equals_single():
+    """Several right-hand sides in one batched two-level solve (one coarse
+    workspace per slot) give the same iterates as each solved alone."""
+    s = Setup(DIMS, BLOCK, eps=0.25, n_stout=2, c_sw=1.7, m0=-0.07, prec=dd.F32, seed=93)
+    tv = np.stack([synth.gaussian_spinor(s.V, 970 + k) for k in range(8)])
+    mg = dd.Multigrid(s.op, tv, setup_iters=3, coarse_max_iter=16, coarse_tol=0.05, sweeps=3, mr_steps=4)
+    bs = np.stack([synth.gaussian_spinor(s.V, 980 + r) for r in range(3)])
+    xb, infob = s.op.solve(bs, tol=1e-10, mg=mg)
+    for r in range(3):
+        x1, info1 = s.op.solve(bs[r], tol=1e-10, mg=mg)
+        assert np.array_equal(x1, xb[r])
+        assert info1[0]["iterations"] == infob[r]["iterations"]
+        assert relerr(s.ref.apply(xb[r]), bs[r]) <= 1e-10
+    mg.close()
+    s.close()
+
+
+def test_two_level_through_server():
+    """Requests that carry a two-level preconditioner, served next to plain
+    SAP requests on the same operator, match their solo solves."""
+    s = Setup(DIMS, BLOCK, eps=0.25, n_stout=2, c_sw=1.7, m0=-0.07, prec=dd.F32, seed=94)
+    tv = np.stack([synth.gaussian_spinor(s.V, 990 + k) for k in range(8)])
+    mg = dd.Multigrid(s.op, tv, setup_iters=3, coarse_max_iter=16, coarse_tol=0.05, sweeps=3, mr_steps=4)
+    srv = dd.Server(max_slots=4, max_batch_rhs=4)
+    jobs = []
+    for k in range(4):
+        b = synth.gaussian_spinor(s.V, 995 + k)
+        use = mg if k % 2 == 0 else None
+        jobs.append((b, use, srv.submit(s.op, b, tol=1e-10, mg=use)))
+    for b, use, t in jobs:
+        st, x, info = srv.wait(t)
+        assert st == dd.DONE
+        x1, _ = s.op.solve(b, tol=1e-10, mg=use)
+        assert np.array_equal(x, x1.reshape(x.shape))
+        assert relerr(s.ref.apply(x), b) <= 1e-10
+    srv.close()
+    mg.close()
+    s.close()
