@@ -161,9 +161,15 @@ extern "C" int dd_solve_noalloc(dd_op_t opp, const dd_solve_params *p, const dou
     DD_CUDA(cudaMemsetAsync(x, 0, f64, st));
   }
   const OpFields &fz_ops = zprec == DD_F64 ? op->f64 : op->f32;
+  bool x_zero = !p->use_x0;   // first cycle from x = 0: D x = 0, no Dslash
   for (;;) {
     // true residual r = b - D x (FP64) in w
-    if ((rc = launch_dirac(g, op->f64, x, w, 1, st))) return rc;
+    if (x_zero) {
+      DD_CUDA(cudaMemsetAsync(w, 0, f64, st));
+      x_zero = false;
+    } else if ((rc = launch_dirac(g, op->f64, x, w, 1, st))) {
+      return rc;
+    }
     if ((rc = bl.xmy(b, w, n, st))) return rc;
     if ((rc = bl.norm2(w, n, hd + 132, st))) return rc;
     if (bnorm < 0 && (rc = bl.norm2(b, n, hd + 133, st))) return rc;

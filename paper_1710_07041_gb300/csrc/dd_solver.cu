@@ -147,6 +147,7 @@ int BatchSolver::start(Slot &s) {
   DD_CUDA(cudaMemcpyAsync(s.canon, s.job.b, f64_, s.job.b_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                           st_));
   if ((rc = launch_pack(g, DD_F64, s.canon, s.b, 1, 1.0, st_))) return rc;
+  s.x_zero = !s.job.use_x0;
   if (s.job.use_x0) {
     DD_CUDA(cudaMemcpyAsync(s.canon, s.job.x, f64_,
                             s.job.x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st_));
@@ -187,14 +188,21 @@ int BatchSolver::restart_phase(std::vector<Slot *> &R) {
   const Geom &g = op_->lat->g;
   const size_t n = (size_t)g.V * 12;
   int rc;
+  // D x for the slots whose x is not known to be zero (w = 0 for the others,
+  // so that w = b - w below gives r = b)
   RhsPtrs rp;
-  rp.n = (int)R.size();
-  for (int i = 0; i < rp.n; i++) {
-    rp.in[i] = R[i]->x;
-    rp.out[i] = R[i]->w;
-  }
+  rp.n = 0;
   cudaEventRecord(ev_[0], st_);
-  if ((rc = launch_dirac(g, op_->f64, rp, st_))) return rc;
+  for (Slot *s : R) {
+    if (s->x_zero) {
+      DD_CUDA(cudaMemsetAsync(s->w, 0, f64_, st_));
+      s->x_zero = false;
+      continue;
+    }
+    rp.in[rp.n] = s->x;
+    rp.out[rp.n++] = s->w;
+  }
+  if (rp.n && (rc = launch_dirac(g, op_->f64, rp, st_))) return rc;
   for (Slot *s : R) {
     double *hd = hdev_ + HSTRIDE * (s - slots_.data());
     if ((rc = blas_.xmy(s->b, s->w, n, st_))) return rc;

@@ -24,6 +24,7 @@ struct RhsJob {
 // Device buffers and FGMRES state of one batch slot.
 struct Slot {
   bool busy = false, need_restart = true;
+  bool x_zero = false;   // x is exactly zero (first cycle without an initial guess): r = b, no Dslash
   RhsJob job;
   int j = 0, its = 0, cycles = 0;
   double bnorm = -1, beta = 0, rel = 1, est = 1, target = 0;
