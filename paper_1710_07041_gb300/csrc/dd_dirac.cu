@@ -63,18 +63,30 @@ int dirac_v(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st)
 
 // Launch variants (threads per CTA, CTAs per SM the register budget must
 // allow): (128, 5) ~100 registers, (128, 6) ~80, (256, 2) ~128 and (256, 3)
-// ~85; a 256-thread CTA covers one whole 4^4 block, so interior neighbours
-// are read by the same SM.
+// ~85; for FP64 (128, 4) ~128, (128, 3) ~168, (256, 2) ~128, (256, 1) 255.
+// A 256-thread CTA covers one whole 4^4 block, so interior neighbours are
+// read by the same SM.
 constexpr int DIRAC_VARIANTS = 4;
 
 template <typename S>
 int dirac_t(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st) {
   auto run = [&](int v) {
-    switch (v) {
-      case 1: return dirac_v<S, 128, 6>(g, f, p, st);
-      case 2: return dirac_v<S, 256, 2>(g, f, p, st);
-      case 3: return dirac_v<S, 256, 3>(g, f, p, st);
-      default: return dirac_v<S, 128, 5>(g, f, p, st);
+    if constexpr (Store<S>::prec == DD_F64) {
+      // FP64 values take two registers each: looser caps (the kernel is
+      // bound by GB300's FP64 rate, and spilling adds to that)
+      switch (v) {
+        case 1: return dirac_v<S, 128, 3>(g, f, p, st);
+        case 2: return dirac_v<S, 256, 2>(g, f, p, st);
+        case 3: return dirac_v<S, 256, 1>(g, f, p, st);
+        default: return dirac_v<S, 128, 4>(g, f, p, st);
+      }
+    } else {
+      switch (v) {
+        case 1: return dirac_v<S, 128, 6>(g, f, p, st);
+        case 2: return dirac_v<S, 256, 2>(g, f, p, st);
+        case 3: return dirac_v<S, 256, 3>(g, f, p, st);
+        default: return dirac_v<S, 128, 5>(g, f, p, st);
+      }
     }
   };
   int v = 0;
