@@ -6,7 +6,7 @@
 //
 // One CTA per block (x one right-hand side). Per phase the CTA
 //   1. stages the block's links, odd-site clover A_oo and even-site inverse
-//      A_ee^-1 into shared memory with cp.async (overlapping step 2),
+//      A_ee^-1 into shared memory with bulk (TMA) copies (overlapping step 2),
 //   2. forms r = b - D x on its sites (neighbour x read from the other colour's
 //      blocks in HBM; skipped when x = 0),
 //   3. Schur right-hand side  bhat = r_o - D_oe A_ee^-1 r_e,
@@ -19,12 +19,14 @@
 // {2h, 2h+1}; the two halves exchange partial hop sums through shared memory.
 // With Vh = block sites / 2 a multiple of 32, h is warp-uniform, so the
 // per-direction code never diverges inside a warp.
-#include <algorithm>
+// This file holds the host side (variant dispatch per storage precision, the
+// graph cache, the wait counter); the kernel templates are in
+// dd_sap_kernels.cuh and instantiated per precision in dd_sap_<prec>.cu.
 #include <map>
 #include <mutex>
 #include <string>
 
-#include "dd_tune.cuh"
+#include "dd_sap_kernels.cuh"
 
 namespace dd {
 
@@ -45,69 +47,36 @@ int device_wait_status() {
   return DD_OK;
 }
 
-namespace {
 
-
-// bulk prefetch of `bytes` (multiple of 16, 16-byte aligned) into L2
-__device__ __forceinline__ void prefetch_l2(const void *gmem, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
-}
-
-// ---- bulk (TMA) staging into shared memory, completion on an mbarrier
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *mbar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
-}
-// the issuing thread's arrival, announcing `bytes` of bulk copies
-__device__ __forceinline__ void mbar_arrive_expect(uint64_t *mbar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(bytes)
-               : "memory");
-}
-// one bulk copy global -> shared (addresses 16-byte aligned, bytes a multiple of 16)
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_test(unsigned mbar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// generic-proxy accesses of shared memory before later bulk copies into it
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-
-// Bounded wait for phase `parity` of the staging barrier (shared address
-// mbar): about one second of SM clock at most, then false.
-constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;
-__device__ __noinline__ bool mbar_wait_slow(unsigned mbar, unsigned parity) {
-  const long long t0 = clock64();
-  while (!mbar_test(mbar, parity))
-    if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
-  return true;
-}
-__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
-  return mbar_test(mbar, parity) || mbar_wait_slow(mbar, parity);
-}
-// the CTA's wait expired: count it, let thread 0's copies land (bounded)
-__device__ __noinline__ void wait_expired(unsigned mbar, unsigned parity) {
-  if (threadIdx.x == 0) {
-    atomicAdd(&g_wait_timeouts, 1u);
-    mbar_wait_slow(mbar, parity);
+// device address of g_wait_timeouts on the current device (cached per device)
+unsigned *sap_timeout_counter() {
+  static std::mutex mu;
+  static std::map<int, unsigned *> addr;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = addr.find(dev);
+  if (it != addr.end()) return it->second;
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_wait_timeouts) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
   }
+  addr[dev] = (unsigned *)p;
+  return (unsigned *)p;
 }
 
+int sap_run_f64(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st);
+int sap_run_f32(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st);
+int sap_run_f16(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st);
+int sap_run_bf16(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st);
+
+namespace {
 // Self-test of the staging handshake: one 16-byte bulk copy tracked by an
 // mbarrier; with `expire` the barrier is told to expect 16 more bytes than
 // are copied, so its phase never completes and the bounded wait must expire.
 // result: 0 copy landed, 1 wait expired, 2 copy landed with wrong data.
-__global__ void k_wait_selftest(const uint4 *src, int expire, int *result) {
+__global__ void k_wait_selftest(const uint4 *src, int expire, int *result, unsigned *timeouts) {
   __shared__ __align__(16) uint4 buf;
   __shared__ __align__(8) uint64_t mbar;
   const unsigned m = smem_u32(&mbar);
@@ -120,488 +89,14 @@ __global__ void k_wait_selftest(const uint4 *src, int expire, int *result) {
   }
   const bool ok = mbar_wait(m, 0);
   if (__syncthreads_or(!ok)) {
-    wait_expired(m, 0);
+    wait_expired(timeouts, m, 0);
     if (threadIdx.x == 0) *result = 1;
     return;
   }
   if (threadIdx.x == 0) *result = (buf.x == src->x && buf.w == src->w) ? 0 : 2;
 }
 
-// Strided view of one block's pair tile: element (i, site) at p[i * stride + site].
-template <typename P> struct Tile {
-  const P *p;
-  int stride;
-};
-
-template <typename C, typename P>
-__device__ __forceinline__ void tile_link(const Tile<P> &t, int s, int mu, Link<C> &u) {
-#pragma unroll
-  for (int i = 0; i < 9; i++) u.m[i] = from_pair<C, P>(t.p[(9 * mu + i) * t.stride + s]);
-}
-template <typename C, typename P>
-__device__ __forceinline__ void tile_block(const Tile<P> &t, int s, int h, cpx<C> *m) {
-#pragma unroll
-  for (int i = 0; i < 18; i++) m[i] = from_pair<C, P>(t.p[(18 * h + i) * t.stride + s]);
-}
-
-// shared-memory vector: [12][Vh] complex, one parity of the block
-template <typename C>
-__device__ __forceinline__ void vec_load(const cpx<C> *v, int Vh, int q, Spinor<C> &o) {
-#pragma unroll
-  for (int i = 0; i < 12; i++) o.c[i] = v[i * Vh + q];
-}
-
-// In-block neighbours of one site for the two directions of its thread half:
-// four 16-bit fields (dir 2h fwd, dir 2h bwd, dir 2h+1 fwd, dir 2h+1 bwd),
-// each the neighbour's index within the other parity's half-vector, NONE if
-// the hop leaves the block.
-constexpr unsigned NONE = 0xFFFFu;
-template <int MU, int DIR>
-__device__ __forceinline__ unsigned inner_index(const Geom &g, const Site &t) {
-  int nb, ns;
-  float sg;
-  bool inside;
-  neighbour(g, t, MU, DIR, &nb, &ns, &sg, &inside);
-  return inside ? (unsigned)(ns - (t.p ? 0 : g.Vh)) : NONE;
-}
-// (the directions are compile-time constants in each branch, so no Geom or
-// Site array is indexed at run time)
-__device__ __forceinline__ uint2 inner_neighbours(const Geom &g, const Site &t, int h) {
-  if (h == 0)
-    return make_uint2(inner_index<0, +1>(g, t) | (inner_index<0, -1>(g, t) << 16),
-                      inner_index<1, +1>(g, t) | (inner_index<1, -1>(g, t) << 16));
-  return make_uint2(inner_index<2, +1>(g, t) | (inner_index<2, -1>(g, t) << 16),
-                    inner_index<3, +1>(g, t) | (inner_index<3, -1>(g, t) << 16));
-}
-
-// acc += hop pair in direction MU into the site at tile position s from the
-// shared half-vector v (the other parity), links from tile L. nf/nbk: neighbour
-// indices (NONE: outside the block); off: tile offset of the other parity.
-template <int MU, typename C, typename P>
-__device__ __forceinline__ void hop_inner_dir(int Vh, int s, unsigned nf, unsigned nbk, int off, const cpx<C> *v,
-                                              const Tile<P> &L, Spinor<C> &acc) {
-  Link<C> u;
-  Spinor<C> psi;
-  if (nf != NONE) {
-    vec_load(v, Vh, (int)nf, psi);
-    tile_link(L, s, MU, u);
-    hop<MU, true>(acc, u, psi, (C)-0.5);
-  }
-  if (nbk != NONE) {
-    vec_load(v, Vh, (int)nbk, psi);
-    tile_link(L, (int)nbk + off, MU, u);
-    hop<MU, false>(acc, u, psi, (C)-0.5);
-  }
-}
-
-template <typename C, typename P>
-__device__ __forceinline__ void hops_inner(int Vh, int s, int h, uint2 nbr, int off, const cpx<C> *v,
-                                           const Tile<P> &L, Spinor<C> &acc) {
-#pragma unroll
-  for (int i = 0; i < 12; i++) acc.c[i] = {0, 0};
-  if (h == 0) {
-    hop_inner_dir<0>(Vh, s, nbr.x & NONE, nbr.x >> 16, off, v, L, acc);
-    hop_inner_dir<1>(Vh, s, nbr.y & NONE, nbr.y >> 16, off, v, L, acc);
-  } else {
-    hop_inner_dir<2>(Vh, s, nbr.x & NONE, nbr.x >> 16, off, v, L, acc);
-    hop_inner_dir<3>(Vh, s, nbr.y & NONE, nbr.y >> 16, off, v, L, acc);
-  }
-}
-
-// acc += hops into site t from the global field x, directions {2h, 2h+1};
-// neighbours inside the block are skipped when self_zero (x known to be 0
-// there), neighbours outside when halo_zero.
-template <int MU, typename S, typename C>
-__device__ __forceinline__ void hop_global_dir(const Geom &g, const Site &t, const void *links, const void *x,
-                                               bool self_zero, bool halo_zero, Spinor<C> &acc) {
-  int nb, ns;
-  float sg;
-  bool inside;
-  Link<C> u;
-  Spinor<C> psi;
-  neighbour(g, t, MU, +1, &nb, &ns, &sg, &inside);
-  if (inside ? !self_zero : !halo_zero) {
-    load_spinor<S, C>(x, g, nb, ns, psi);
-    load_link<S, C>(links, g, t.b, t.s, MU, u);
-    hop<MU, true>(acc, u, psi, (C)(-0.5f * sg));
-  }
-  neighbour(g, t, MU, -1, &nb, &ns, &sg, &inside);
-  if (inside ? !self_zero : !halo_zero) {
-    load_spinor<S, C>(x, g, nb, ns, psi);
-    load_link<S, C>(links, g, nb, ns, MU, u);
-    hop<MU, false>(acc, u, psi, (C)(-0.5f * sg));
-  }
-}
-
-template <typename S, typename C>
-__device__ __forceinline__ void hops_global(const Geom &g, const Site &t, int h, const void *links, const void *x,
-                                            bool self_zero, bool halo_zero, Spinor<C> &acc) {
-#pragma unroll
-  for (int i = 0; i < 12; i++) acc.c[i] = {0, 0};
-  if (h == 0) {
-    hop_global_dir<0, S, C>(g, t, links, x, self_zero, halo_zero, acc);
-    hop_global_dir<1, S, C>(g, t, links, x, self_zero, halo_zero, acc);
-  } else {
-    hop_global_dir<2, S, C>(g, t, links, x, self_zero, halo_zero, acc);
-    hop_global_dir<3, S, C>(g, t, links, x, self_zero, halo_zero, acc);
-  }
-}
-
-// the six components of spin half h (selects, so the register arrays are
-// never indexed at run time)
-template <typename C>
-__device__ __forceinline__ void half_of(const Spinor<C> &s, int h, cpx<C> *out) {
-#pragma unroll
-  for (int i = 0; i < 6; i++) out[i] = h ? s.c[6 + i] : s.c[i];
-}
-
-// Exchange partial hop sums between the two halves of a site pair: on return
-// own[0..5] = full sum of the components of half h. xch: [12][Vh] smem. A
-// thread reads only the entries its partner wrote for it, so the next write
-// to xch needs one barrier after this call (every caller has one).
-template <typename C>
-__device__ __forceinline__ void exchange(cpx<C> *xch, int Vh, int j, int h, const Spinor<C> &part, cpx<C> *own) {
-  const int other = 6 * (1 - h), mine = 6 * h;
-#pragma unroll
-  for (int i = 0; i < 6; i++) xch[(other + i) * Vh + j] = h ? part.c[i] : part.c[6 + i];
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < 6; i++) {
-    cpx<C> a = h ? part.c[6 + i] : part.c[i], b = xch[(mine + i) * Vh + j];
-    own[i] = {a.re + b.re, a.im + b.im};
-  }
-}
-
-// deterministic block sum of three values; red: smem [3][32]
-template <typename C>
-__device__ __forceinline__ void block_sum3(C &a, C &b, C &c, C *red) {
-  const int width = blockDim.x < 32 ? blockDim.x : 32;
-  const unsigned mask = width == 32 ? 0xffffffffu : ((1u << width) - 1u);
-  for (int o = width / 2; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(mask, a, o);
-    b += __shfl_xor_sync(mask, b, o);
-    c += __shfl_xor_sync(mask, c, o);
-  }
-  const int w = threadIdx.x / 32, nw = (blockDim.x + 31) / 32;
-  if ((threadIdx.x & 31) == 0) {
-    red[w] = a;
-    red[32 + w] = b;
-    red[64 + w] = c;
-  }
-  __syncthreads();
-  a = b = c = 0;
-  for (int i = 0; i < nw; i++) {
-    a += red[i];
-    b += red[32 + i];
-    c += red[64 + i];
-  }
-  __syncthreads();
-}
-
-template <typename S> struct SapSmem {
-  using C = typename Store<S>::comp_t;
-  using P = typename Store<S>::pair_t;
-  static size_t vec_bytes(const Geom &g) { return (size_t)12 * g.Vh * sizeof(cpx<C>); }
-  // stage: 0 nothing staged, 1 links + A_oo + A_ee^-1, 2 links only
-  static size_t bytes(const Geom &g, int stage) {
-    size_t b = 3 * vec_bytes(g) + 96 * sizeof(C) + 16;   // + staging mbarrier
-    if (stage == 1) b += (size_t)36 * (g.Vb + 2 * g.Vh) * sizeof(P);
-    if (stage == 2) b += (size_t)36 * g.Vb * sizeof(P);
-    return b;
-  }
-};
-
-// STAGE: 0 operator tiles read through L1/L2; 1 links, A_oo and A_ee^-1 staged
-// in shared memory; 2 links staged, the clover blocks (each read by one
-// thread only) through L1/L2, which halves the footprint.
-template <typename S, int STAGE, int MINB, int NT>
-__global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g, const void *__restrict__ links,
-                                                   const void *__restrict__ clov, const void *__restrict__ cinv,
-                                                   const RhsPtrs rp, int colour, int self_zero,
-                                                   int halo_zero, int nmr, int tile) {
-  using C = typename Store<S>::comp_t;
-  using P = typename Store<S>::pair_t;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int Vh = g.Vh, Vb = g.Vb;
-  const int h = threadIdx.x / Vh, j = threadIdx.x - h * Vh;
-
-  cpx<C> *rho = (cpx<C> *)smem;   // MR residual on odd sites (then e_o)
-  cpx<C> *te = rho + 12 * Vh;     // even-site temporary
-  cpx<C> *xch = te + 12 * Vh;     // partial-sum exchange between thread halves
-  C *red = (C *)(xch + 12 * Vh);
-  uint64_t *mbar = (uint64_t *)(red + 96);   // staging barrier (16 bytes reserved)
-  unsigned char *tiles = (unsigned char *)(red + 96) + 16;
-  unsigned phase = 0;                        // parity of the staging barrier's current phase
-  if constexpr (STAGE != 0) {
-    if (threadIdx.x == 0) mbar_init(mbar);
-    __syncthreads();
-  }
-  const unsigned mbar_s = smem_u32(mbar);
-
-  // Work items: (block of this colour, right-hand-side tile), block fastest.
-  // A CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...; while it works
-  // on one, the next one's operator tiles and fields are prefetched into L2.
-  const int nbc = g.nblocks / 2;
-  const int nitems = nbc * ((rp.n + tile - 1) / tile);
-  // the i-th block of this colour: blocks 2i and 2i+1 differ in colour
-  auto block_of = [&](int bi) {
-    int bb = 2 * bi, bc[4];
-    block_coords(g, bb, bc);
-    return (((bc[0] + bc[1] + bc[2] + bc[3]) & 1) != colour) ? bb + 1 : bb;
-  };
-#pragma unroll 1
-  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-  const int b = block_of(item % nbc), rt = item / nbc;
-  if (threadIdx.x == 0 && item + (int)gridDim.x < nitems) {
-    const int nitem = item + gridDim.x, nb = block_of(nitem % nbc), nrt = nitem / nbc;
-    prefetch_l2((const P *)links + (size_t)nb * 36 * Vb, 36u * Vb * sizeof(P));
-    prefetch_l2((const P *)clov + (size_t)nb * 36 * Vb, 36u * Vb * sizeof(P));
-    prefetch_l2((const P *)cinv + (size_t)nb * 36 * Vh, 36u * Vh * sizeof(P));
-    constexpr int NC = spinor_chunks<S>();
-    for (int q = 0; q < tile; q++) {
-      const int r = nrt * tile + q;
-      if (r >= rp.n) break;
-      const size_t off = (size_t)nb * NC * Vb * 16;
-      prefetch_l2((const char *)rp.in[r] + off, NC * Vb * 16u);
-      if (!self_zero) prefetch_l2((const char *)rp.out[r] + off, NC * Vb * 16u);
-    }
-  }
-
-  // Staging by bulk copies (the TMA engine), issued by thread 0 and tracked
-  // by the mbarrier: the links tile (36 x Vb pairs, contiguous per block),
-  // and for STAGE 1 the odd half of every clover row (36 pieces of Vh pairs)
-  // and the even-site inverse tile (36 x Vh, contiguous). Every size is a
-  // multiple of 16 bytes (Vh is even) and every address 16-byte aligned.
-  Tile<P> Lt, Ao, Ai;
-  if constexpr (STAGE == 1) {
-    P *sl = (P *)tiles;
-    P *sa = sl + (size_t)36 * Vb;
-    P *si = sa + (size_t)36 * Vh;
-    if (threadIdx.x == 0) {
-      const P *gl = (const P *)links + (size_t)b * 36 * Vb;
-      const P *ga = (const P *)clov + (size_t)b * 36 * Vb;
-      const unsigned lb = 36u * Vb * sizeof(P), rb = (unsigned)(Vh * sizeof(P));
-      fence_proxy_async();
-      mbar_arrive_expect(mbar, lb + 72u * rb);
-      bulk_g2s(sl, gl, lb, mbar);
-      for (int i = 0; i < 36; i++) bulk_g2s(sa + (size_t)i * Vh, ga + (size_t)i * Vb + Vh, rb, mbar);
-      bulk_g2s(si, (const P *)cinv + (size_t)b * 36 * Vh, 36u * rb, mbar);
-    }
-    Lt = {sl, Vb};
-    Ao = {sa, Vh};
-    Ai = {si, Vh};
-  } else if constexpr (STAGE == 2) {
-    P *sl = (P *)tiles;
-    if (threadIdx.x == 0) {
-      const unsigned lb = 36u * Vb * sizeof(P);
-      fence_proxy_async();
-      mbar_arrive_expect(mbar, lb);
-      bulk_g2s(sl, (const P *)links + (size_t)b * 36 * Vb, lb, mbar);
-    }
-    Lt = {sl, Vb};
-    Ao = {(const P *)clov + (size_t)b * 36 * Vb + Vh, Vb};
-    Ai = {(const P *)cinv + (size_t)b * 36 * Vh, Vh};
-  } else {
-    Lt = {(const P *)links + (size_t)b * 36 * Vb, Vb};
-    Ao = {(const P *)clov + (size_t)b * 36 * Vb + Vh, Vb};
-    Ai = {(const P *)cinv + (size_t)b * 36 * Vh, Vh};
-  }
-
-  const Site se = decode(g, b, j), so = decode(g, b, Vh + j);
-  const uint2 nbr_e = inner_neighbours(g, se, h), nbr_o = inner_neighbours(g, so, h);
-  // right-hand sides blockIdx.y * tile ... share the staged tiles
-#pragma unroll 1
-  for (int rr = 0; rr < tile; rr++) {
-    const int r = rt * tile + rr;
-    if (r >= rp.n) break;
-    const void *bf = rp.in[r];
-    void *xf = rp.out[r];
-    cpx<C> r_e[6], r_o[6];
-
-    // ---- 2. block residual r = b - D x (halves h of the even and odd site)
-    {
-      Spinor<C> bb;
-      load_spinor<S, C>(bf, g, b, j, bb);
-      half_of(bb, h, r_e);
-      load_spinor<S, C>(bf, g, b, Vh + j, bb);
-      half_of(bb, h, r_o);
-    }
-    if (!(self_zero && halo_zero)) {
-  #pragma unroll 1
-      for (int par = 0; par < 2; par++) {
-        const Site &t = par ? so : se;
-        Spinor<C> part;
-        hops_global<S, C>(g, t, h, links, xf, self_zero, halo_zero, part);
-        cpx<C> hx[6], ax[6] = {}, m[18], xh[6];
-        exchange(xch, Vh, j, h, part, hx);
-        if (!self_zero) {
-          Spinor<C> xs;
-          load_spinor<S, C>(xf, g, b, t.s, xs);
-          half_of(xs, h, xh);
-          load_clover_block<S, C>(clov, Vb, b, t.s, h, m);
-          herm6_mv(m, xh, ax);
-        }
-  #pragma unroll
-        for (int i = 0; i < 6; i++) {
-          cpx<C> d = {ax[i].re + hx[i].re, ax[i].im + hx[i].im};
-          if (par) { r_o[i].re -= d.re; r_o[i].im -= d.im; }
-          else     { r_e[i].re -= d.re; r_e[i].im -= d.im; }
-        }
-        __syncthreads();
-      }
-    }
-    if constexpr (STAGE != 0) {
-      // the staging of this item completes phase `phase` of the barrier;
-      // a CTA whose wait expired leaves as a whole (the flag is raised)
-      if (rr == 0) {
-        const bool ok = mbar_wait(mbar_s, phase);
-        if (__syncthreads_or(!ok)) {
-          wait_expired(mbar_s, phase);
-          return;
-        }
-        phase ^= 1u;
-      }
-    }
-
-    // ---- 3.-5. Schur right-hand side, MR steps, reconstruction: one loop of
-    // half-steps, odd steps on the odd site (input te), even steps on the even
-    // site (input rho). Step 0: rho = r_o - D_oe A_ee^-1 r_e. Steps 1..2 n_MR:
-    // te = A_ee^-1 D_eo rho, then p = A_oo rho - D_oe te and the MR update.
-    // Last step: e_e = A_ee^-1 (r_e - D_eo e_o).
-    cpx<C> m[18], tmp[6], rh[6], eo[6], ee[6];
-    tile_block(Ai, j, h, m);
-    herm6_mv(m, r_e, tmp);
-  #pragma unroll
-    for (int i = 0; i < 6; i++) {
-      te[(6 * h + i) * Vh + j] = tmp[i];
-      eo[i] = {0, 0};
-      rh[i] = {0, 0};
-    }
-    __syncthreads();
-    const int last = 2 * nmr + 1;
-  #pragma unroll 1
-    for (int step = 0; step <= last; step++) {
-      const bool odd = (step & 1) == 0;
-      Spinor<C> part;
-      hops_inner(Vh, odd ? Vh + j : j, h, odd ? nbr_o : nbr_e, odd ? 0 : Vh, odd ? te : rho, Lt, part);
-      cpx<C> hv[6], u[6], mu[6];
-      exchange(xch, Vh, j, h, part, hv);
-      // one clover multiply per step: A_oo rho (odd), A_ee^-1 D_eo rho (even),
-      // A_ee^-1 (r_e - D_eo e_o) (last)
-  #pragma unroll
-      for (int i = 0; i < 6; i++)
-        u[i] = odd ? rh[i] : (step == last ? cpx<C>{r_e[i].re - hv[i].re, r_e[i].im - hv[i].im} : hv[i]);
-      tile_block(odd ? Ao : Ai, j, h, m);
-      herm6_mv(m, u, mu);
-      if (odd) {
-        if (step == 0) {
-  #pragma unroll
-          for (int i = 0; i < 6; i++) rh[i] = {r_o[i].re - hv[i].re, r_o[i].im - hv[i].im};
-        } else {
-          cpx<C> p[6];
-          C pr_re = 0, pr_im = 0, pp = 0;
-  #pragma unroll
-          for (int i = 0; i < 6; i++) {
-            p[i] = {mu[i].re - hv[i].re, mu[i].im - hv[i].im};
-            pr_re += p[i].re * rh[i].re + p[i].im * rh[i].im;
-            pr_im += p[i].re * rh[i].im - p[i].im * rh[i].re;
-            pp += p[i].re * p[i].re + p[i].im * p[i].im;
-          }
-          block_sum3(pr_re, pr_im, pp, red);
-          C a_re = 0, a_im = 0;
-          if (pp > (C)0) {
-            a_re = pr_re / pp;
-            a_im = pr_im / pp;
-          }
-  #pragma unroll
-          for (int i = 0; i < 6; i++) {
-            eo[i].re += a_re * rh[i].re - a_im * rh[i].im;
-            eo[i].im += a_re * rh[i].im + a_im * rh[i].re;
-            rh[i].re -= a_re * p[i].re - a_im * p[i].im;
-            rh[i].im -= a_re * p[i].im + a_im * p[i].re;
-          }
-        }
-        // the even half-step after the last MR update reads e_o instead of rho
-        const bool last_odd = step == 2 * nmr;
-  #pragma unroll
-        for (int i = 0; i < 6; i++) rho[(6 * h + i) * Vh + j] = last_odd ? eo[i] : rh[i];
-      } else if (step == last) {
-  #pragma unroll
-        for (int i = 0; i < 6; i++) ee[i] = mu[i];
-      } else {
-  #pragma unroll
-        for (int i = 0; i < 6; i++) te[(6 * h + i) * Vh + j] = mu[i];
-      }
-      __syncthreads();
-    }
-
-    // ---- x += e: gather both halves through shared memory, then half 0
-    // writes the even site j and half 1 the odd site j
-  #pragma unroll
-    for (int i = 0; i < 6; i++) {
-      te[(6 * h + i) * Vh + j] = ee[i];
-      xch[(6 * h + i) * Vh + j] = eo[i];
-    }
-    __syncthreads();
-    {
-      const cpx<C> *src = h ? xch : te;
-      const int s = h ? Vh + j : j;
-      Spinor<C> xs, e;
-      vec_load(src, Vh, j, e);
-      if (self_zero) {
-        xs = e;
-      } else {
-        load_spinor<S, C>(xf, g, b, s, xs);
-  #pragma unroll
-        for (int i = 0; i < 12; i++) {
-          xs.c[i].re += e.c[i].re;
-          xs.c[i].im += e.c[i].im;
-        }
-      }
-      store_spinor<S, C>(xf, g, b, s, xs);
-    }
-    __syncthreads();   // shared vectors are reused by the next right-hand side
-  }
-  }  // work items
-}
-
-template <typename S, int STAGE, int MINB, int NT = 256>
-int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, int tile, bool persistent,
-          cudaStream_t st) {
-  size_t smem = SapSmem<S>::bytes(g, STAGE);
-  auto kern = k_sap_phase<S, STAGE, MINB, NT>;
-  // raise the kernel's dynamic shared-memory limit once (never during a capture)
-  static std::mutex mu;
-  static int raised = 0;
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    if (raised < (int)smem) {
-      DD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-      raised = 227 * 1024;
-    }
-  }
-  const int nitems = g.nblocks / 2 * ((rp.n + tile - 1) / tile);
-  int grid = nitems;
-  if (persistent) {
-    int dev = 0, sms = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, g.Vb, smem);
-    if (occ < 1) occ = 1;
-    grid = std::min(nitems, sms * occ);
-  }
-  for (int sw = 0; sw < p.sweeps; sw++)
-    for (int colour = 0; colour < 2; colour++) {
-      // with x = 0 on entry: the first phase sees x = 0 everywhere, the
-      // second still has x = 0 on its own (colour-1) blocks
-      int self_zero = (p.x_is_zero && sw == 0) ? 1 : 0;
-      int halo_zero = (p.x_is_zero && sw == 0 && colour == 0) ? 1 : 0;
-      kern<<<grid, g.Vb, smem, st>>>(g, f.links, f.clov, f.cinv, rp, colour, self_zero, halo_zero, p.mr_steps,
-                                     tile);
-      DD_LAUNCHED();
-    }
-  return DD_OK;
-}
+}  // namespace
 
 // The 2 x sweeps phase launches of one smoother application are captured once
 // into a CUDA graph per (operator, parameters, variant, field pointers) and
@@ -614,8 +109,8 @@ struct GraphCache {
 };
 static GraphCache g_graphs;
 
-static int launch_as_graph(const std::string &key, int variant, int nkernels, const OpFields &f, const RhsPtrs &rp,
-                           const std::function<int()> &enqueue, cudaStream_t st) {
+int sap_launch_as_graph(const std::string &key, int variant, int nkernels, const OpFields &f, const RhsPtrs &rp,
+                        const std::function<int()> &enqueue, cudaStream_t st) {
   const char *env = getenv("DD_SAP_GRAPHS");
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cap);
@@ -654,70 +149,6 @@ static int launch_as_graph(const std::string &key, int variant, int nkernels, co
   return cuda_fail(cudaGraphLaunch(exec, st), "sap graph launch");
 }
 
-// Launch variants: tiles staged in shared memory with one CTA per SM; tiles
-// staged with two CTAs per SM (fits when the storage is 16-bit); only the
-// links staged, with two CTAs per SM (when the full staging does not fit
-// twice); tiles read through L1/L2 with two CTAs per SM. Variants that do not
-// fit are skipped.
-// With several right-hand sides a CTA also solves `tile` of them with one
-// staging of its block's operator (rhs_tile; 0 lets the autotuner choose).
-template <typename S>
-int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
-  const size_t limit = 227 * 1024, half = 113 * 1024;
-  const bool stage1 = SapSmem<S>::bytes(g, 1) <= limit;
-  const bool stage2 = SapSmem<S>::bytes(g, 1) <= half;
-  const bool links2 = !stage2 && SapSmem<S>::bytes(g, 2) <= half;
-  const bool nost2 = SapSmem<S>::bytes(g, 0) <= half;
-  if (!stage1 && SapSmem<S>::bytes(g, 0) > limit) {
-    set_error("sap: block of %d sites needs more shared memory than available", g.Vb);
-    return DD_EINVAL;
-  }
-  int layouts[4], nl = 0;
-  if (g.Vb > 256) {
-    // 512-site blocks (e.g. 8 x 4^3): 512 threads, one CTA per SM
-    layouts[nl++] = stage1 ? 3 : 4;
-  } else {
-    if (stage1) layouts[nl++] = 0;
-    if (stage2) layouts[nl++] = 1;
-    if (links2) layouts[nl++] = 5;
-    if (nost2 || !stage1) layouts[nl++] = 2;
-  }
-  int tiles[6], nt = 0;
-  if (p.rhs_tile > 0) {
-    tiles[nt++] = p.rhs_tile < rp.n ? p.rhs_tile : rp.n;
-  } else {
-    const int cand[5] = {1, 2, 4, 8, 12};
-    for (int c : cand)
-      if (c <= rp.n) tiles[nt++] = c;
-  }
-  // variant k: layout k % nl, RHS tile (k / nl) % nt, persistent grid if k >= nl * nt
-  auto run = [&](int k) {
-    const int layout = layouts[k % nl], tile = tiles[(k / nl) % nt];
-    const bool pers = k >= nl * nt;
-    switch (layout) {
-      case 1: return sap_t<S, 1, 2>(g, f, p, rp, tile, pers, st);
-      case 2: return sap_t<S, 0, 2>(g, f, p, rp, tile, pers, st);
-      case 3: return sap_t<S, 1, 1, 512>(g, f, p, rp, tile, pers, st);
-      case 4: return sap_t<S, 0, 1, 512>(g, f, p, rp, tile, pers, st);
-      case 5: return sap_t<S, 2, 2>(g, f, p, rp, tile, pers, st);
-      default: return sap_t<S, 1, 1>(g, f, p, rp, tile, pers, st);
-    }
-  };
-  int k = 0;
-  std::string key = tune_key("sap", g, f.prec, rp.n) + "|" + std::to_string(p.sweeps) + "," +
-                    std::to_string(p.mr_steps) + "," + std::to_string(p.rhs_tile);
-  // x is pure output when x_is_zero, so trial runs leave the same result
-  if (p.x_is_zero) {
-    int rc = tuned_variant(key, 2 * nl * nt, run, st, &k);
-    if (rc) return rc;
-  } else {
-    int c = tune_lookup(key);
-    k = c >= 0 ? c : 0;
-  }
-  return launch_as_graph(key, k, 2 * p.sweeps, f, rp, [&] { return run(k); }, st);
-}
-
-}  // namespace
 
 int wait_selftest(int expire) {
   uint4 *src = nullptr;
@@ -727,7 +158,9 @@ int wait_selftest(int expire) {
   const uint4 pat = make_uint4(0x01234567u, 0x89abcdefu, 0x0f1e2d3cu, 0x4b5a6978u);
   int got = -1, rc = cuda_fail(cudaMemcpy(src, &pat, sizeof(pat), cudaMemcpyHostToDevice), "wait selftest");
   if (rc == DD_OK) {
-    k_wait_selftest<<<1, 32>>>(src, expire, res);
+    unsigned *cnt = sap_timeout_counter();
+    if (!cnt) return cuda_fail(cudaErrorInvalidSymbol, "wait selftest");
+    k_wait_selftest<<<1, 32>>>(src, expire, res, cnt);
     rc = launched("k_wait_selftest");
   }
   if (rc == DD_OK) rc = cuda_fail(cudaMemcpy(&got, res, sizeof(int), cudaMemcpyDeviceToHost), "wait selftest");
@@ -769,11 +202,15 @@ int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const R
     set_error("sap: blocks of more than 512 sites are not supported (got %d)", g.Vb);
     return DD_EINVAL;
   }
+  if (!sap_timeout_counter()) {   // resolved here, before any graph capture of the launches
+    set_error("sap: wait counter not available");
+    return DD_ECUDA;
+  }
   switch (f.prec) {
-    case DD_F64: return sap_variants<double>(g, f, p, rp, st);
-    case DD_F32: return sap_variants<float>(g, f, p, rp, st);
-    case DD_F16: return sap_variants<__half>(g, f, p, rp, st);
-    case DD_BF16: return sap_variants<__nv_bfloat16>(g, f, p, rp, st);
+    case DD_F64: return sap_run_f64(g, f, p, rp, st);
+    case DD_F32: return sap_run_f32(g, f, p, rp, st);
+    case DD_F16: return sap_run_f16(g, f, p, rp, st);
+    case DD_BF16: return sap_run_bf16(g, f, p, rp, st);
   }
   set_error("sap: bad precision %d", f.prec);
   return DD_EINVAL;

@@ -1,0 +1,8 @@
+// Schwarz kernel instances for __nv_bfloat16 storage (see dd_sap.cu).
+#include "dd_sap_kernels.cuh"
+
+namespace dd {
+int sap_run_bf16(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
+  return sap_variants<__nv_bfloat16>(g, f, p, rp, st);
+}
+}  // namespace dd

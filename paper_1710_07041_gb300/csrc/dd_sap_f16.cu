@@ -1,0 +1,8 @@
+// Schwarz kernel instances for __half storage (see dd_sap.cu).
+#include "dd_sap_kernels.cuh"
+
+namespace dd {
+int sap_run_f16(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
+  return sap_variants<__half>(g, f, p, rp, st);
+}
+}  // namespace dd

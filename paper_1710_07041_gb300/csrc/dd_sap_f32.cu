@@ -1,0 +1,8 @@
+// Schwarz kernel instances for float storage (see dd_sap.cu).
+#include "dd_sap_kernels.cuh"
+
+namespace dd {
+int sap_run_f32(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
+  return sap_variants<float>(g, f, p, rp, st);
+}
+}  // namespace dd
