@@ -32,10 +32,12 @@ __device__ __forceinline__ void dirac_dir(const Geom &g, const Site &t, const vo
 
 // TPB threads per CTA; MINB resident CTAs per SM requested from the compiler
 // (caps registers so more warps keep loads in flight).
-template <typename S, int TPB, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) k_dirac(Geom g, const void *__restrict__ links,
+// SHAPE: the block shape as compile-time constants (see block_shape), or 0.
+template <typename S, int TPB, int MINB, int SHAPE>
+__global__ void __launch_bounds__(TPB, MINB) k_dirac(Geom g_in, const void *__restrict__ links,
                                                      const void *__restrict__ clov, const RhsPtrs p) {
   using C = typename Store<S>::comp_t;
+  const Geom g = block_shape<SHAPE>(g_in);
   const int nrhs = p.n;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= g.V * nrhs) return;
@@ -57,7 +59,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_dirac(Geom g, const void *__restr
 template <typename S, int TPB, int MINB>
 int dirac_v(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st) {
   long long n = g.V * p.n;
-  k_dirac<S, TPB, MINB><<<(unsigned)((n + TPB - 1) / TPB), TPB, 0, st>>>(g, f.links, f.clov, p);
+  const unsigned grid = (unsigned)((n + TPB - 1) / TPB);
+  if (shape_of(g) == 1) k_dirac<S, TPB, MINB, 1><<<grid, TPB, 0, st>>>(g, f.links, f.clov, p);
+  else k_dirac<S, TPB, MINB, 0><<<grid, TPB, 0, st>>>(g, f.links, f.clov, p);
   return launched("k_dirac");
 }
 

@@ -144,6 +144,39 @@ __host__ __device__ inline long long canonical_index(const Geom &g, int b, int s
   return c[0] + g.L[0] * (c[1] + (long long)g.L[1] * (c[2] + (long long)g.L[2] * c[3]));
 }
 
+// SHAPE: 0 block shape from g at run time; 1 the 4^4 block, 2 the 8x4^3
+// block (T x Z x Y x X) as compile-time constants, so that every tile and
+// shared-vector stride is an immediate offset instead of index arithmetic.
+template <int SHAPE>
+__device__ __forceinline__ Geom block_shape(Geom g) {
+  if constexpr (SHAPE == 1) {
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+      g.bd[mu] = 4;
+      g.lbd[mu] = 2;
+    }
+    g.Vb = 256;
+    g.Vh = 128;
+  } else if constexpr (SHAPE == 2) {
+#pragma unroll
+    for (int mu = 0; mu < 3; mu++) {
+      g.bd[mu] = 4;
+      g.lbd[mu] = 2;
+    }
+    g.bd[3] = 8;
+    g.lbd[3] = 3;
+    g.Vb = 512;
+    g.Vh = 256;
+  }
+  return g;
+}
+// the SHAPE a launch may use for geometry g (0: none matches)
+__host__ __device__ inline int shape_of(const Geom &g) {
+  if (g.bd[0] == 4 && g.bd[1] == 4 && g.bd[2] == 4 && g.bd[3] == 4) return 1;
+  if (g.bd[0] == 4 && g.bd[1] == 4 && g.bd[2] == 4 && g.bd[3] == 8) return 2;
+  return 0;
+}
+
 // ------------------------------------------------------------- precisions
 template <typename S> struct Store;
 template <> struct Store<double> {

@@ -262,39 +262,6 @@ template <typename S> struct SapSmem {
 // STAGE: 0 operator tiles read through L1/L2; 1 links, A_oo and A_ee^-1 staged
 // in shared memory; 2 links staged, the clover blocks (each read by one
 // thread only) through L1/L2, which halves the footprint.
-// SHAPE: 0 block shape from g at run time; 1 the 4^4 block, 2 the 8x4^3
-// block (T x Z x Y x X) as compile-time constants, so that every tile and
-// shared-vector stride is an immediate offset instead of index arithmetic.
-template <int SHAPE>
-__device__ __forceinline__ Geom block_shape(Geom g) {
-  if constexpr (SHAPE == 1) {
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-      g.bd[mu] = 4;
-      g.lbd[mu] = 2;
-    }
-    g.Vb = 256;
-    g.Vh = 128;
-  } else if constexpr (SHAPE == 2) {
-#pragma unroll
-    for (int mu = 0; mu < 3; mu++) {
-      g.bd[mu] = 4;
-      g.lbd[mu] = 2;
-    }
-    g.bd[3] = 8;
-    g.lbd[3] = 3;
-    g.Vb = 512;
-    g.Vh = 256;
-  }
-  return g;
-}
-// the SHAPE a launch may use for geometry g (0: none matches)
-inline int shape_of(const Geom &g) {
-  if (g.bd[0] == 4 && g.bd[1] == 4 && g.bd[2] == 4 && g.bd[3] == 4) return 1;
-  if (g.bd[0] == 4 && g.bd[1] == 4 && g.bd[2] == 4 && g.bd[3] == 8) return 2;
-  return 0;
-}
-
 template <typename S, int STAGE, int MINB, int NT, int SHAPE>
 __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *__restrict__ links,
                                                    const void *__restrict__ clov, const void *__restrict__ cinv,
