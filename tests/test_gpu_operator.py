@@ -121,3 +121,21 @@ def test_reported_true_residual_matches_oracle(prec):
     assert want <= 1e-10
     assert abs(info[0]["true_rel_residual"] - want) <= 0.02 * want, (info[0]["true_rel_residual"], want)
     s.close()
+
+
+def test_apply_D_more_rhs_than_one_launch():
+    """70 right-hand sides: the library splits them into launches of at most
+    64 (the per-launch pointer table); every result equals its single apply."""
+    s = Setup((4, 4, 4, 8), (2, 2, 2, 2), prec=dd.F32, seed=10)
+    n = 70
+    psi = np.stack([synth.gaussian_spinor(s.V, 200 + r) for r in range(n)])
+    fin = s.lat.to_field(psi, dd.F32)
+    fout = s.lat.new_field(dd.F32, n)
+    s.op.apply_D(dd.F32, fin, fout, nrhs=n)
+    batched = s.lat.from_field(fout, dd.F32, n)
+    for r in (0, 63, 64, 69):
+        o1 = s.lat.new_field(dd.F32)
+        s.op.apply_D(dd.F32, s.lat.to_field(psi[r], dd.F32), o1)
+        assert np.array_equal(s.lat.from_field(o1, dd.F32), batched[r])
+    assert relerr(batched[69], s.ref.apply(psi[69])) <= 1e-6
+    s.close()

@@ -103,3 +103,31 @@ def test_sap_reduces_residual():
         res.append(relerr(s.ref.apply(x), b))
     assert res[0] < 1 and res[1] < res[0] and res[2] < res[1]
     s.close()
+
+
+@pytest.mark.parametrize("prec", [dd.F64, dd.F32])
+def test_sap_zero_mr_steps(prec):
+    """Degenerate block solve: with no MR step e_o = 0 and e_e = A_ee^-1 r_e
+    on every block; the oracle takes the same reading."""
+    s = Setup((8, 8, 8, 8), (4, 4, 4, 4), prec=prec, seed=21)
+    b = synth.gaussian_spinor(s.V, 22)
+    fb, fx = s.lat.to_field(b, prec), s.lat.new_field(prec)
+    s.op.sap_smooth(fb, fx, 2, 0)
+    assert relerr(s.lat.from_field(fx, prec), s.ref.sap(s.block, b, 2, 0)) <= TOL[prec]
+    s.close()
+
+
+def test_sap_more_rhs_than_one_launch():
+    """66 right-hand sides in one call (two launches of the pointer table)
+    equal their single smoother applications bit for bit."""
+    s = Setup((4, 4, 4, 8), (2, 2, 2, 2), prec=dd.F32, seed=23)
+    n = 66
+    bs = np.stack([synth.gaussian_spinor(s.V, 300 + r) for r in range(n)])
+    fb, fx = s.lat.to_field(bs, dd.F32), s.lat.new_field(dd.F32, n)
+    s.op.sap_smooth(fb, fx, 2, 3, nrhs=n)
+    batched = s.lat.from_field(fx, dd.F32, n)
+    for r in (0, 64, 65):
+        x1 = s.lat.new_field(dd.F32)
+        s.op.sap_smooth(s.lat.to_field(bs[r], dd.F32), x1, 2, 3)
+        assert np.array_equal(s.lat.from_field(x1, dd.F32), batched[r])
+    s.close()
