@@ -69,6 +69,12 @@ enum {
 
 /* storage precisions; arithmetic is FP32 for all but DD_F64 */
 enum { DD_F64 = 0, DD_F32 = 1, DD_F16 = 2, DD_BF16 = 3 };
+/* dd_apply_D only (no counterpart in the paper): FP64 input and output
+ * fields, double-float arithmetic (pairs of FP32, ~48-bit significands) on
+ * the operator's pre-split FP64 links and clover; the operator a
+ * mixed-precision dd_solve uses for its true residual. Operators created with
+ * a DD_F64 smoother do not hold these fields (DD_EINVAL). */
+enum { DD_F64_DF = 4 };
 
 /* data location flags for dd_solve / requests */
 enum { DD_HOST = 0, DD_DEVICE = 1 };

@@ -18,6 +18,7 @@ import numpy as np
 from . import build as _build
 
 F64, F32, F16, BF16 = 0, 1, 2, 3
+F64_DF = 4   # apply_D only: FP64 fields in and out, double-float arithmetic
 PREC = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
 HOST, DEVICE = 0, 1
 QUEUED, RUNNING, DONE, FAILED, CANCELLED = 0, 1, 2, 3, 4

@@ -84,6 +84,7 @@ void release_op(Op *op) {
   free_fields(op->f64);
   free_fields(op->f32);
   if (op->prec == DD_F16 || op->prec == DD_BF16) free_fields(op->fp);
+  free_fields(op->fdf);
   release_gauge(op->gauge);
   op->magic = 0;
   delete op;
@@ -233,6 +234,19 @@ static int create_op(Gauge *ga, double c_sw, double m0, int prec, Fill fill, dd_
     if (rc == DD_OK)
       rc = launch_convert_pairs(prec, (const double *)op->f64.cinv, op->fp.cinv, (size_t)g.V / 2 * 36, st);
   }
+  if (rc == DD_OK && prec != DD_F64) {
+    // double-float copies of the FP64 links and site blocks (the true residual of mixed-precision solves)
+    op->fdf.prec = DD_PREC_DF;
+    const size_t np = (size_t)g.V * 36;
+    if (cudaMalloc(&op->fdf.links, np * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc(&op->fdf.clov, np * sizeof(float4)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("dd_create_op: out of device memory");
+      rc = DD_ENOMEM;
+    }
+    if (rc == DD_OK) rc = launch_split_pairs((const double *)op->f64.links, op->fdf.links, np, st);
+    if (rc == DD_OK) rc = launch_split_pairs((const double *)op->f64.clov, op->fdf.clov, np, st);
+  }
   int hbad = 0;
   if (rc == DD_OK) rc = cuda_fail(cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost), "dd_create_op");
   cudaFree(bad);
@@ -244,6 +258,7 @@ static int create_op(Gauge *ga, double c_sw, double m0, int prec, Fill fill, dd_
     free_fields(op->f64);
     free_fields(op->f32);
     free_fields(op->fp);
+    free_fields(op->fdf);
     delete op;
     return rc;
   }
@@ -371,6 +386,24 @@ int dd_apply_D(dd_op_t opp, int prec, const void *in, void *out, int nrhs, void 
   if (!op || op->magic != MAGIC_OP || !in || !out || in == out || nrhs < 1) {
     set_error("dd_apply_D: bad argument");
     return DD_EINVAL;
+  }
+  if (prec == DD_F64_DF) {
+    if (!op->fdf.links) {
+      set_error("dd_apply_D: this operator holds no double-float fields (FP64 smoother)");
+      return DD_EINVAL;
+    }
+    const Geom &g = op->lat->g;
+    const size_t fb = (size_t)g.V * 24 * 8, n = (size_t)g.V * 12;
+    void *tmp = nullptr;   // the split input, one right-hand side at a time
+    DD_CUDA(cudaMalloc(&tmp, fb));
+    int rc = DD_OK;
+    for (int r = 0; r < nrhs && rc == DD_OK; r++) {
+      rc = launch_split_pairs((const double *)((const char *)in + r * fb), tmp, n, (cudaStream_t)stream);
+      if (rc == DD_OK) rc = launch_dirac_df(g, op->fdf, contiguous(tmp, (char *)out + r * fb, 1, fb), (cudaStream_t)stream);
+    }
+    cudaStreamSynchronize((cudaStream_t)stream);
+    cudaFree(tmp);
+    return rc;
   }
   const OpFields *f = fields_for(op, prec);
   if (!f) {

@@ -33,7 +33,8 @@ __device__ __forceinline__ void dirac_dir(const Geom &g, const Site &t, const vo
 // TPB threads per CTA; MINB resident CTAs per SM requested from the compiler
 // (caps registers so more warps keep loads in flight).
 // SHAPE: the block shape as compile-time constants (see block_shape), or 0.
-template <typename S, int TPB, int MINB, int SHAPE>
+// SO: storage of the output fields (the input's, or FP64 for double-float inputs).
+template <typename S, int TPB, int MINB, int SHAPE, typename SO = S>
 __global__ void __launch_bounds__(TPB, MINB) k_dirac(Geom g_in, const void *__restrict__ links,
                                                      const void *__restrict__ clov, const RhsPtrs p) {
   using C = typename Store<S>::comp_t;
@@ -53,15 +54,15 @@ __global__ void __launch_bounds__(TPB, MINB) k_dirac(Geom g_in, const void *__re
   dirac_dir<1, S, C>(g, st, links, inr, acc);
   dirac_dir<2, S, C>(g, st, links, inr, acc);
   dirac_dir<3, S, C>(g, st, links, inr, acc);
-  store_spinor<S, C>(p.out[r], g, b, s, acc);
+  store_spinor<SO, C>(p.out[r], g, b, s, acc);
 }
 
-template <typename S, int TPB, int MINB>
+template <typename S, int TPB, int MINB, typename SO = S>
 int dirac_v(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st) {
   long long n = g.V * p.n;
   const unsigned grid = (unsigned)((n + TPB - 1) / TPB);
-  if (shape_of(g) == 1) k_dirac<S, TPB, MINB, 1><<<grid, TPB, 0, st>>>(g, f.links, f.clov, p);
-  else k_dirac<S, TPB, MINB, 0><<<grid, TPB, 0, st>>>(g, f.links, f.clov, p);
+  if (shape_of(g) == 1) k_dirac<S, TPB, MINB, 1, SO><<<grid, TPB, 0, st>>>(g, f.links, f.clov, p);
+  else k_dirac<S, TPB, MINB, 0, SO><<<grid, TPB, 0, st>>>(g, f.links, f.clov, p);
   return launched("k_dirac");
 }
 
@@ -72,17 +73,16 @@ int dirac_v(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st)
 // read by the same SM.
 constexpr int DIRAC_VARIANTS = 4;
 
-template <typename S>
+template <typename S, typename SO = S>
 int dirac_t(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st) {
   auto run = [&](int v) {
-    if constexpr (Store<S>::prec == DD_F64) {
-      // FP64 values take two registers each: looser caps (the kernel is
-      // bound by GB300's FP64 rate, and spilling adds to that)
+    if constexpr (Store<S>::prec == DD_F64 || Store<S>::prec == DD_PREC_DF) {
+      // FP64 and double-float values take two registers each: looser caps
       switch (v) {
-        case 1: return dirac_v<S, 128, 3>(g, f, p, st);
-        case 2: return dirac_v<S, 256, 2>(g, f, p, st);
-        case 3: return dirac_v<S, 256, 1>(g, f, p, st);
-        default: return dirac_v<S, 128, 4>(g, f, p, st);
+        case 1: return dirac_v<S, 128, 3, SO>(g, f, p, st);
+        case 2: return dirac_v<S, 256, 2, SO>(g, f, p, st);
+        case 3: return dirac_v<S, 256, 1, SO>(g, f, p, st);
+        default: return dirac_v<S, 128, 4, SO>(g, f, p, st);
       }
     } else {
       switch (v) {
@@ -124,6 +124,14 @@ int launch_dirac(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_
   }
   set_error("apply_D: precision %d not available", f.prec);
   return DD_EINVAL;
+}
+
+int launch_dirac_df(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st) {
+  if (p.n < 1 || p.n > MAX_RHS || f.prec != DD_PREC_DF || !f.links) {
+    set_error("apply_D (double-float): double-float fields and 1..%d right-hand sides", MAX_RHS);
+    return DD_EINVAL;
+  }
+  return dirac_t<dfs, double>(g, f, p, st);
 }
 
 int launch_dirac(const Geom &g, const OpFields &f, const void *in, void *out, int nrhs, cudaStream_t st) {

@@ -390,6 +390,20 @@ int launch_convert_pairs(int prec, const double *in, void *out, size_t n, cudaSt
   return launched("k_convert_pairs");
 }
 
+// FP64 complex -> double-float: hi = RN(v), lo = RN(v - hi) (v - hi is exact)
+__global__ void k_split_pairs(const double2 *__restrict__ in, float4 *out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 d = in[i];
+    const float rh = __double2float_rn(d.x), ih = __double2float_rn(d.y);
+    out[i] = make_float4(rh, __double2float_rn(d.x - (double)rh), ih, __double2float_rn(d.y - (double)ih));
+  }
+}
+
+int launch_split_pairs(const double *in, void *out, size_t n, cudaStream_t st) {
+  k_split_pairs<<<2048, 256, 0, st>>>((const double2 *)in, (float4 *)out, n);
+  return launched("k_split_pairs");
+}
+
 int launch_load_clover(const Geom &g, const double *A_canon, double *clov64, double *cinv64, int *bad,
                        cudaStream_t st) {
   k_load_clover<<<grid_for(g.V, 128), 128, 0, st>>>(g, (const double2 *)A_canon, (double2 *)clov64,

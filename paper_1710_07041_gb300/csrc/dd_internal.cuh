@@ -204,7 +204,56 @@ template <> struct Store<__nv_bfloat16> {
   using comp_t = float;
 };
 
-inline size_t real_bytes(int prec) { return prec == DD_F64 ? 8 : prec == DD_F32 ? 4 : 2; }
+// Double-float numbers: an unevaluated sum hi + lo of two FP32 values
+// (|lo| <= ulp(hi) / 2), about 48 significant bits, from error-free FP32
+// transformations (Knuth's TwoSum, Dekker's FastTwoSum, the FMA-exact
+// product). GB300 runs FP64 at a small fraction of its FP32 rate; this type
+// runs the true residual's Dslash of a mixed-precision solve on the FP32
+// pipes. Each operation has a relative error of a few units of 2^-44 of its
+// operands (the "sloppy" double-float add and product). The library is not
+// built with reassociating fast-math flags, which would break them.
+struct dfl {
+  float hi, lo;
+  dfl() = default;
+  __host__ __device__ __forceinline__ dfl(int v) : hi((float)v), lo(0.f) {}
+  __host__ __device__ __forceinline__ dfl(float v) : hi(v), lo(0.f) {}
+  __host__ __device__ __forceinline__ dfl(float h, float l, int) : hi(h), lo(l) {}
+};
+__device__ __forceinline__ dfl df_fast2(float s, float e) {   // |s| >= |e|
+  const float h = s + e;
+  return dfl(h, e - (h - s), 0);
+}
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);   // TwoSum error of a.hi + b.hi
+  e += a.lo + b.lo;
+  return df_fast2(s, e);
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.hi, -a.lo, 0); }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);              // exact error of the product
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return df_fast2(p, e);
+}
+__device__ __forceinline__ dfl &operator+=(dfl &a, dfl b) { return a = a + b; }
+__device__ __forceinline__ dfl &operator-=(dfl &a, dfl b) { return a = a - b; }
+
+// Double-float storage (internal only): a complex number as float4
+// {re.hi, re.lo, im.hi, im.lo}, the FP64 fields' layout with each double
+// split once into hi + lo.
+constexpr int DD_PREC_DF = 100;
+struct dfs {};
+template <> struct Store<dfs> {
+  static constexpr int prec = DD_PREC_DF;
+  static constexpr int reals_per_chunk = 2;
+  using pair_t = float4;
+  using comp_t = dfl;
+};
+
+inline size_t real_bytes(int prec) { return (prec == DD_F64 || prec == DD_PREC_DF) ? 8 : prec == DD_F32 ? 4 : 2; }
 inline size_t pair_bytes(int prec) { return 2 * real_bytes(prec); }
 
 template <typename S> __host__ __device__ constexpr int spinor_chunks() { return 24 / Store<S>::reals_per_chunk; }
@@ -224,6 +273,9 @@ template <> __device__ __forceinline__ cpx<float> from_pair<float, __nv_bfloat16
   return {f.x, f.y};
 }
 
+template <> __device__ __forceinline__ cpx<dfl> from_pair<dfl, float4>(float4 v) {
+  return {dfl(v.x, v.y, 0), dfl(v.z, v.w, 0)};
+}
 template <typename P, typename C> __device__ __forceinline__ P to_pair(C re, C im);
 template <> __device__ __forceinline__ double2 to_pair<double2, double>(double re, double im) { return make_double2(re, im); }
 template <> __device__ __forceinline__ float2 to_pair<float2, float>(float re, float im) { return make_float2(re, im); }
@@ -247,6 +299,11 @@ template <> __device__ __forceinline__ __nv_bfloat162 to_pair<__nv_bfloat162, do
 // A spinor in registers: 12 complex, index 3*spin + colour.
 template <typename C> struct Spinor { cpx<C> c[12]; };
 
+// a compute value as FP64
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(float v) { return (double)v; }
+__device__ __forceinline__ double to_d(dfl v) { return (double)v.hi + (double)v.lo; }
+
 // Load spinor (b, s) from a field of storage S.
 template <typename S, typename C>
 __device__ __forceinline__ void load_spinor(const void *field, const Geom &g, int b, int s, Spinor<C> &out) {
@@ -259,6 +316,9 @@ __device__ __forceinline__ void load_spinor(const void *field, const Geom &g, in
       double2 v = __ldg((const double2 *)(base + c * cstride));
       out.c[c] = {(C)v.x, (C)v.y};
     }
+  } else if constexpr (Store<S>::prec == DD_PREC_DF) {
+#pragma unroll
+    for (int c = 0; c < 12; c++) out.c[c] = from_pair<C, float4>(__ldg((const float4 *)(base + c * cstride)));
   } else if constexpr (Store<S>::prec == DD_F32) {
 #pragma unroll
     for (int c = 0; c < 6; c++) {
@@ -285,7 +345,7 @@ __device__ __forceinline__ void store_spinor(void *field, const Geom &g, int b, 
   const size_t cstride = (size_t)g.Vb * 16;
   if constexpr (Store<S>::prec == DD_F64) {
 #pragma unroll
-    for (int c = 0; c < 12; c++) *(double2 *)(base + c * cstride) = make_double2(v.c[c].re, v.c[c].im);
+    for (int c = 0; c < 12; c++) *(double2 *)(base + c * cstride) = make_double2(to_d(v.c[c].re), to_d(v.c[c].im));
   } else if constexpr (Store<S>::prec == DD_F32) {
 #pragma unroll
     for (int c = 0; c < 6; c++)
@@ -501,6 +561,7 @@ struct Op {
   double c_sw, m0;
   int prec;             // smoother precision
   OpFields f64, f32, fp;  // fp = smoother precision fields (aliases f64/f32 when equal)
+  OpFields fdf;           // links and A split into double-float (mixed-precision ops: true residual)
   int refs;             // the caller's handle plus multigrid objects built on it
 };
 void release_op(Op *op);
@@ -530,6 +591,11 @@ int launch_build_clover(const Geom &g, const double *links_canon, double c_sw, d
 int launch_convert_pairs(int prec, const double *in, void *out, size_t npairs, cudaStream_t st);
 int launch_dirac(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st);
 int launch_dirac(const Geom &g, const OpFields &f, const void *in, void *out, int nrhs, cudaStream_t st);
+// y = D x with double-float fields (f = op->fdf) and double-float inputs p.in
+// (FP64 fields split by launch_split_pairs), FP64 outputs p.out
+int launch_dirac_df(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st);
+// n complex FP64 values -> double-float {hi, lo} pairs, same positions
+int launch_split_pairs(const double *in, void *out, size_t n, cudaStream_t st);
 // Schwarz sweeps; p.in = right-hand sides b, p.out = iterates x
 int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &sp, const RhsPtrs &p, cudaStream_t st);
 int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &sp, const void *b, void *x, int nrhs,

@@ -167,6 +167,9 @@ extern "C" int dd_solve_noalloc(dd_op_t opp, const dd_solve_params *p, const dou
     if (x_zero) {
       DD_CUDA(cudaMemsetAsync(w, 0, f64, st));
       x_zero = false;
+    } else if (df) {   // double-float Dslash on the pre-split fields, as dd_solve
+      if ((rc = launch_split_pairs(x, canon, n, st))) return rc;
+      if ((rc = launch_dirac_df(g, op->fdf, contiguous(canon, w, 1, f64), st))) return rc;
     } else if ((rc = launch_dirac(g, op->f64, x, w, 1, st))) {
       return rc;
     }

@@ -190,6 +190,9 @@ int BatchSolver::restart_phase(std::vector<Slot *> &R) {
   int rc;
   // D x for the slots whose x is not known to be zero (w = 0 for the others,
   // so that w = b - w below gives r = b)
+  // In a mixed-precision solve the Dslash runs in double-float arithmetic on
+  // the operator's pre-split fields: x is split into the slot's staging
+  // buffer (free at this point; FP64 field size); the result stays FP64.
   RhsPtrs rp;
   rp.n = 0;
   cudaEventRecord(ev_[0], st_);
@@ -199,10 +202,11 @@ int BatchSolver::restart_phase(std::vector<Slot *> &R) {
       s->x_zero = false;
       continue;
     }
-    rp.in[rp.n] = s->x;
+    if (df_ && (rc = launch_split_pairs(s->x, s->canon, n, st_))) return rc;
+    rp.in[rp.n] = df_ ? (const void *)s->canon : (const void *)s->x;
     rp.out[rp.n++] = s->w;
   }
-  if (rp.n && (rc = launch_dirac(g, op_->f64, rp, st_))) return rc;
+  if (rp.n && (rc = df_ ? launch_dirac_df(g, op_->fdf, rp, st_) : launch_dirac(g, op_->f64, rp, st_))) return rc;
   for (Slot *s : R) {
     double *hd = hdev_ + HSTRIDE * (s - slots_.data());
     if ((rc = blas_.xmy(s->b, s->w, n, st_))) return rc;

@@ -139,3 +139,25 @@ def test_apply_D_more_rhs_than_one_launch():
         assert np.array_equal(s.lat.from_field(o1, dd.F32), batched[r])
     assert relerr(batched[69], s.ref.apply(psi[69])) <= 1e-6
     s.close()
+
+
+@pytest.mark.parametrize("nrhs", [1, 2])
+def test_apply_D_double_float_matches_oracle(nrhs):
+    """DD_F64_DF: FP64 fields, double-float arithmetic on the operator's
+    pre-split fields (the true-residual operator of mixed-precision solves).
+    Each operation errs by a few units of 2^-44 of its operands; an output
+    sums ~100 terms of the input's size, so 1e-12 relative L2 leaves margin
+    while excluding FP32 arithmetic (~1e-7)."""
+    s = Setup((8, 8, 8, 16), (4, 4, 4, 4), eps=0.3, n_stout=1, c_sw=1.7, m0=-0.02, prec=dd.F32, seed=15)
+    b = np.stack([synth.gaussian_spinor(s.V, 16 + r) for r in range(nrhs)])
+    fin, fout = s.lat.to_field(b, dd.F64), s.lat.new_field(dd.F64, nrhs)
+    s.op.apply_D(dd.F64_DF, fin, fout, nrhs=nrhs)
+    got = s.lat.from_field(fout, dd.F64, nrhs).reshape(nrhs, s.V, 4, 3)
+    for r in range(nrhs):
+        assert relerr(got[r], s.ref.apply(b[r])) <= 1e-12
+    s.close()
+    s64 = Setup((4, 4, 4, 8), (2, 2, 2, 2), prec=dd.F64, seed=3)   # FP64 smoother: no split fields
+    f = s64.lat.new_field(dd.F64)
+    with pytest.raises(dd.DDError):
+        s64.op.apply_D(dd.F64_DF, f, s64.lat.new_field(dd.F64))
+    s64.close()
