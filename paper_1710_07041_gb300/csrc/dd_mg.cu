@@ -10,8 +10,9 @@
 //   D_c = P^dagger D P (Galerkin), a nearest-neighbour stencil on the block
 //      grid with 2N x 2N blocks: self, +mu and -mu for mu = x, y, z, t;
 //   M r = P e_c + SAP(r - D P e_c), e_c ~ D_c^-1 P^dagger r by GMRES.
-// Everything here works in FP32 (the preconditioner's precision); FGMRES
-// outside keeps the FP64/double-float outer arithmetic.
+// Everything here computes in FP32 (the preconditioner's precision; P and
+// D_c are stored in FP16); FGMRES outside keeps the FP64-class outer
+// arithmetic.
 #include <cmath>
 #include <cstring>
 #include <new>

@@ -4,11 +4,15 @@
 // SAP-preconditioned fine-grid Krylov solve, with mixed precision in the
 // spirit of Sec. 3.1's half-precision storage: the smoother works in the
 // operator's storage precision, while the Arnoldi orthogonalisation, the
-// least-squares update and the true residual are FP64. Preconditioned vectors
-// z_j are kept in FP32 (FP64 for an FP64 operator) and the Arnoldi product
-// D z_j uses the operator in that same precision, so D Z = V H holds to that
-// precision; each cycle ends with the FP64 true residual, so restarts act as
-// iterative refinement.
+// least-squares update and the true residual are FP64-class: IEEE FP64 for
+// an FP64 operator; for a mixed-precision one the Krylov basis and the true
+// residual's Dslash use double-float arithmetic (FP32 pairs, ~48-bit
+// significands, on GB300's FP32 pipes), the least-squares update, x and the
+// residual's inputs and outputs stay FP64. Preconditioned vectors z_j are
+// kept in FP32 (FP64 for an FP64 operator) and the Arnoldi product D z_j uses
+// the operator in that same precision, so D Z = V H holds to that precision;
+// each cycle ends with the true residual, so restarts act as iterative
+// refinement.
 //
 // Batching: right-hand sides that share an operator occupy the slots of one
 // BatchSolver. Per Arnoldi step all slots' Schwarz sweeps are one launch per
