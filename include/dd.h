@@ -19,7 +19,8 @@
  * smoother is red-black multiplicative Schwarz over lattice blocks, each block
  * solved by even-odd (odd-site Schur complement) minimal-residual steps; the
  * outer solver is FGMRES(m) right-preconditioned by it, with its Arnoldi
- * orthogonalisation, least-squares update and true residual in FP64.
+ * orthogonalisation, least-squares update and true residual in FP64-class
+ * arithmetic (IEEE FP64, or double-float FP32 pairs where dd_solve says so).
  *
  * Conventions.
  *   dims  = {T, Z, Y, X}; canonical site n = x + X*(y + Y*(z + Z*t)).
@@ -130,7 +131,9 @@ int dd_create_gauge(dd_lattice_t lat, const double *links_host, dd_gauge_t *out)
  * DD_F16, DD_BF16). Builds on the device (FP64): the clover term C(n) from the
  * four-leaf plaquette sum, A(n) = 4 + m0 + C(n) as two 6x6 Hermitian chirality
  * blocks per site, and the inverses of the even-site blocks; stores them in
- * FP64 (true residual), FP32 (outer-solver operator) and `prec` (smoother).
+ * FP64 (true residual), FP32 (outer-solver operator) and `prec` (smoother);
+ * with prec != DD_F64 also the FP64 links and blocks split into double-float
+ * pairs (the true residual of mixed-precision solves).
  * Returns DD_EINVAL if a 6x6 block is singular. Synchronous. */
 int dd_create_op(dd_gauge_t gauge, double c_sw, double m0, int prec, dd_op_t *out);
 
@@ -205,15 +208,18 @@ typedef struct {
   int status;             /* DD_OK, DD_ENOTCONV, ...                               */
   int iterations;         /* preconditioned Arnoldi steps                          */
   int cycles;             /* restart cycles                                        */
-  double true_rel_residual; /* ||b - D x|| / ||b|| in FP64 at exit                  */
+  double true_rel_residual; /* ||b - D x|| / ||b|| recomputed at exit (see dd_solve) */
   double est_rel_residual;  /* FGMRES estimate at exit                              */
   double ms_total, ms_sap, ms_dirac, ms_orth; /* wall time split (ms)               */
 } dd_solve_info;
 
 /* Solve D x = b for nrhs canonical FP64 right-hand sides ([nrhs][V][4][3][2],
  * host or device per p->where) with SAP-preconditioned FGMRES. The smoother
- * runs in the op's precision; FP64 is used for orthogonalisation, the
- * least-squares update and the true residual. x receives the solutions
+ * runs in the op's precision. With an FP64 op the orthogonalisation, the
+ * least-squares update and the true residual are IEEE FP64; with a
+ * mixed-precision op the Krylov basis and the true residual's Dslash use
+ * double-float arithmetic (FP32 pairs, ~48-bit significands), the
+ * least-squares update, x and the residual norms stay FP64. x receives the solutions
  * (and holds the initial guesses if p->use_x0). info (may be NULL) receives
  * nrhs records. Returns DD_OK when every right-hand side converged, else
  * DD_ENOTCONV (x holds the best iterates) or an error. Synchronous with
