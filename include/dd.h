@@ -74,7 +74,8 @@ enum { DD_F64 = 0, DD_F32 = 1, DD_F16 = 2, DD_BF16 = 3 };
  * fields, double-float arithmetic (pairs of FP32, ~48-bit significands) on
  * the operator's pre-split FP64 links and clover; the operator a
  * mixed-precision dd_solve uses for its true residual. Operators created with
- * a DD_F64 smoother do not hold these fields (DD_EINVAL). */
+ * a DD_F64 smoother do not hold these fields (DD_EINVAL). A diagnostic path:
+ * it allocates one temporary field and synchronises `stream` on return. */
 enum { DD_F64_DF = 4 };
 
 /* data location flags for dd_solve / requests */
