@@ -130,10 +130,12 @@ def library_path() -> str:
 
 
 def lib():
-    """Load (building first if needed) the CUDA library; raise if impossible."""
+    """Load (building first if needed) the CUDA library; raise if impossible.
+    DD_LIBRARY=<path> loads that build instead (e.g. the index-checking one
+    from build.py --checked)."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = os.environ.get("DD_LIBRARY") or _build.build()
         L = ctypes.CDLL(path)
         for name, (args, res) in EXPORTS.items():
             f = getattr(L, name)

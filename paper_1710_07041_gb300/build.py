@@ -34,16 +34,20 @@ def _stale(lib: str, srcs) -> bool:
     return any(os.path.getmtime(s) > t for s in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> str:
+def build(force: bool = False, verbose: bool = False, extra=None, checked: bool = False) -> str:
+    """Compile the library; checked=True builds the index-checking variant
+    (-DDD_CHECKED) into _build_checked/libdd.so instead."""
+    out = OUT + "_checked" if checked else OUT
+    lib = os.path.join(out, "libdd.so")
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    if not force and not _stale(LIB, srcs):
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+    if not force and not _stale(lib, srcs):
+        return lib
+    os.makedirs(out, exist_ok=True)
     nvcc = _nvcc()
-    flags = ARCH + NVCC_FLAGS + (extra or [])
+    flags = ARCH + NVCC_FLAGS + (["-DDD_CHECKED"] if checked else []) + (extra or [])
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src) + ".o")
+        obj = os.path.join(out, os.path.basename(src) + ".o")
         cmd = [nvcc, *flags, "-c", src, "-o", obj]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
@@ -54,15 +58,15 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None, checked="--checked" in sys.argv))

@@ -112,6 +112,7 @@ RhsPtrs contiguous(const void *in, void *out, int nrhs, size_t field_bytes) {
 }
 
 int launch_dirac(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st) {
+  NvtxRange range("dd:dirac");
   if (p.n < 1 || p.n > MAX_RHS) {
     set_error("apply_D: 1..%d right-hand sides per launch", MAX_RHS);
     return DD_EINVAL;

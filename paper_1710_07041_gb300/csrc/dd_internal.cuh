@@ -25,6 +25,8 @@
 
 #include "../../include/dd.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace dd {
 
 // ---------------------------------------------------------------- errors
@@ -177,6 +179,37 @@ __host__ __device__ inline int shape_of(const Geom &g) {
   return 0;
 }
 
+// Checked build (compiled with -DDD_CHECKED; the stand-in for a memory
+// checker, which is not available on the target machines): the main global
+// and shared-memory access paths check their indices; an index out of range
+// is counted and replaced by 0, so no access leaves its buffer, and
+// dd_device_status reports the count. Normal builds check nothing.
+#ifdef DD_CHECKED
+static __device__ unsigned dd_bounds_errors = 0;
+#define DD_CHECK_INDEX(i, n)                                              \
+  do {                                                                    \
+    if ((unsigned long long)(i) >= (unsigned long long)(n)) {             \
+      atomicAdd(&dd_bounds_errors, 1u);                                   \
+      (i) = 0;                                                            \
+    }                                                                     \
+  } while (0)
+int register_bounds_reader(unsigned (*read)());
+// this translation unit's counter, read and cleared (registered at load time)
+static unsigned dd_read_bounds_errors() {
+  unsigned n = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&n, dd_bounds_errors, sizeof n) != cudaSuccess) return 0;
+  if (n) cudaMemcpyToSymbol(dd_bounds_errors, &z, sizeof z);
+  return n;
+}
+[[maybe_unused]] static const int dd_bounds_registered = register_bounds_reader(&dd_read_bounds_errors);
+#else
+#define DD_CHECK_INDEX(i, n) \
+  do {                       \
+  } while (0)
+#endif
+// total count of all translation units' checked-build counters (0 unless -DDD_CHECKED)
+unsigned bounds_errors_all();
+
 // ------------------------------------------------------------- precisions
 template <typename S> struct Store;
 template <> struct Store<double> {
@@ -307,6 +340,8 @@ __device__ __forceinline__ double to_d(dfl v) { return (double)v.hi + (double)v.
 // Load spinor (b, s) from a field of storage S.
 template <typename S, typename C>
 __device__ __forceinline__ void load_spinor(const void *field, const Geom &g, int b, int s, Spinor<C> &out) {
+  DD_CHECK_INDEX(b, g.nblocks);
+  DD_CHECK_INDEX(s, g.Vb);
   constexpr int NC = spinor_chunks<S>();
   const char *base = (const char *)field + (((size_t)b * NC) * g.Vb + s) * 16;
   const size_t cstride = (size_t)g.Vb * 16;
@@ -340,6 +375,8 @@ __device__ __forceinline__ void load_spinor(const void *field, const Geom &g, in
 
 template <typename S, typename C>
 __device__ __forceinline__ void store_spinor(void *field, const Geom &g, int b, int s, const Spinor<C> &v) {
+  DD_CHECK_INDEX(b, g.nblocks);
+  DD_CHECK_INDEX(s, g.Vb);
   constexpr int NC = spinor_chunks<S>();
   char *base = (char *)field + (((size_t)b * NC) * g.Vb + s) * 16;
   const size_t cstride = (size_t)g.Vb * 16;
@@ -370,6 +407,9 @@ template <typename C> struct Link { cpx<C> m[9]; };
 template <typename S, typename C>
 __device__ __forceinline__ void load_link(const void *links, const Geom &g, int b, int s, int mu, Link<C> &u) {
   using P = typename Store<S>::pair_t;
+  DD_CHECK_INDEX(b, g.nblocks);
+  DD_CHECK_INDEX(s, g.Vb);
+  DD_CHECK_INDEX(mu, 4);
   const P *base = (const P *)links + ((size_t)b * 36 + 9 * mu) * g.Vb + s;
 #pragma unroll
   for (int i = 0; i < 9; i++) u.m[i] = from_pair<C, P>(__ldg(base + (size_t)i * g.Vb));
@@ -512,6 +552,8 @@ __device__ __forceinline__ void herm6_mv(const cpx<C> *m, const cpx<C> *x, cpx<C
 template <typename S, typename C>
 __device__ __forceinline__ void load_clover_block(const void *clov, size_t tile_sites, int b, int s, int h,
                                                   cpx<C> *m) {
+  DD_CHECK_INDEX(s, tile_sites);
+  DD_CHECK_INDEX(h, 2);
   using P = typename Store<S>::pair_t;
   const P *base = (const P *)clov + ((size_t)b * 36 + 18 * h) * tile_sites + s;
 #pragma unroll
@@ -567,6 +609,14 @@ struct Op {
 void release_op(Op *op);
 
 const OpFields *fields_for(const Op *op, int prec);
+
+// NVTX range for profilers (nsys/ncu --nvtx); costs nothing without a tool
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Per-right-hand-side field pointers, passed to kernels by value so that a
 // batch may mix vectors held anywhere in device memory.

@@ -290,7 +290,9 @@ __global__ void __launch_bounds__(256) k_coarse_apply(Geom g, const __half2 *__r
   const float sc = scale ? 1.f / *scale : 1.f;
   for (int q = threadIdx.x; q < ncol; q += blockDim.x) {
     const int d = q / n2, c = q - d * n2;
-    const float2 v = x[(size_t)coarse_nbr(g, a, d) * n2 + c];
+    int na = coarse_nbr(g, a, d);
+    DD_CHECK_INDEX(na, g.nblocks);
+    const float2 v = x[(size_t)na * n2 + c];
     xs[q] = make_float2(v.x * sc, v.y * sc);
   }
   __syncthreads();
@@ -799,6 +801,7 @@ static int mg_enqueue(const Mg *mg, MgWork &W, const float *r, float *x, cudaStr
 // capture. DD_MG_GRAPHS=0 disables the graphs; a stream under capture by the
 // caller, or the legacy stream, gets the launches directly.
 int mg_apply(const Mg *mg, MgWork &W, const float *r, float *x, cudaStream_t st, float scale) {
+  NvtxRange range("dd:mg_apply");
   const char *env = getenv("DD_MG_GRAPHS");
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cap);

@@ -37,6 +37,10 @@ __device__ unsigned g_wait_timeouts = 0;
 int device_wait_status() {
   int rc = cuda_fail(cudaDeviceSynchronize(), "device status");
   if (rc) return rc;
+  if (const unsigned nb = bounds_errors_all()) {   // checked builds only
+    set_error("%u out-of-range indices caught by the checked build", nb);
+    return DD_ECUDA;
+  }
   unsigned n = 0, zero = 0;
   if ((rc = cuda_fail(cudaMemcpyFromSymbol(&n, g_wait_timeouts, sizeof(n)), "device status"))) return rc;
   if (n) {
@@ -194,6 +198,7 @@ int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const v
 }
 
 int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
+  NvtxRange range("dd:sap");
   if (rp.n < 1 || rp.n > MAX_RHS) {
     set_error("sap: 1..%d right-hand sides per launch", MAX_RHS);
     return DD_EINVAL;

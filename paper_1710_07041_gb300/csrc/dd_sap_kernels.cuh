@@ -83,11 +83,14 @@ template <typename P> struct Tile {
 
 template <typename C, typename P>
 __device__ __forceinline__ void tile_link(const Tile<P> &t, int s, int mu, Link<C> &u) {
+  DD_CHECK_INDEX(s, t.stride);
 #pragma unroll
   for (int i = 0; i < 9; i++) u.m[i] = from_pair<C, P>(t.p[(9 * mu + i) * t.stride + s]);
 }
 template <typename C, typename P>
 __device__ __forceinline__ void tile_block(const Tile<P> &t, int s, int h, cpx<C> *m) {
+  DD_CHECK_INDEX(s, t.stride);
+  DD_CHECK_INDEX(h, 2);
 #pragma unroll
   for (int i = 0; i < 18; i++) m[i] = from_pair<C, P>(t.p[(18 * h + i) * t.stride + s]);
 }
@@ -95,6 +98,7 @@ __device__ __forceinline__ void tile_block(const Tile<P> &t, int s, int h, cpx<C
 // shared-memory vector: [12][Vh] complex, one parity of the block
 template <typename C>
 __device__ __forceinline__ void vec_load(const cpx<C> *v, int Vh, int q, Spinor<C> &o) {
+  DD_CHECK_INDEX(q, Vh);
 #pragma unroll
   for (int i = 0; i < 12; i++) o.c[i] = v[i * Vh + q];
 }

@@ -189,6 +189,7 @@ int BatchSolver::retire(Slot &s, int status) {
 
 // True residual r = b - D x (FP64) for the slots in R; retire or begin a cycle.
 int BatchSolver::restart_phase(std::vector<Slot *> &R) {
+  NvtxRange range("dd:true_residual");
   const Geom &g = op_->lat->g;
   const size_t n = (size_t)g.V * 12;
   int rc;
@@ -297,6 +298,7 @@ int BatchSolver::maxpy(Slot *s, int kk, const double *h, double *wn2) {
 
 // One preconditioned Arnoldi step for every slot in A.
 int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
+  NvtxRange range("dd:arnoldi_step");
   const Geom &g = op_->lat->g;
   const size_t n = (size_t)g.V * 12;
   const int m = p_.restart;
