@@ -202,11 +202,29 @@ __device__ __forceinline__ void block_reduce_df(df *v, double *smem, double *out
   }
 }
 
+// Element e of a DF vector (complex number c of site s in block b, at
+// e = (b * 12 + c) * Vb + s) read from an FP32 spinor field instead, as the
+// double-float {value, 0}: the Arnoldi vector w = D z straight from the FP32
+// Dslash, without a conversion pass (lvb = log2 Vb).
+__device__ __forceinline__ float4 w_from_f32(const float *w32, size_t e, int lvb) {
+  const size_t s = e & (((size_t)1 << lvb) - 1), q = e >> lvb;
+  const size_t c = q % 12, b = q / 12;
+  const float2 v = *(const float2 *)(w32 + ((((b * 6 + (c >> 1)) << lvb) + s) << 2) + ((c & 1) << 1));
+  return make_float4(v.x, v.y, 0.f, 0.f);
+}
+template <bool W32>
+__device__ __forceinline__ float4 w_at(const float4 *w, const float *w32, size_t e, int lvb) {
+  if constexpr (W32) return w_from_f32(w32, e, lvb);
+  return w[e];
+}
+
 // partial[blk] = this block's sums of conj(V_i) w (i < k) and |w|^2, as doubles.
-// Two elements per thread and iteration keep more loads in flight.
-template <int KMAX>
+// Two elements per thread and iteration keep more loads in flight. W32: w is
+// read from the FP32 field w32 (see w_from_f32).
+template <int KMAX, bool W32 = false>
 __global__ void __launch_bounds__(RED_TPB) k_df_mdot(const float4 *__restrict__ V, size_t ldv, int k,
-                                                     const float4 *__restrict__ w, size_t n, double *partial) {
+                                                     const float4 *__restrict__ w, size_t n, double *partial,
+                                                     const float *__restrict__ w32 = nullptr, int lvb = 0) {
   __shared__ double smem[(2 * KMAX + 1) * 32];
   df acc[2 * KMAX + 1];
 #pragma unroll
@@ -215,7 +233,7 @@ __global__ void __launch_bounds__(RED_TPB) k_df_mdot(const float4 *__restrict__ 
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += 2 * stride) {
     const size_t e2 = e + stride;
     const bool two = e2 < n;
-    float4 we = w[e], we2 = two ? w[e2] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 we = w_at<W32>(w, w32, e, lvb), we2 = two ? w_at<W32>(w, w32, e2, lvb) : make_float4(0.f, 0.f, 0.f, 0.f);
     float4 v[KMAX], v2[KMAX];
 #pragma unroll
     for (int i = 0; i < KMAX; i++)
@@ -245,11 +263,14 @@ __global__ void __launch_bounds__(RED_TPB) k_df_mdot(const float4 *__restrict__ 
   block_reduce_df<2 * KMAX + 1>(acc, smem, partial + (size_t)blockIdx.x * (2 * KMAX + 1));
 }
 
-// w -= sum_i h_i V_i (h complex doubles on the device); partial[blk] = |w|^2
-template <int KMAX>
+// w -= sum_i h_i V_i (h complex doubles on the device); partial[blk] = |w|^2.
+// W32: the input w is read from the FP32 field w32 (see w_from_f32) and the
+// result written to w.
+template <int KMAX, bool W32 = false>
 __global__ void __launch_bounds__(RED_TPB) k_df_maxpy_norm(const float4 *__restrict__ V, size_t ldv, int k,
                                                            const double2 *__restrict__ h, float4 *w, size_t n,
-                                                           double *partial) {
+                                                           double *partial, const float *__restrict__ w32 = nullptr,
+                                                           int lvb = 0) {
   __shared__ double smem[32];
   __shared__ float4 hs[KMAX];   // (re_hi, im_hi, re_lo, im_lo)
   if (threadIdx.x < KMAX) {
@@ -263,7 +284,7 @@ __global__ void __launch_bounds__(RED_TPB) k_df_maxpy_norm(const float4 *__restr
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += 2 * stride) {
     const size_t e2 = e + stride;
     const bool two = e2 < n;
-    float4 we = w[e], we2 = two ? w[e2] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 we = w_at<W32>(w, w32, e, lvb), we2 = two ? w_at<W32>(w, w32, e2, lvb) : make_float4(0.f, 0.f, 0.f, 0.f);
     float4 v[KMAX], v2[KMAX];
 #pragma unroll
     for (int i = 0; i < KMAX; i++)
@@ -472,12 +493,17 @@ int Blas::xmy(const double *x, double *y, size_t n, cudaStream_t st) {
 }
 
 int Blas::df_mdot(const float *V, size_t ldv, int k, const float *w, size_t n, double *h_dev, double *wnorm2_dev,
-                  cudaStream_t st) {
+                  cudaStream_t st, const float *w32, int lvb) {
   for (int i0 = 0; i0 < k || (k == 0 && i0 == 0); i0 += 8) {
     int kk = k - i0 < 8 ? k - i0 : 8;
     if (kk < 0) kk = 0;
     const float4 *Vi = (const float4 *)V + (size_t)i0 * ldv;
-    if (kk <= 4)
+    if (w32) {
+      if (kk <= 4)
+        k_df_mdot<4, true><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, nullptr, n, partial, w32, lvb);
+      else
+        k_df_mdot<8, true><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, nullptr, n, partial, w32, lvb);
+    } else if (kk <= 4)
       k_df_mdot<4><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, (const float4 *)w, n, partial);
     else
       k_df_mdot<8><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, (const float4 *)w, n, partial);
@@ -494,13 +520,20 @@ int Blas::df_mdot(const float *V, size_t ldv, int k, const float *w, size_t n, d
 }
 
 int Blas::df_maxpy_norm(const float *V, size_t ldv, int k, const double *h_dev, float *w, size_t n, double *norm2_dev,
-                        cudaStream_t st) {
-  if (k == 0) return df_mdot(V, ldv, 0, w, n, nullptr, norm2_dev, st);
+                        cudaStream_t st, const float *w32, int lvb) {
+  if (k == 0) return df_mdot(V, ldv, 0, w, n, nullptr, norm2_dev, st, w32, lvb);
   for (int i0 = 0; i0 < k; i0 += 8) {
     int kk = k - i0 < 8 ? k - i0 : 8;
     const float4 *Vi = (const float4 *)V + (size_t)i0 * ldv;
     const double2 *hi = (const double2 *)h_dev + i0;
-    if (kk <= 4)
+    // the first chunk reads the FP32 input (when given) and writes w; later chunks update w
+    const bool from32 = w32 && i0 == 0;
+    if (from32) {
+      if (kk <= 4)
+        k_df_maxpy_norm<4, true><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial, w32, lvb);
+      else
+        k_df_maxpy_norm<8, true><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial, w32, lvb);
+    } else if (kk <= 4)
       k_df_maxpy_norm<4><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial);
     else
       k_df_maxpy_norm<8><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial);

@@ -23,10 +23,13 @@ struct Blas {
   int xmy(const double *x, double *y, size_t n, cudaStream_t st);  // y = x - y
   // Double-float (DF) variants: vectors of n complex entries stored as float4
   // (re_hi, im_hi, re_lo, im_lo); V_i = V + i * ldv complex entries.
+  // w32 != nullptr: w is the FP32 spinor field w32 (block-major, lvb = log2 of
+  // the block volume), read as double-float {value, 0}; df_maxpy_norm then
+  // writes the updated vector to w.
   int df_mdot(const float *V, size_t ldv, int k, const float *w, size_t n, double *h_dev, double *wnorm2_dev,
-              cudaStream_t st);
+              cudaStream_t st, const float *w32 = nullptr, int lvb = 0);
   int df_maxpy_norm(const float *V, size_t ldv, int k, const double *h_dev, float *w, size_t n, double *norm2_dev,
-                    cudaStream_t st);
+                    cudaStream_t st, const float *w32 = nullptr, int lvb = 0);
   int df_scale(float *y, const float *x, double a, size_t n, cudaStream_t st);
   int f64_to_df(float *y, const double *x, double a, size_t n, cudaStream_t st);  // y = a x
   // site-wise: DF field -> storage `prec` (scaled), and FP32 field -> DF field

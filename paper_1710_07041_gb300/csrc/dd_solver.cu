@@ -284,15 +284,25 @@ int BatchSolver::end_cycle(Slot &s) {
   return rc;
 }
 
-int BatchSolver::mdot(Slot *s, int kk, double *h, double *wn2) {
-  const size_t n = (size_t)op_->lat->g.V * 12;
-  if (df_) return blas_.df_mdot((const float *)s->Vb, n, kk, (const float *)s->w, n, h, wn2, st_);
+// from32: w is still the FP32 Dslash output in s->zt (the first Gram-Schmidt
+// pass of a double-float solve reads it there; maxpy writes the DF result to s->w)
+int BatchSolver::mdot(Slot *s, int kk, double *h, double *wn2, bool from32) {
+  const Geom &g = op_->lat->g;
+  const size_t n = (size_t)g.V * 12;
+  const int lvb = g.lbd[0] + g.lbd[1] + g.lbd[2] + g.lbd[3];
+  if (df_)
+    return blas_.df_mdot((const float *)s->Vb, n, kk, (const float *)s->w, n, h, wn2, st_,
+                         from32 ? (const float *)s->zt : nullptr, lvb);
   return blas_.mdot(s->Vb, n, kk, s->w, n, h, wn2, st_);
 }
 
-int BatchSolver::maxpy(Slot *s, int kk, const double *h, double *wn2) {
-  const size_t n = (size_t)op_->lat->g.V * 12;
-  if (df_) return blas_.df_maxpy_norm((const float *)s->Vb, n, kk, h, (float *)s->w, n, wn2, st_);
+int BatchSolver::maxpy(Slot *s, int kk, const double *h, double *wn2, bool from32) {
+  const Geom &g = op_->lat->g;
+  const size_t n = (size_t)g.V * 12;
+  const int lvb = g.lbd[0] + g.lbd[1] + g.lbd[2] + g.lbd[3];
+  if (df_)
+    return blas_.df_maxpy_norm((const float *)s->Vb, n, kk, h, (float *)s->w, n, wn2, st_,
+                               from32 ? (const float *)s->zt : nullptr, lvb);
   return blas_.maxpy_norm(s->Vb, n, kk, h, s->w, n, wn2, st_);
 }
 
@@ -339,18 +349,16 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
     }
   }
   cudaEventRecord(ev_[1], st_);
-  // w = D z_j in zprec
+  // w = D z_j in zprec (a double-float solve keeps it in the FP32 field zt;
+  // the first Gram-Schmidt pass reads it there and writes the DF w)
   if ((rc = launch_dirac(g, zprec_ == DD_F64 ? op_->f64 : op_->f32, d_ptrs, st_))) return rc;
-  if (zprec_ != DD_F64)
-    for (Slot *s : A)
-      if ((rc = blas_.field_to_df(g, DD_F32, s->zt, (float *)s->w, st_))) return rc;
   cudaEventRecord(ev_[2], st_);
   // classical Gram-Schmidt, repeated once for slots whose norm drops by more than 1/sqrt(2)
   for (Slot *s : A) {
     double *hd = hdev_ + HSTRIDE * (s - slots_.data());
     const int kk = s->j + 1;
-    if ((rc = mdot(s, kk, hd, hd + W0))) return rc;
-    if ((rc = maxpy(s, kk, hd, hd + W1))) return rc;
+    if ((rc = mdot(s, kk, hd, hd + W0, df_))) return rc;
+    if ((rc = maxpy(s, kk, hd, hd + W1, df_))) return rc;
   }
   if ((rc = sync_h())) return rc;
   std::vector<std::vector<cd>> hcol(A.size());

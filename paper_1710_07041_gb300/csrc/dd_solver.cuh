@@ -66,8 +66,8 @@ class BatchSolver {
   int end_cycle(Slot &s);
   int retire(Slot &s, int status);
   int sync_h();
-  int mdot(Slot *s, int kk, double *h, double *wn2);
-  int maxpy(Slot *s, int kk, const double *h, double *wn2);
+  int mdot(Slot *s, int kk, double *h, double *wn2, bool from32 = false);
+  int maxpy(Slot *s, int kk, const double *h, double *wn2, bool from32 = false);
 
   const Op *op_;
   dd_solve_params p_;
