@@ -353,7 +353,7 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
   // the first Gram-Schmidt pass reads it there and writes the DF w)
   if ((rc = launch_dirac(g, zprec_ == DD_F64 ? op_->f64 : op_->f32, d_ptrs, st_))) return rc;
   cudaEventRecord(ev_[2], st_);
-  // classical Gram-Schmidt, repeated once for slots whose norm drops by more than 1/sqrt(2)
+  // classical Gram-Schmidt, repeated once for slots whose norm drops below 1e-3 of its value (REORTH2)
   for (Slot *s : A) {
     double *hd = hdev_ + HSTRIDE * (s - slots_.data());
     const int kk = s->j + 1;
