@@ -551,7 +551,9 @@ def run_serve(args):
     mixed-precision (FP16) solves to 1e-10 through the continuous-batching
     server. Reports p50/p99 latency and solves/s next to the plain FP64 GPU
     solve of the same request mix (estimated from one timed FP64 solve per
-    lattice size)."""
+    lattice size). --rate sets the offered request rate: 200/s overloads the
+    GPU ~100x (latency is then queueing); a rate below capacity measures the
+    service latency of requests that find the server idle or lightly loaded."""
     import torch
 
     import paper_1710_07041_gb300 as dd
@@ -571,7 +573,7 @@ def run_serve(args):
         return ops[k]
 
     nreq = args.requests
-    rate = 200.0
+    rate = float(args.rate)
     u = synth.uniform(4 * nreq, 51)
     arrivals = np.cumsum(-np.log(u[:nreq]) / rate)
     reqs = []
@@ -644,6 +646,7 @@ def main():
                          "48^3x96 workload; serve: the Poisson request stream; mg: two-level "
                          "preconditioner against SAP alone (no contract line)")
     ap.add_argument("--requests", type=int, default=40, help="requests in --mode serve")
+    ap.add_argument("--rate", type=float, default=200.0, help="offered requests/s in --mode serve")
     ap.add_argument("--solve-iters", type=int, default=20, help="iteration cap of the solve in --mode kernels")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
