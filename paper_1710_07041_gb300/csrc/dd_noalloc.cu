@@ -210,8 +210,13 @@ extern "C" int dd_solve_noalloc(dd_op_t opp, const dd_solve_params *p, const dou
       if (rc) return rc;
       dd_sap_params sp = p->sap;
       sp.x_is_zero = 1;
-      if ((rc = launch_sap(g, op->fp, sp, tin, tout, 1, st))) return rc;
-      if ((rc = launch_convert_field(g, op->prec, tout, zprec, zj, 1, 1.0 / sigma, st))) return rc;
+      // z_j = SAP(sigma v_j), kept scaled by sigma as in dd_solve (H and y carry the factor)
+      if (op->prec == zprec) {
+        if ((rc = launch_sap(g, op->fp, sp, tin, zj, 1, st))) return rc;
+      } else {
+        if ((rc = launch_sap(g, op->fp, sp, tin, tout, 1, st))) return rc;
+        if ((rc = launch_convert_field(g, op->prec, tout, zprec, zj, 1, 1.0, st))) return rc;
+      }
       if ((rc = launch_dirac(g, fz_ops, zj, zprec == DD_F64 ? (void *)w : zt, 1, st))) return rc;
       if (zprec != DD_F64 && (rc = bl.field_to_df(g, DD_F32, zt, (float *)w, st))) return rc;
       const int kk = j + 1;

@@ -313,7 +313,9 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
   const size_t n = (size_t)g.V * 12;
   const int m = p_.restart;
   int rc;
-  // z_j = SAP(v_j): pack with scale sigma, smooth, keep z_j / sigma in zprec
+  // z_j = SAP(sigma v_j) in zprec. z_j is kept scaled by sigma (the smoother
+  // input's scale): then w = D z_j, the Hessenberg column and y carry the same
+  // factor and x += Z y is unchanged, with no rescaling pass.
   cudaEventRecord(ev_[0], st_);
   RhsPtrs sp_ptrs, d_ptrs;
   sp_ptrs.n = d_ptrs.n = (int)A.size();
@@ -323,19 +325,23 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
       Slot *s = A[i];
       char *zj = s->Z + (size_t)s->j * fz_;
       if ((rc = blas_.df_to_field(g, (const float *)(s->Vb + 2 * n * s->j), DD_F32, s->zt, sigma_, st_))) return rc;
-      if ((rc = mg_apply((const Mg *)p_.mg, *s->mgw, (const float *)s->zt, (float *)zj, st_, (float)(1.0 / sigma_))))
-        return rc;
+      if ((rc = mg_apply((const Mg *)p_.mg, *s->mgw, (const float *)s->zt, (float *)zj, st_, 1.f))) return rc;
       d_ptrs.in[i] = zj;
       d_ptrs.out[i] = s->zt;
     }
   } else {
+    const bool direct = op_->prec == zprec_ && A.size() == 1;
     for (int i = 0; i < (int)A.size(); i++) {
       Slot *s = A[i];
       if (df_) rc = blas_.df_to_field(g, (const float *)(s->Vb + 2 * n * s->j), op_->prec, s->tin, sigma_, st_);
       else rc = launch_convert_field(g, DD_F64, s->Vb + 2 * n * s->j, op_->prec, s->tin, 1, sigma_, st_);
       if (rc) return rc;
+      // a single slot's smoother writes z_j straight into Z when it works in
+      // Z's precision (with several slots the fixed output buffers keep the
+      // smoother's graph cache to one entry per slot set; the copy below is
+      // exact, so results are the same either way)
       sp_ptrs.in[i] = s->tin;
-      sp_ptrs.out[i] = s->tout;
+      sp_ptrs.out[i] = direct ? (void *)(s->Z + (size_t)s->j * fz_) : s->tout;
     }
     dd_sap_params sp = p_.sap;
     sp.x_is_zero = 1;
@@ -343,7 +349,7 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
     for (int i = 0; i < (int)A.size(); i++) {
       Slot *s = A[i];
       char *zj = s->Z + (size_t)s->j * fz_;
-      if ((rc = launch_convert_field(g, op_->prec, s->tout, zprec_, zj, 1, 1.0 / sigma_, st_))) return rc;
+      if (!direct && (rc = launch_convert_field(g, op_->prec, s->tout, zprec_, zj, 1, 1.0, st_))) return rc;
       d_ptrs.in[i] = zj;
       d_ptrs.out[i] = zprec_ == DD_F64 ? (void *)s->w : s->zt;
     }
