@@ -270,11 +270,15 @@ template <int KMAX, bool W32 = false>
 __global__ void __launch_bounds__(RED_TPB) k_df_maxpy_norm(const float4 *__restrict__ V, size_t ldv, int k,
                                                            const double2 *__restrict__ h, float4 *w, size_t n,
                                                            double *partial, const float *__restrict__ w32 = nullptr,
-                                                           int lvb = 0) {
+                                                           int lvb = 0, const double *__restrict__ scl = nullptr) {
   __shared__ double smem[32];
   __shared__ float4 hs[KMAX];   // (re_hi, im_hi, re_lo, im_lo)
   if (threadIdx.x < KMAX) {
     double2 c = threadIdx.x < k ? h[threadIdx.x] : make_double2(0, 0);
+    if (scl && threadIdx.x < k) {   // per-vector coefficient factor (see Blas::df_maxpy_norm)
+      c.x *= scl[threadIdx.x];
+      c.y *= scl[threadIdx.x];
+    }
     float rh = (float)c.x, ih = (float)c.y;
     hs[threadIdx.x] = make_float4(rh, ih, (float)(c.x - rh), (float)(c.y - ih));
   }
@@ -520,27 +524,34 @@ int Blas::df_mdot(const float *V, size_t ldv, int k, const float *w, size_t n, d
 }
 
 int Blas::df_maxpy_norm(const float *V, size_t ldv, int k, const double *h_dev, float *w, size_t n, double *norm2_dev,
-                        cudaStream_t st, const float *w32, int lvb) {
+                        cudaStream_t st, const float *w32, int lvb, const double *scl) {
   if (k == 0) return df_mdot(V, ldv, 0, w, n, nullptr, norm2_dev, st, w32, lvb);
   for (int i0 = 0; i0 < k; i0 += 8) {
     int kk = k - i0 < 8 ? k - i0 : 8;
     const float4 *Vi = (const float4 *)V + (size_t)i0 * ldv;
     const double2 *hi = (const double2 *)h_dev + i0;
+    const double *si = scl ? scl + i0 : nullptr;
     // the first chunk reads the FP32 input (when given) and writes w; later chunks update w
     const bool from32 = w32 && i0 == 0;
     if (from32) {
       if (kk <= 4)
-        k_df_maxpy_norm<4, true><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial, w32, lvb);
+        k_df_maxpy_norm<4, true><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial, w32, lvb, si);
       else
-        k_df_maxpy_norm<8, true><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial, w32, lvb);
+        k_df_maxpy_norm<8, true><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial, w32, lvb, si);
     } else if (kk <= 4)
-      k_df_maxpy_norm<4><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial);
+      k_df_maxpy_norm<4><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial, nullptr, 0, si);
     else
-      k_df_maxpy_norm<8><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial);
+      k_df_maxpy_norm<8><<<nblk, RED_TPB, 0, st>>>(Vi, ldv, kk, hi, (float4 *)w, n, partial, nullptr, 0, si);
     DD_LAUNCHED();
   }
   k_sum_partials<<<1, 256, 0, st>>>(partial, nblk, 1, 1, norm2_dev);
   return launched("k_sum_partials");
+}
+
+__global__ void k_set_double(double *p, double v) { *p = v; }
+int Blas::set_double(double *dev, double v, cudaStream_t st) {
+  k_set_double<<<1, 1, 0, st>>>(dev, v);
+  return launched("k_set_double");
 }
 
 int Blas::df_scale(float *y, const float *x, double a, size_t n, cudaStream_t st) {

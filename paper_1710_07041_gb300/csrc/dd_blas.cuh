@@ -28,8 +28,12 @@ struct Blas {
   // writes the updated vector to w.
   int df_mdot(const float *V, size_t ldv, int k, const float *w, size_t n, double *h_dev, double *wnorm2_dev,
               cudaStream_t st, const float *w32 = nullptr, int lvb = 0);
+  // scl (device, optional): the coefficients h_i are multiplied by scl[i]
+  // before the update (for a basis stored as v_i = s_i V_i with h_i = <V_i, w>
+  // the caller passes s_i^2)
   int df_maxpy_norm(const float *V, size_t ldv, int k, const double *h_dev, float *w, size_t n, double *norm2_dev,
-                    cudaStream_t st, const float *w32 = nullptr, int lvb = 0);
+                    cudaStream_t st, const float *w32 = nullptr, int lvb = 0, const double *scl = nullptr);
+  int set_double(double *dev, double v, cudaStream_t st);   // *dev = v, stream-ordered
   int df_scale(float *y, const float *x, double a, size_t n, cudaStream_t st);
   int f64_to_df(float *y, const double *x, double a, size_t n, cudaStream_t st);  // y = a x
   // site-wise: DF field -> storage `prec` (scaled), and FP32 field -> DF field

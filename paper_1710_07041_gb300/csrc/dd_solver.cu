@@ -71,7 +71,7 @@ BatchSolver::BatchSolver(const Op *op, const dd_solve_params &p, int slots, cuda
 
 BatchSolver::~BatchSolver() {
   for (auto &s : slots_) {
-    void *ptrs[] = {s.Vb, s.Z, s.x, s.b, s.w, s.canon, s.tin, s.tout, s.zt};
+    void *ptrs[] = {s.Vb, s.Z, s.x, s.b, s.w, s.canon, s.tin, s.tout, s.zt, s.sdev};
     for (void *q : ptrs)
       if (q) cudaFree(q);
     delete s.mgw;
@@ -97,7 +97,8 @@ int BatchSolver::init() {
               cudaMalloc((void **)&s.x, f64_) == cudaSuccess && cudaMalloc((void **)&s.b, f64_) == cudaSuccess &&
               cudaMalloc((void **)&s.w, f64_) == cudaSuccess && cudaMalloc((void **)&s.canon, f64_) == cudaSuccess &&
               cudaMalloc(&s.tin, fp_) == cudaSuccess && cudaMalloc(&s.tout, fp_) == cudaSuccess &&
-              cudaMalloc(&s.zt, fz_) == cudaSuccess;
+              cudaMalloc(&s.zt, fz_) == cudaSuccess && cudaMalloc((void **)&s.sdev, sizeof(double) * (m + 1)) == cudaSuccess;
+    s.scl.assign(m + 1, 1.0);
     if (!ok) {
       cudaGetLastError();
       set_error("solver: out of device memory for %d FGMRES(%d) slots (%zu bytes each)", n, m,
@@ -256,8 +257,13 @@ int BatchSolver::restart_phase(std::vector<Slot *> &R) {
     std::fill(s->g.begin(), s->g.end(), cd(0));
     s->g[0] = s->beta;
     s->target = std::max(p_.tol * s->bnorm, p_.inner_reduction * s->beta);
-    if (df_) rc = blas_.f64_to_df((float *)s->Vb, s->w, 1.0 / s->beta, n, st_);
-    else rc = blas_.scale(s->Vb, s->w, 1.0 / s->beta, n, st_);
+    if (df_) {
+      rc = blas_.f64_to_df((float *)s->Vb, s->w, 1.0 / s->beta, n, st_);
+      s->scl[0] = 1.0;
+      if (rc == DD_OK) rc = blas_.set_double(s->sdev, 1.0, st_);
+    } else {
+      rc = blas_.scale(s->Vb, s->w, 1.0 / s->beta, n, st_);
+    }
     if (rc) return rc;
   }
   return DD_OK;
@@ -284,14 +290,18 @@ int BatchSolver::end_cycle(Slot &s) {
   return rc;
 }
 
-// from32: w is still the FP32 Dslash output in s->zt (the first Gram-Schmidt
-// pass of a double-float solve reads it there; maxpy writes the DF result to s->w)
+// Double-float solves: the first Gram-Schmidt pass reads w = D z_j from the
+// FP32 field s->zt (from32) and maxpy writes the result straight into the
+// basis slot j+1 (kk = j+1); the re-orthogonalisation pass works on that
+// slot. The dots h_i = <Vb_i, w> are taken against the stored
+// (unnormalised) vectors; the Hessenberg entry is scl[i] h_i and the update
+// w -= <v_i, w> v_i applies scl[i]^2 h_i to Vb_i (sdev). FP64 solves use s->w.
 int BatchSolver::mdot(Slot *s, int kk, double *h, double *wn2, bool from32) {
   const Geom &g = op_->lat->g;
   const size_t n = (size_t)g.V * 12;
   const int lvb = g.lbd[0] + g.lbd[1] + g.lbd[2] + g.lbd[3];
   if (df_)
-    return blas_.df_mdot((const float *)s->Vb, n, kk, (const float *)s->w, n, h, wn2, st_,
+    return blas_.df_mdot((const float *)s->Vb, n, kk, (const float *)(s->Vb + 2 * n * kk), n, h, wn2, st_,
                          from32 ? (const float *)s->zt : nullptr, lvb);
   return blas_.mdot(s->Vb, n, kk, s->w, n, h, wn2, st_);
 }
@@ -301,8 +311,8 @@ int BatchSolver::maxpy(Slot *s, int kk, const double *h, double *wn2, bool from3
   const size_t n = (size_t)g.V * 12;
   const int lvb = g.lbd[0] + g.lbd[1] + g.lbd[2] + g.lbd[3];
   if (df_)
-    return blas_.df_maxpy_norm((const float *)s->Vb, n, kk, h, (float *)s->w, n, wn2, st_,
-                               from32 ? (const float *)s->zt : nullptr, lvb);
+    return blas_.df_maxpy_norm((const float *)s->Vb, n, kk, h, (float *)(s->Vb + 2 * n * kk), n, wn2, st_,
+                               from32 ? (const float *)s->zt : nullptr, lvb, s->sdev);
   return blas_.maxpy_norm(s->Vb, n, kk, h, s->w, n, wn2, st_);
 }
 
@@ -324,7 +334,9 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
     for (int i = 0; i < (int)A.size(); i++) {
       Slot *s = A[i];
       char *zj = s->Z + (size_t)s->j * fz_;
-      if ((rc = blas_.df_to_field(g, (const float *)(s->Vb + 2 * n * s->j), DD_F32, s->zt, sigma_, st_))) return rc;
+      if ((rc = blas_.df_to_field(g, (const float *)(s->Vb + 2 * n * s->j), DD_F32, s->zt, sigma_ * s->scl[s->j],
+                                  st_)))
+        return rc;
       if ((rc = mg_apply((const Mg *)p_.mg, *s->mgw, (const float *)s->zt, (float *)zj, st_, 1.f))) return rc;
       d_ptrs.in[i] = zj;
       d_ptrs.out[i] = s->zt;
@@ -333,7 +345,8 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
     const bool direct = op_->prec == zprec_ && A.size() == 1;
     for (int i = 0; i < (int)A.size(); i++) {
       Slot *s = A[i];
-      if (df_) rc = blas_.df_to_field(g, (const float *)(s->Vb + 2 * n * s->j), op_->prec, s->tin, sigma_, st_);
+      if (df_)
+        rc = blas_.df_to_field(g, (const float *)(s->Vb + 2 * n * s->j), op_->prec, s->tin, sigma_ * s->scl[s->j], st_);
       else rc = launch_convert_field(g, DD_F64, s->Vb + 2 * n * s->j, op_->prec, s->tin, 1, sigma_, st_);
       if (rc) return rc;
       // a single slot's smoother writes z_j straight into Z when it works in
@@ -373,7 +386,7 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
     Slot *s = A[i];
     const double *hp = hpin_ + HSTRIDE * (s - slots_.data());
     hcol[i].resize(s->j + 1);
-    for (int q = 0; q <= s->j; q++) hcol[i][q] = cd(hp[2 * q], hp[2 * q + 1]);
+    for (int q = 0; q <= s->j; q++) hcol[i][q] = cd(hp[2 * q], hp[2 * q + 1]) * (df_ ? s->scl[q] : 1.0);
     if (hp[W1] < REORTH2 * hp[W0]) again.push_back(s);
   }
   if (!again.empty()) {
@@ -390,7 +403,7 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
       for (Slot *t : again) re |= t == s;
       if (!re) continue;
       const double *hp = hpin_ + HSTRIDE * (s - slots_.data());
-      for (int q = 0; q <= s->j; q++) hcol[i][q] += cd(hp[2 * q], hp[2 * q + 1]);
+      for (int q = 0; q <= s->j; q++) hcol[i][q] += cd(hp[2 * q], hp[2 * q + 1]) * (df_ ? s->scl[q] : 1.0);
     }
   }
   cudaEventRecord(ev_[3], st_);
@@ -407,8 +420,12 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
     const double hn = std::sqrt(std::max(hp[W1], 0.0));
     for (int q = 0; q <= j; q++) s.H[(size_t)q * m + j] = hcol[i][q];
     if (hn > 0) {
-      if (df_) rc = blas_.df_scale((float *)(s.Vb + 2 * n * (j + 1)), (const float *)s.w, 1.0 / hn, n, st_);
-      else rc = blas_.scale(s.Vb + 2 * n * (j + 1), s.w, 1.0 / hn, n, st_);
+      if (df_) {   // v_{j+1} = Vb_{j+1} / hn, kept as a scale
+        s.scl[j + 1] = 1.0 / hn;
+        rc = blas_.set_double(s.sdev + j + 1, 1.0 / (hn * hn), st_);
+      } else {
+        rc = blas_.scale(s.Vb + 2 * n * (j + 1), s.w, 1.0 / hn, n, st_);
+      }
       if (rc) return rc;
     }
     for (int q = 0; q < j; q++) {

@@ -34,6 +34,10 @@ struct Slot {
   std::chrono::steady_clock::time_point t0;
   // device memory
   double *Vb = nullptr;  // (m+1) basis fields: FP64, or double-float (float4 per complex)
+  // double-float basis: vector i is stored unnormalised, v_i = scl[i] * Vb_i
+  // (the Gram-Schmidt update writes it in place; no normalisation pass)
+  std::vector<double> scl;
+  double *sdev = nullptr;   // device scl[i]^2: the update coefficient of Vb_i is scl[i]^2 <Vb_i, w>
   char *Z = nullptr;     // m preconditioned fields (zprec)
   double *x = nullptr, *b = nullptr, *w = nullptr, *canon = nullptr;
   void *tin = nullptr, *tout = nullptr, *zt = nullptr;
