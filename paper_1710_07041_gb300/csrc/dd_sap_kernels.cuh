@@ -224,7 +224,9 @@ __device__ __forceinline__ void exchange(cpx<C> *xch, int Vh, int j, int h, cons
   }
 }
 
-// deterministic block sum of three values; red: smem [3][32]
+// deterministic block sum of three values; red: smem [3][32]. The reads of
+// red are not followed by a barrier here: the caller reaches one (the end of
+// its half-step) before any thread can write red again.
 template <typename C>
 __device__ __forceinline__ void block_sum3(C &a, C &b, C &c, C *red) {
   const int width = blockDim.x < 32 ? blockDim.x : 32;
@@ -247,7 +249,6 @@ __device__ __forceinline__ void block_sum3(C &a, C &b, C &c, C *red) {
     b += red[32 + i];
     c += red[64 + i];
   }
-  __syncthreads();
 }
 
 template <typename S> struct SapSmem {
@@ -416,9 +417,9 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
       }
     }
 
-    // ---- 3.-5. Schur right-hand side, MR steps, reconstruction: one loop of
-    // half-steps, odd steps on the odd site (input te), even steps on the even
-    // site (input rho). Step 0: rho = r_o - D_oe A_ee^-1 r_e. Steps 1..2 n_MR:
+    // ---- 3.-5. Schur right-hand side, MR steps, reconstruction: half-steps,
+    // odd steps on the odd site (input te), even steps on the even site
+    // (input rho). Step 0: rho = r_o - D_oe A_ee^-1 r_e. Steps 1..2 n_MR:
     // te = A_ee^-1 D_eo rho, then p = A_oo rho - D_oe te and the MR update.
     // Last step: e_e = A_ee^-1 (r_e - D_eo e_o).
     cpx<C> m[18], tmp[6], rh[6], eo[6], ee[6];
@@ -431,9 +432,22 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
       rh[i] = {0, 0};
     }
     __syncthreads();
+    // step 0: rho = r_o - D_oe te (no clover multiply: rho is still zero)
+    {
+      Spinor<C> part;
+      hops_inner(Vh, Vh + j, h, nbr_o, 0, te, Lt, part);
+      cpx<C> hv[6];
+      exchange(xch, Vh, j, h, part, hv);
+  #pragma unroll
+      for (int i = 0; i < 6; i++) {
+        rh[i] = {r_o[i].re - hv[i].re, r_o[i].im - hv[i].im};
+        rho[(6 * h + i) * Vh + j] = nmr == 0 ? eo[i] : rh[i];
+      }
+      __syncthreads();
+    }
     const int last = 2 * nmr + 1;
   #pragma unroll 1
-    for (int step = 0; step <= last; step++) {
+    for (int step = 1; step <= last; step++) {
       const bool odd = (step & 1) == 0;
       Spinor<C> part;
       hops_inner(Vh, odd ? Vh + j : j, h, odd ? nbr_o : nbr_e, odd ? 0 : Vh, odd ? te : rho, Lt, part);
@@ -447,32 +461,27 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
       tile_block(odd ? Ao : Ai, j, h, m);
       herm6_mv(m, u, mu);
       if (odd) {
-        if (step == 0) {
+        cpx<C> p[6];
+        C pr_re = 0, pr_im = 0, pp = 0;
   #pragma unroll
-          for (int i = 0; i < 6; i++) rh[i] = {r_o[i].re - hv[i].re, r_o[i].im - hv[i].im};
-        } else {
-          cpx<C> p[6];
-          C pr_re = 0, pr_im = 0, pp = 0;
+        for (int i = 0; i < 6; i++) {
+          p[i] = {mu[i].re - hv[i].re, mu[i].im - hv[i].im};
+          pr_re += p[i].re * rh[i].re + p[i].im * rh[i].im;
+          pr_im += p[i].re * rh[i].im - p[i].im * rh[i].re;
+          pp += p[i].re * p[i].re + p[i].im * p[i].im;
+        }
+        block_sum3(pr_re, pr_im, pp, red);
+        C a_re = 0, a_im = 0;
+        if (pp > (C)0) {
+          a_re = pr_re / pp;
+          a_im = pr_im / pp;
+        }
   #pragma unroll
-          for (int i = 0; i < 6; i++) {
-            p[i] = {mu[i].re - hv[i].re, mu[i].im - hv[i].im};
-            pr_re += p[i].re * rh[i].re + p[i].im * rh[i].im;
-            pr_im += p[i].re * rh[i].im - p[i].im * rh[i].re;
-            pp += p[i].re * p[i].re + p[i].im * p[i].im;
-          }
-          block_sum3(pr_re, pr_im, pp, red);
-          C a_re = 0, a_im = 0;
-          if (pp > (C)0) {
-            a_re = pr_re / pp;
-            a_im = pr_im / pp;
-          }
-  #pragma unroll
-          for (int i = 0; i < 6; i++) {
-            eo[i].re += a_re * rh[i].re - a_im * rh[i].im;
-            eo[i].im += a_re * rh[i].im + a_im * rh[i].re;
-            rh[i].re -= a_re * p[i].re - a_im * p[i].im;
-            rh[i].im -= a_re * p[i].im + a_im * p[i].re;
-          }
+        for (int i = 0; i < 6; i++) {
+          eo[i].re += a_re * rh[i].re - a_im * rh[i].im;
+          eo[i].im += a_re * rh[i].im + a_im * rh[i].re;
+          rh[i].re -= a_re * p[i].re - a_im * p[i].im;
+          rh[i].im -= a_re * p[i].im + a_im * p[i].re;
         }
         // the even half-step after the last MR update reads e_o instead of rho
         const bool last_odd = step == 2 * nmr;
