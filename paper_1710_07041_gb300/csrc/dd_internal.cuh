@@ -484,14 +484,16 @@ __device__ __forceinline__ void project(const Spinor<C> &p, cpx<C> *chi) {
   }
 }
 
-// acc += sgn * reconstruct(h): upper spins h, lower spins -+ A^+ h.
-template <int MU, bool FWD, typename C>
+// acc += sgn * reconstruct(h): upper spins h, lower spins -+ A^+ h. With SW
+// the two spin halves of acc are stored swapped (upper in c[6..11]).
+template <int MU, bool FWD, typename C, bool SW = false>
 __device__ __forceinline__ void accum_recon(Spinor<C> &acc, const cpx<C> *h, C sgn) {
+  constexpr int UP = SW ? 6 : 0, LO = SW ? 0 : 6;
 #pragma unroll
   for (int c = 0; c < 3; c++) {
     cpx<C> h0 = {sgn * h[c].re, sgn * h[c].im}, h1 = {sgn * h[3 + c].re, sgn * h[3 + c].im};
-    acc.c[c].re += h0.re; acc.c[c].im += h0.im;
-    acc.c[3 + c].re += h1.re; acc.c[3 + c].im += h1.im;
+    acc.c[UP + c].re += h0.re; acc.c[UP + c].im += h0.im;
+    acc.c[UP + 3 + c].re += h1.re; acc.c[UP + 3 + c].im += h1.im;
     cpx<C> l0, l1;
     if constexpr (MU == 0) {        // A^+ h = (i h1, i h0)
       l0 = {-h1.im, h1.re}; l1 = {-h0.im, h0.re};
@@ -503,23 +505,24 @@ __device__ __forceinline__ void accum_recon(Spinor<C> &acc, const cpx<C> *h, C s
       l0 = h0; l1 = h1;
     }
     if (FWD) {
-      acc.c[6 + c].re -= l0.re; acc.c[6 + c].im -= l0.im;
-      acc.c[9 + c].re -= l1.re; acc.c[9 + c].im -= l1.im;
+      acc.c[LO + c].re -= l0.re; acc.c[LO + c].im -= l0.im;
+      acc.c[LO + 3 + c].re -= l1.re; acc.c[LO + 3 + c].im -= l1.im;
     } else {
-      acc.c[6 + c].re += l0.re; acc.c[6 + c].im += l0.im;
-      acc.c[9 + c].re += l1.re; acc.c[9 + c].im += l1.im;
+      acc.c[LO + c].re += l0.re; acc.c[LO + c].im += l0.im;
+      acc.c[LO + 3 + c].re += l1.re; acc.c[LO + 3 + c].im += l1.im;
     }
   }
 }
 
-// One hop: acc += sgn * (1 -+ g_mu) W psi, W = U (FWD) or U^dagger.
-template <int MU, bool FWD, typename C>
+// One hop: acc += sgn * (1 -+ g_mu) W psi, W = U (FWD) or U^dagger (SW: acc's
+// spin halves stored swapped).
+template <int MU, bool FWD, typename C, bool SW = false>
 __device__ __forceinline__ void hop(Spinor<C> &acc, const Link<C> &u, const Spinor<C> &psi, C sgn) {
   cpx<C> chi[6], h[6];
   project<MU, FWD>(psi, chi);
   if (FWD) su3_mul(u, chi, h);
   else su3_dmul(u, chi, h);
-  accum_recon<MU, FWD>(acc, h, sgn);
+  accum_recon<MU, FWD, C, SW>(acc, h, sgn);
 }
 
 // ------------------------------------------------------------ clover blocks

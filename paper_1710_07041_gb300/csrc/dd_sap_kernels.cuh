@@ -129,7 +129,8 @@ __device__ __forceinline__ uint2 inner_neighbours(const Geom &g, const Site &t, 
 // acc += hop pair in direction MU into the site at tile position s from the
 // shared half-vector v (the other parity), links from tile L. nf/nbk: neighbour
 // indices (NONE: outside the block); off: tile offset of the other parity.
-template <int MU, typename C, typename P>
+// SW: acc holds its spin halves swapped.
+template <int MU, bool SW, typename C, typename P>
 __device__ __forceinline__ void hop_inner_dir(int Vh, int s, unsigned nf, unsigned nbk, int off, const cpx<C> *v,
                                               const Tile<P> &L, Spinor<C> &acc) {
   Link<C> u;
@@ -137,33 +138,35 @@ __device__ __forceinline__ void hop_inner_dir(int Vh, int s, unsigned nf, unsign
   if (nf != NONE) {
     vec_load(v, Vh, (int)nf, psi);
     tile_link(L, s, MU, u);
-    hop<MU, true>(acc, u, psi, (C)-0.5);
+    hop<MU, true, C, SW>(acc, u, psi, (C)-0.5);
   }
   if (nbk != NONE) {
     vec_load(v, Vh, (int)nbk, psi);
     tile_link(L, (int)nbk + off, MU, u);
-    hop<MU, false>(acc, u, psi, (C)-0.5);
+    hop<MU, false, C, SW>(acc, u, psi, (C)-0.5);
   }
 }
 
+// The thread's partial sum over its two directions, its own spin half h in
+// acc.c[0..5] and the partner's half in acc.c[6..11] (exchange's layout).
 template <typename C, typename P>
 __device__ __forceinline__ void hops_inner(int Vh, int s, int h, uint2 nbr, int off, const cpx<C> *v,
                                            const Tile<P> &L, Spinor<C> &acc) {
 #pragma unroll
   for (int i = 0; i < 12; i++) acc.c[i] = {0, 0};
   if (h == 0) {
-    hop_inner_dir<0>(Vh, s, nbr.x & NONE, nbr.x >> 16, off, v, L, acc);
-    hop_inner_dir<1>(Vh, s, nbr.y & NONE, nbr.y >> 16, off, v, L, acc);
+    hop_inner_dir<0, false>(Vh, s, nbr.x & NONE, nbr.x >> 16, off, v, L, acc);
+    hop_inner_dir<1, false>(Vh, s, nbr.y & NONE, nbr.y >> 16, off, v, L, acc);
   } else {
-    hop_inner_dir<2>(Vh, s, nbr.x & NONE, nbr.x >> 16, off, v, L, acc);
-    hop_inner_dir<3>(Vh, s, nbr.y & NONE, nbr.y >> 16, off, v, L, acc);
+    hop_inner_dir<2, true>(Vh, s, nbr.x & NONE, nbr.x >> 16, off, v, L, acc);
+    hop_inner_dir<3, true>(Vh, s, nbr.y & NONE, nbr.y >> 16, off, v, L, acc);
   }
 }
 
 // acc += hops into site t from the global field x, directions {2h, 2h+1};
 // neighbours inside the block are skipped when self_zero (x known to be 0
-// there), neighbours outside when halo_zero.
-template <int MU, typename S, typename C>
+// there), neighbours outside when halo_zero. SW: acc's spin halves swapped.
+template <int MU, bool SW, typename S, typename C>
 __device__ __forceinline__ void hop_global_dir(const Geom &g, const Site &t, const void *links, const void *x,
                                                bool self_zero, bool halo_zero, Spinor<C> &acc) {
   int nb, ns;
@@ -175,27 +178,28 @@ __device__ __forceinline__ void hop_global_dir(const Geom &g, const Site &t, con
   if (inside ? !self_zero : !halo_zero) {
     load_spinor<S, C>(x, g, nb, ns, psi);
     load_link<S, C>(links, g, t.b, t.s, MU, u);
-    hop<MU, true>(acc, u, psi, (C)(-0.5f * sg));
+    hop<MU, true, C, SW>(acc, u, psi, (C)(-0.5f * sg));
   }
   neighbour(g, t, MU, -1, &nb, &ns, &sg, &inside);
   if (inside ? !self_zero : !halo_zero) {
     load_spinor<S, C>(x, g, nb, ns, psi);
     load_link<S, C>(links, g, nb, ns, MU, u);
-    hop<MU, false>(acc, u, psi, (C)(-0.5f * sg));
+    hop<MU, false, C, SW>(acc, u, psi, (C)(-0.5f * sg));
   }
 }
 
+// (own spin half in acc.c[0..5], the partner's in acc.c[6..11], as hops_inner)
 template <typename S, typename C>
 __device__ __forceinline__ void hops_global(const Geom &g, const Site &t, int h, const void *links, const void *x,
                                             bool self_zero, bool halo_zero, Spinor<C> &acc) {
 #pragma unroll
   for (int i = 0; i < 12; i++) acc.c[i] = {0, 0};
   if (h == 0) {
-    hop_global_dir<0, S, C>(g, t, links, x, self_zero, halo_zero, acc);
-    hop_global_dir<1, S, C>(g, t, links, x, self_zero, halo_zero, acc);
+    hop_global_dir<0, false, S, C>(g, t, links, x, self_zero, halo_zero, acc);
+    hop_global_dir<1, false, S, C>(g, t, links, x, self_zero, halo_zero, acc);
   } else {
-    hop_global_dir<2, S, C>(g, t, links, x, self_zero, halo_zero, acc);
-    hop_global_dir<3, S, C>(g, t, links, x, self_zero, halo_zero, acc);
+    hop_global_dir<2, true, S, C>(g, t, links, x, self_zero, halo_zero, acc);
+    hop_global_dir<3, true, S, C>(g, t, links, x, self_zero, halo_zero, acc);
   }
 }
 
@@ -207,7 +211,8 @@ __device__ __forceinline__ void half_of(const Spinor<C> &s, int h, cpx<C> *out) 
   for (int i = 0; i < 6; i++) out[i] = h ? s.c[6 + i] : s.c[i];
 }
 
-// Exchange partial hop sums between the two halves of a site pair: on return
+// Exchange partial hop sums between the two halves of a site pair (part:
+// own spin half h in c[0..5], the partner's in c[6..11]): on return
 // own[0..5] = full sum of the components of half h. xch: [12][Vh] smem. A
 // thread reads only the entries its partner wrote for it, so the next write
 // to xch needs one barrier after this call (every caller has one).
@@ -215,28 +220,34 @@ template <typename C>
 __device__ __forceinline__ void exchange(cpx<C> *xch, int Vh, int j, int h, const Spinor<C> &part, cpx<C> *own) {
   const int other = 6 * (1 - h), mine = 6 * h;
 #pragma unroll
-  for (int i = 0; i < 6; i++) xch[(other + i) * Vh + j] = h ? part.c[i] : part.c[6 + i];
+  for (int i = 0; i < 6; i++) xch[(other + i) * Vh + j] = part.c[6 + i];
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < 6; i++) {
-    cpx<C> a = h ? part.c[6 + i] : part.c[i], b = xch[(mine + i) * Vh + j];
+    cpx<C> a = part.c[i], b = xch[(mine + i) * Vh + j];
     own[i] = {a.re + b.re, a.im + b.im};
   }
 }
 
-// deterministic block sum of three values; red: smem [3][32]. The reads of
-// red are not followed by a barrier here: the caller reaches one (the end of
-// its half-step) before any thread can write red again.
-template <typename C>
+// deterministic block sum of three values; red: smem [3][32]. NW: warps per
+// CTA when the block shape fixes it at compile time (whole warps), else 0
+// (any blockDim.x up to 1024). The reads of red are not followed by a barrier
+// here: the caller reaches one (the end of its half-step) before any thread
+// can write red again.
+template <int NW, typename C>
 __device__ __forceinline__ void block_sum3(C &a, C &b, C &c, C *red) {
-  const int width = blockDim.x < 32 ? blockDim.x : 32;
+  static_assert(NW >= 0 && NW <= 32, "warps per CTA");
+  const int width = NW > 0 ? 32 : (blockDim.x < 32 ? blockDim.x : 32);
   const unsigned mask = width == 32 ? 0xffffffffu : ((1u << width) - 1u);
-  for (int o = width / 2; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(mask, a, o);
-    b += __shfl_xor_sync(mask, b, o);
-    c += __shfl_xor_sync(mask, c, o);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    if (o < width) {
+      a += __shfl_xor_sync(mask, a, o);
+      b += __shfl_xor_sync(mask, b, o);
+      c += __shfl_xor_sync(mask, c, o);
+    }
   }
-  const int w = threadIdx.x / 32, nw = (blockDim.x + 31) / 32;
+  const int w = threadIdx.x / 32, nw = NW > 0 ? NW : (blockDim.x + 31) / 32;
   if ((threadIdx.x & 31) == 0) {
     red[w] = a;
     red[32 + w] = b;
@@ -244,7 +255,9 @@ __device__ __forceinline__ void block_sum3(C &a, C &b, C &c, C *red) {
   }
   __syncthreads();
   a = b = c = 0;
-  for (int i = 0; i < nw; i++) {
+#pragma unroll
+  for (int i = 0; i < (NW > 0 ? NW : 32); i++) {
+    if (NW == 0 && i >= nw) break;
     a += red[i];
     b += red[32 + i];
     c += red[64 + i];
@@ -274,6 +287,8 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
                                                    int halo_zero, int nmr, int tile, unsigned *timeouts) {
   using C = typename Store<S>::comp_t;
   using P = typename Store<S>::pair_t;
+  // a specialised shape is launched with one thread per site: blockDim.x == NT
+  static_assert(SHAPE == 0 || (SHAPE == 1 && NT == 256) || (SHAPE == 2 && NT == 512), "shape / threads");
   extern __shared__ __align__(16) unsigned char smem[];
   const Geom g = block_shape<SHAPE>(g_in);
   const int Vh = g.Vh, Vb = g.Vb;
@@ -470,7 +485,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
           pr_im += p[i].re * rh[i].im - p[i].im * rh[i].re;
           pp += p[i].re * p[i].re + p[i].im * p[i].im;
         }
-        block_sum3(pr_re, pr_im, pp, red);
+        block_sum3<SHAPE != 0 ? NT / 32 : 0>(pr_re, pr_im, pp, red);
         C a_re = 0, a_im = 0;
         if (pp > (C)0) {
           a_re = pr_re / pp;
