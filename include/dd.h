@@ -228,6 +228,18 @@ typedef struct {
 int dd_solve(dd_op_t op, const dd_solve_params *p, const double *b, double *x, int nrhs,
              dd_solve_info *info, void *stream);
 
+/* The workspace of dd_solve (Krylov basis, preconditioned vectors, scratch
+ * fields and reduction buffers: about 6 kB per site and right-hand side at
+ * restart 16) is cached when the call ends and reused by the next dd_solve
+ * that needs buffers of the same sizes on the same device, which saves the
+ * allocation and release (milliseconds, and a device synchronisation) per
+ * call. A solve that cannot allocate releases the cache first; the cache
+ * holds at most half of the device memory and 64 MB of pinned host memory;
+ * dd_server_create releases it (the server budgets device memory itself and
+ * its workers free their buffers). This call frees every cached buffer (all
+ * devices), e.g. to return the memory to other users. Returns DD_OK. */
+int dd_release_workspace(void);
+
 /* ------------------------------------------------------- two-level multigrid */
 
 typedef struct {

@@ -82,6 +82,7 @@ EXPORTS = {
     "dd_kernel_launches": ([], ctypes.c_uint64),
     "dd_device_status": ([], ctypes.c_int),
     "dd_selftest_wait": ([ctypes.c_int], ctypes.c_int),
+    "dd_release_workspace": ([], ctypes.c_int),
     "dd_create_lattice": ([ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                            ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "dd_lattice_volume": ([ctypes.c_void_p], ctypes.c_long),
@@ -463,6 +464,12 @@ def device_status():
     """Wait for the device; raise DDError if a bounded in-kernel wait expired
     since the previous call (dd_device_status)."""
     _check(lib().dd_device_status(), "dd_device_status")
+
+
+def release_workspace():
+    """dd_release_workspace: free the cached solver workspaces (device and
+    pinned host buffers) that finished solves left for reuse."""
+    _check(lib().dd_release_workspace(), "dd_release_workspace")
 
 
 def selftest_wait(expire: bool):

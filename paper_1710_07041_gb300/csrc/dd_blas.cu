@@ -4,6 +4,7 @@
 // with a fixed grid and a fixed summation order, so every result is
 // bit-reproducible and independent of what else runs on the device.
 #include "dd_blas.cuh"
+#include "dd_pool.cuh"
 
 namespace dd {
 namespace {
@@ -430,10 +431,21 @@ Blas::~Blas() {
 
 int Blas::init(int sms) {
   nblk = sms > 0 ? 4 * sms : 608;
-  DD_CUDA(cudaMalloc(&partial, sizeof(double) * (size_t)nblk * (2 * 16 + 1)));
-  DD_CUDA(cudaMalloc(&result, sizeof(double) * 256));
-  DD_CUDA(cudaMallocHost(&hpin, sizeof(double) * 256));
+  partial = (double *)pool_dev_alloc(sizeof(double) * (size_t)nblk * (2 * 16 + 1));
+  result = (double *)pool_dev_alloc(sizeof(double) * 256);
+  hpin = (double *)pool_host_alloc(sizeof(double) * 256);
+  if (!partial || !result || !hpin) {
+    set_error("blas: out of memory for reduction scratch");
+    return DD_ENOMEM;
+  }
   return DD_OK;
+}
+
+void Blas::release_to_pool() {
+  pool_dev_free(partial, sizeof(double) * (size_t)nblk * (2 * 16 + 1));
+  pool_dev_free(result, sizeof(double) * 256);
+  pool_host_free(hpin, sizeof(double) * 256);
+  partial = result = hpin = nullptr;
 }
 
 int Blas::mdot(const double *V, size_t ldv, int k, const double *w, size_t n, double *h_dev, double *wnorm2_dev,

@@ -12,6 +12,8 @@ struct Blas {
   double *hpin = nullptr;     // pinned host mirror
   ~Blas();
   int init(int sms);
+  // return the scratch to the workspace cache (no queued work may use it)
+  void release_to_pool();
   // h[i] = <V_i, w> (i < k, complex, FP64), *wnorm2 = <w, w>; V_i = V + i * ldv complex
   int mdot(const double *V, size_t ldv, int k, const double *w, size_t n, double *h_dev, double *wnorm2_dev,
            cudaStream_t st);

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "dd_solver.cuh"
+#include "dd_pool.cuh"
 
 namespace dd {
 
@@ -112,6 +113,7 @@ static void worker_main(Worker *w) {
   Server *srv = w->srv;
   cudaSetDevice(srv->device);
   std::unique_ptr<BatchSolver> bs(new BatchSolver(w->op, w->params, w->slots, w->stream));
+  bs->set_cache_workspace(false);   // the budget accounts for this memory: free it on exit
   int rc = bs->init();
   auto next = [&](RhsJob &job) -> bool {
     std::lock_guard<std::mutex> lk(srv->mu);
@@ -166,15 +168,17 @@ static void worker_main(Worker *w) {
     if (!srv->cv.wait_for(lk, std::chrono::milliseconds(500), [&] { return srv->stop || has_work(); }) ||
         srv->stop || rc != DD_OK) {
       if (has_work() && !srv->stop && rc == DD_OK) continue;
-      w->exited = true;
-      srv->in_use -= w->bytes;
-      w->bytes = 0;
-      srv->cv.notify_all();
+      w->exited = true;   // takes no new work
       break;
     }
   }
   bs.reset();
   cudaStreamSynchronize(w->stream);
+  // the budget gets the memory back only once it is freed
+  std::lock_guard<std::mutex> lk(srv->mu);
+  srv->in_use -= w->bytes;
+  w->bytes = 0;
+  srv->cv.notify_all();
 }
 
 static void scheduler_main(Server *srv) {
@@ -272,6 +276,9 @@ int dd_server_create(const dd_server_params *p, dd_server_t *out) {
   if (!srv) return DD_ENOMEM;
   srv->p = *p;
   cudaGetDevice(&srv->device);
+  // the server budgets device memory itself: cached solver workspaces of
+  // earlier dd_solve calls are released first
+  pool_release();
   size_t free_b = 0, total_b = 0;
   cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
   if (e != cudaSuccess) {

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "dd_solver.cuh"
+#include "dd_pool.cuh"
 
 namespace dd {
 
@@ -69,17 +70,38 @@ BatchSolver::BatchSolver(const Op *op, const dd_solve_params &p, int slots, cuda
   sigma_ = std::sqrt(24.0 * (double)g.V);  // unit-norm vector -> unit RMS entries
 }
 
+// The device buffers of one slot with their sizes (allocation and release
+// walk the same list).
+std::vector<std::pair<void **, size_t>> BatchSolver::slot_buffers(Slot &s) const {
+  const size_t m = (size_t)m_alloc_;
+  return {{(void **)&s.Vb, (m + 1) * f64_}, {(void **)&s.Z, m * fz_},   {(void **)&s.x, f64_},
+          {(void **)&s.b, f64_},           {(void **)&s.w, f64_},       {(void **)&s.canon, f64_},
+          {&s.tin, fp_},                   {&s.tout, fp_},              {&s.zt, fz_},
+          {(void **)&s.sdev, sizeof(double) * (m + 1)}};
+}
+
 BatchSolver::~BatchSolver() {
-  for (auto &s : slots_) {
-    void *ptrs[] = {s.Vb, s.Z, s.x, s.b, s.w, s.canon, s.tin, s.tout, s.zt, s.sdev};
-    for (void *q : ptrs)
-      if (q) cudaFree(q);
-    delete s.mgw;
+  if (cache_) {
+    // the workspace goes back to the cache, so no queued work may still use it
+    cudaStreamSynchronize(st_);
+    const size_t n = slots_.size();
+    for (auto &s : slots_)
+      for (auto &pb : slot_buffers(s)) pool_dev_free(*pb.first, pb.second);
+    pool_dev_free(hdev_, sizeof(double) * HSTRIDE * n);
+    pool_dev_free(ydev_, sizeof(double) * 2 * 64 * n);
+    pool_host_free(hpin_, sizeof(double) * HSTRIDE * n);
+    pool_host_free(ypin_, sizeof(double) * 2 * 64 * n);
+    blas_.release_to_pool();
+  } else {
+    for (auto &s : slots_)
+      for (auto &pb : slot_buffers(s))
+        if (*pb.first) cudaFree(*pb.first);
+    if (hdev_) cudaFree(hdev_);
+    if (ydev_) cudaFree(ydev_);
+    if (hpin_) cudaFreeHost(hpin_);
+    if (ypin_) cudaFreeHost(ypin_);
   }
-  if (hdev_) cudaFree(hdev_);
-  if (ydev_) cudaFree(ydev_);
-  if (hpin_) cudaFreeHost(hpin_);
-  if (ypin_) cudaFreeHost(ypin_);
+  for (auto &s : slots_) delete s.mgw;
   for (auto &e : ev_)
     if (e) cudaEventDestroy(e);
   if (own_stream_) cudaStreamDestroy(st_);
@@ -87,20 +109,17 @@ BatchSolver::~BatchSolver() {
 
 int BatchSolver::init() {
   const int m = p_.restart, n = (int)slots_.size();
+  m_alloc_ = m;
   if (n < 1 || n > MAX_RHS) {
     set_error("solver: 1..%d slots", MAX_RHS);
     return DD_EINVAL;
   }
   for (auto &s : slots_) {
-    bool ok = cudaMalloc((void **)&s.Vb, (size_t)(m + 1) * f64_) == cudaSuccess &&
-              cudaMalloc((void **)&s.Z, (size_t)m * fz_) == cudaSuccess &&
-              cudaMalloc((void **)&s.x, f64_) == cudaSuccess && cudaMalloc((void **)&s.b, f64_) == cudaSuccess &&
-              cudaMalloc((void **)&s.w, f64_) == cudaSuccess && cudaMalloc((void **)&s.canon, f64_) == cudaSuccess &&
-              cudaMalloc(&s.tin, fp_) == cudaSuccess && cudaMalloc(&s.tout, fp_) == cudaSuccess &&
-              cudaMalloc(&s.zt, fz_) == cudaSuccess && cudaMalloc((void **)&s.sdev, sizeof(double) * (m + 1)) == cudaSuccess;
+    bool ok = true;
+    for (auto &pb : slot_buffers(s))
+      if (ok) ok = (*pb.first = pool_dev_alloc(pb.second)) != nullptr;
     s.scl.assign(m + 1, 1.0);
     if (!ok) {
-      cudaGetLastError();
       set_error("solver: out of device memory for %d FGMRES(%d) slots (%zu bytes each)", n, m,
                 bytes_per_slot(op_->lat->g, op_->prec, m));
       return DD_ENOMEM;
@@ -116,10 +135,14 @@ int BatchSolver::init() {
     s.y.assign(m, 0);
     s.cs.assign(m, 0);
   }
-  DD_CUDA(cudaMalloc((void **)&hdev_, sizeof(double) * HSTRIDE * n));
-  DD_CUDA(cudaMalloc((void **)&ydev_, sizeof(double) * 2 * 64 * n));
-  DD_CUDA(cudaMallocHost((void **)&hpin_, sizeof(double) * HSTRIDE * n));
-  DD_CUDA(cudaMallocHost((void **)&ypin_, sizeof(double) * 2 * 64 * n));
+  hdev_ = (double *)pool_dev_alloc(sizeof(double) * HSTRIDE * n);
+  ydev_ = (double *)pool_dev_alloc(sizeof(double) * 2 * 64 * n);
+  hpin_ = (double *)pool_host_alloc(sizeof(double) * HSTRIDE * n);
+  ypin_ = (double *)pool_host_alloc(sizeof(double) * 2 * 64 * n);
+  if (!hdev_ || !ydev_ || !hpin_ || !ypin_) {
+    set_error("solver: out of memory for the Hessenberg buffers");
+    return DD_ENOMEM;
+  }
   for (auto &e : ev_) DD_CUDA(cudaEventCreate(&e));
   // work on a stream of our own when given the legacy default stream, so the
   // smoother's launches can be captured into CUDA graphs
@@ -517,6 +540,7 @@ extern "C" int dd_solve(dd_op_t opp, const dd_solve_params *p, const double *b, 
   // as many slots as right-hand sides, bounded by free device memory
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
+  free_b += pool_cached_bytes();   // cached workspaces are reused or released
   size_t per = BatchSolver::bytes_per_slot(g, op->prec, p->restart);
   if (p->mg) per += MgWork::bytes(g, op->prec, ((Mg *)p->mg)->N, ((Mg *)p->mg)->p.coarse_max_iter);
   int slots = nrhs < MAX_RHS ? nrhs : MAX_RHS;

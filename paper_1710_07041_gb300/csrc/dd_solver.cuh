@@ -3,6 +3,7 @@
 #include <chrono>
 #include <complex>
 #include <functional>
+#include <utility>
 #include <vector>
 
 #include "dd_mg.cuh"
@@ -62,6 +63,8 @@ class BatchSolver {
   const Op *op() const { return op_; }
   const dd_solve_params &params() const { return p_; }
   void set_params(const dd_solve_params &p) { p_ = p; }
+  // false: the destructor frees the workspace instead of caching it for reuse
+  void set_cache_workspace(bool on) { cache_ = on; }
 
  private:
   int start(Slot &s);
@@ -70,6 +73,7 @@ class BatchSolver {
   int end_cycle(Slot &s);
   int retire(Slot &s, int status);
   int sync_h();
+  std::vector<std::pair<void **, size_t>> slot_buffers(Slot &s) const;
   int mdot(Slot *s, int kk, double *h, double *wn2, bool from32 = false);
   int maxpy(Slot *s, int kk, const double *h, double *wn2, bool from32 = false);
 
@@ -90,6 +94,8 @@ class BatchSolver {
   cudaStream_t caller_ = nullptr;  // the caller's stream
   bool own_stream_ = false;        // st_ created here (the caller passed the legacy stream)
   int failed_ = 0;
+  bool cache_ = true;   // release the workspace into the cache (dd_pool.cu)
+  int m_alloc_ = 0;     // restart length the slot buffers were sized for
 };
 
 constexpr int HSTRIDE = 2 * 65 + 6;  // h column (complex) + norms

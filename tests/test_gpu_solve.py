@@ -68,3 +68,29 @@ def test_not_converged_and_zero_rhs():
     x, info = s.op.solve(np.zeros_like(b))
     assert info[0]["status"] == 0 and not x.any()
     s.close()
+
+
+def test_workspace_cache_reuse_and_release():
+    """A solve reuses the workspace the previous one left in the cache (its
+    buffers still hold that solve's data): the result is bitwise the same as
+    the first solve's. dd_release_workspace gives the memory back."""
+    import torch
+    s = Setup((8, 8, 8, 16), (4, 4, 4, 4), prec=dd.F32, seed=27)
+    b = synth.gaussian_spinor(s.V, 28)
+    b2 = synth.gaussian_spinor(s.V, 29)
+    dd.release_workspace()
+    x1, info1 = s.op.solve(b, tol=1e-10)
+    s.op.solve(b2, tol=1e-10)            # leaves different data in the cached buffers
+    x3, info3 = s.op.solve(b, tol=1e-10)
+    assert info1[0]["status"] == 0 and info3[0]["status"] == 0
+    assert info3[0]["iterations"] == info1[0]["iterations"]
+    assert np.array_equal(x1, x3)
+    assert true_res(s, x3, b) <= 1e-10
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    dd.release_workspace()
+    free1 = torch.cuda.mem_get_info()[0]
+    # the cached slot: (m + 1) double-float basis fields, m FP32 fields, and
+    # scratch - at least the basis, 17 x 24 x 8 bytes per site
+    assert free1 - free0 >= 17 * 24 * 8 * s.V
+    s.close()
