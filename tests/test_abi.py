@@ -55,3 +55,9 @@ def test_null_arguments_are_rejected():
     assert L.dd_sap_smooth(None, None, None, None, 1, None) == -1
     assert L.dd_solve(None, None, None, None, 1, None, None) == -1
     L.dd_destroy(None)
+
+
+def test_release_workspace_with_nothing_cached():
+    """dd_release_workspace on a process that has not solved anything (here,
+    no GPU at all): nothing to free, DD_OK."""
+    assert dd.lib().dd_release_workspace() == 0
