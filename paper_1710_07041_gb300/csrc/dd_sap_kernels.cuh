@@ -279,8 +279,9 @@ template <typename S> struct SapSmem {
 
 // STAGE: 0 operator tiles read through L1/L2; 1 links, A_oo and A_ee^-1 staged
 // in shared memory; 2 links staged, the clover blocks (each read by one
-// thread only) through L1/L2, which halves the footprint.
-template <typename S, int STAGE, int MINB, int NT, int SHAPE>
+// thread only) through L1/L2, which halves the footprint. UNROLL (specialised
+// shapes only): the MR loop's even and odd half-steps as separate code.
+template <typename S, int STAGE, int MINB, int NT, int SHAPE, bool UNROLL = false>
 __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *__restrict__ links,
                                                    const void *__restrict__ clov, const void *__restrict__ cinv,
                                                    const RhsPtrs rp, int colour, int self_zero,
@@ -460,6 +461,67 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
       }
       __syncthreads();
     }
+    if constexpr (UNROLL && SHAPE != 0) {
+    // steps 2k-1 (even) and 2k (odd) for k = 1..n_MR as separate code, then
+    // the last even step: no run-time parity selects, twice the hop code
+  #pragma unroll 1
+    for (int k = 1; k <= nmr + 1; k++) {
+      const bool last = k == nmr + 1;
+      {   // even: te = A_ee^-1 D_eo rho, or on the last step e_e = A_ee^-1 (r_e - D_eo e_o)
+        Spinor<C> part;
+        hops_inner(Vh, j, h, nbr_e, Vh, rho, Lt, part);
+        cpx<C> hv[6], u[6], mu[6];
+        exchange(xch, Vh, j, h, part, hv);
+  #pragma unroll
+        for (int i = 0; i < 6; i++) u[i] = last ? cpx<C>{r_e[i].re - hv[i].re, r_e[i].im - hv[i].im} : hv[i];
+        tile_block(Ai, j, h, m);
+        herm6_mv(m, u, mu);
+        if (last) {
+  #pragma unroll
+          for (int i = 0; i < 6; i++) ee[i] = mu[i];
+        } else {
+  #pragma unroll
+          for (int i = 0; i < 6; i++) te[(6 * h + i) * Vh + j] = mu[i];
+        }
+        __syncthreads();
+      }
+      if (last) break;
+      {   // odd: p = A_oo rho - D_oe te and the MR update of e_o and rho
+        Spinor<C> part;
+        hops_inner(Vh, Vh + j, h, nbr_o, 0, te, Lt, part);
+        cpx<C> hv[6], mu[6], p[6];
+        exchange(xch, Vh, j, h, part, hv);
+        tile_block(Ao, j, h, m);
+        herm6_mv(m, rh, mu);
+        C pr_re = 0, pr_im = 0, pp = 0;
+  #pragma unroll
+        for (int i = 0; i < 6; i++) {
+          p[i] = {mu[i].re - hv[i].re, mu[i].im - hv[i].im};
+          pr_re += p[i].re * rh[i].re + p[i].im * rh[i].im;
+          pr_im += p[i].re * rh[i].im - p[i].im * rh[i].re;
+          pp += p[i].re * p[i].re + p[i].im * p[i].im;
+        }
+        block_sum3<SHAPE != 0 ? NT / 32 : 0>(pr_re, pr_im, pp, red);
+        C a_re = 0, a_im = 0;
+        if (pp > (C)0) {
+          a_re = pr_re / pp;
+          a_im = pr_im / pp;
+        }
+  #pragma unroll
+        for (int i = 0; i < 6; i++) {
+          eo[i].re += a_re * rh[i].re - a_im * rh[i].im;
+          eo[i].im += a_re * rh[i].im + a_im * rh[i].re;
+          rh[i].re -= a_re * p[i].re - a_im * p[i].im;
+          rh[i].im -= a_re * p[i].im + a_im * p[i].re;
+        }
+        // the even step after the last MR update reads e_o instead of rho
+        const bool last_odd = k == nmr;
+  #pragma unroll
+        for (int i = 0; i < 6; i++) rho[(6 * h + i) * Vh + j] = last_odd ? eo[i] : rh[i];
+        __syncthreads();
+      }
+    }
+    } else {
     const int last = 2 * nmr + 1;
   #pragma unroll 1
     for (int step = 1; step <= last; step++) {
@@ -511,6 +573,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
       }
       __syncthreads();
     }
+    }
 
     // ---- x += e: gather both halves through shared memory, then half 0
     // writes the even site j and half 1 the odd site j
@@ -542,11 +605,11 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
   }  // work items
 }
 
-template <typename S, int STAGE, int MINB, int NT, int SHAPE>
+template <typename S, int STAGE, int MINB, int NT, int SHAPE, bool UNROLL = false>
 int sap_k(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, int tile, bool persistent,
           cudaStream_t st) {
   size_t smem = SapSmem<S>::bytes(g, STAGE);
-  auto kern = k_sap_phase<S, STAGE, MINB, NT, SHAPE>;
+  auto kern = k_sap_phase<S, STAGE, MINB, NT, SHAPE, UNROLL>;
   // raise the kernel's dynamic shared-memory limit once (never during a capture)
   static std::mutex mu;
   static int raised = 0;
@@ -588,12 +651,26 @@ int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtr
   if (shape_of(g) == SH) return sap_k<S, STAGE, MINB, NT, SH>(g, f, p, rp, tile, persistent, st);
   return sap_k<S, STAGE, MINB, NT, 0>(g, f, p, rp, tile, persistent, st);
 }
+// the MR loop unrolled by parity (specialised shape only)
+template <typename S, int STAGE, int MINB, int NT = 256>
+int sap_u(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, int tile, bool persistent,
+          cudaStream_t st) {
+  constexpr int SH = NT == 256 ? 1 : 2;
+  if (shape_of(g) != SH) {
+    set_error("sap: the unrolled MR loop exists for the specialised block shapes only");
+    return DD_EINVAL;
+  }
+  return sap_k<S, STAGE, MINB, NT, SH, true>(g, f, p, rp, tile, persistent, st);
+}
+
+template <typename S> constexpr bool sixteen_bit() { return Store<S>::prec == DD_F16 || Store<S>::prec == DD_BF16; }
 
 // Launch variants: tiles staged in shared memory with one CTA per SM; tiles
 // staged with two CTAs per SM (fits when the storage is 16-bit); only the
 // links staged, with two CTAs per SM (when the full staging does not fit
-// twice); tiles read through L1/L2 with two CTAs per SM. Variants that do not
-// fit are skipped.
+// twice); tiles read through L1/L2 with two CTAs per SM; for 16-bit storage
+// on the 4^4 shape with one right-hand side, the two-CTA layouts again with
+// the MR loop unrolled by parity. Variants that do not fit are skipped.
 // With several right-hand sides a CTA also solves `tile` of them with one
 // staging of its block's operator (rhs_tile; 0 lets the autotuner choose).
 template <typename S>
@@ -607,7 +684,7 @@ int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const
     set_error("sap: block of %d sites needs more shared memory than available", g.Vb);
     return DD_EINVAL;
   }
-  int layouts[4], nl = 0;
+  int layouts[6], nl = 0;
   if (g.Vb > 256) {
     // 512-site blocks (e.g. 8 x 4^3): 512 threads, one CTA per SM
     layouts[nl++] = stage1 ? 3 : 4;
@@ -616,6 +693,13 @@ int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const
     if (stage2) layouts[nl++] = 1;
     if (links2) layouts[nl++] = 5;
     if (nost2 || !stage1) layouts[nl++] = 2;
+    // 16-bit storage on the 4^4 shape with one right-hand side: the two-CTA
+    // layouts also with the MR loop unrolled by parity (measured faster
+    // there, slower in multi-source tiles and for FP32)
+    if (sixteen_bit<S>() && shape_of(g) == 1 && rp.n == 1) {
+      if (stage2) layouts[nl++] = 6;
+      if (nost2 || !stage1) layouts[nl++] = 7;
+    }
   }
   int tiles[6], nt = 0;
   if (p.rhs_tile > 0) {
@@ -635,6 +719,13 @@ int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const
       case 3: return sap_t<S, 1, 1, 512>(g, f, p, rp, tile, pers, st);
       case 4: return sap_t<S, 0, 1, 512>(g, f, p, rp, tile, pers, st);
       case 5: return sap_t<S, 2, 2>(g, f, p, rp, tile, pers, st);
+      case 6:
+      case 7:
+        if constexpr (sixteen_bit<S>()) {
+          if (layout == 6) return sap_u<S, 1, 2>(g, f, p, rp, tile, pers, st);
+          return sap_u<S, 0, 2>(g, f, p, rp, tile, pers, st);
+        }
+        return (int)DD_EINVAL;
       default: return sap_t<S, 1, 1>(g, f, p, rp, tile, pers, st);
     }
   };

@@ -1,7 +1,8 @@
 """Every launch variant the autotuner can pick, forced one at a time
 (DD_TUNE_VARIANT), against the FP64 oracle: the Schwarz smoother's
 shared-memory layouts (all tiles staged with one or two CTAs per SM, links
-only staged, nothing staged), each with the one-CTA-per-block and the
+only staged, nothing staged; for 16-bit storage also the two-CTA layouts with
+the MR loop unrolled by parity), each with the one-CTA-per-block and the
 persistent grid, and the four Dslash launch shapes. Bounds as in
 test_gpu_sap.py and test_gpu_operator.py."""
 import os
@@ -42,7 +43,7 @@ def setup(request):
     s.close()
 
 
-@pytest.mark.parametrize("k", range(8))
+@pytest.mark.parametrize("k", range(10))
 def test_sap_variant(setup, k):
     s, b, want, _ = setup
     fb = s.lat.to_field(b, s.prec)
