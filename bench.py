@@ -5,7 +5,11 @@ A step is one full solve of D x = b to a true relative residual of 1e-10 on
 the 64 x 32^3 workload (T x L^3): links exp(i 0.25 H) with two stout steps
 (rho = 0.1), c_sw = 1.7, m0 = -0.02, Gaussian right-hand side; Schwarz
 smoother with 4^4 blocks, 4 sweeps x 4 MR steps in FP32 storage; FGMRES(16)
-with FP64 orthogonalisation, least-squares update and true residual.
+whose Krylov basis and true-residual Dslash are double-float (FP32 pairs,
+~48-bit significands) with an FP64 least-squares update and solution
+(--outer-f64: IEEE FP64 for those too). `config` names what ran.
+`mixed_96x48^3` adds apply_D and the Schwarz phase with FP16 and BF16
+storage on the 96 x 48^3 mixed-precision workload.
 
 Prints one JSON line. `value` is solves/s with all inputs resident in HBM;
 `e2e` is the same metric through dd_solve with host buffers (host-to-device
@@ -60,9 +64,9 @@ def measured_peaks():
     return dict(hbm_gbs=6800.0, bf16=1900.0, src="fallback", sm_max_mhz=2070.0)
 
 
-def fp32_alu_peak_tflops(sm_mhz):
-    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_alu_peak_tflops(sm_mhz, sms):
+    # SMs x 128 FP32 lanes x 2 flops (FMA) per clock
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 def kernel_traffic(kernel):
@@ -143,68 +147,175 @@ def oracle_operator(wl, U):
     return op, time.perf_counter() - t0
 
 
-def oracle_sample(wl, U, b, iters, cycles, op=None, t_setup=None):
-    """Time the FP64 oracle on a bounded sample of the workload (one Dslash and
-    one Schwarz sweep over the full lattice plus one orthogonalisation step)
-    and scale it to one solve with the given iteration and cycle counts."""
-    if op is None:
-        op, t_setup = oracle_operator(wl, U)
+def cpu_model():
+    """Host CPU model name (lscpu), else the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def oracle_iteration(wl, op, b, threads, basis=None):
+    """Time the FP64 oracle's parts of one FGMRES iteration on the full lattice
+    with `threads` OpenMP threads: one apply_D, one Schwarz sweep and the
+    oracle's own modified Gram-Schmidt step against the average basis length
+    of a cycle (restart / 2 + 1 vectors; the oracle runs it on one thread)."""
+    import oracle
+    used = oracle.set_threads(threads)
     t0 = time.perf_counter()
     op.apply(b)
     t_apply = time.perf_counter() - t0
     t0 = time.perf_counter()
     op.sap(wl["block"], b, 1, wl["mr_steps"])
     t_sweep = time.perf_counter() - t0
-    v = b.reshape(-1)
+    t_orth = None
+    if basis is not None:
+        t0 = time.perf_counter()
+        oracle.gram_schmidt(basis, b)
+        t_orth = time.perf_counter() - t0
+    return dict(threads=used, apply_D_s=t_apply, sweep_s=t_sweep, gram_schmidt_s=t_orth)
+
+
+def gram_schmidt_basis(wl, b):
+    L = wl["restart"] // 2 + 1
+    return np.tile(b.reshape(1, -1), (L, 1))
+
+
+def solve_seconds(wl, it, iters, cycles):
+    """Seconds of one oracle solve with `iters` Arnoldi steps and `cycles`
+    restarts from the measured parts of one iteration."""
+    t_iter = wl["sweeps"] * it["sweep_s"] + it["apply_D_s"] + it["gram_schmidt_s"]
+    return iters * t_iter + (cycles + 1) * it["apply_D_s"], t_iter
+
+
+SMALL_SOLVE_DIMS = (16, 8, 8, 8)
+
+
+def oracle_small_solve(wl):
+    """A whole oracle SAP-FGMRES solve, measured, on a 16 x 8^3 lattice with
+    the workload's gauge recipe, operator and solver parameters."""
+    import oracle
+    oracle.set_threads(host_cores())
+    U = synth.gauge(SMALL_SOLVE_DIMS, wl["eps"], wl["n_stout"], wl["rho"], wl["gauge_seed"])
+    b = synth.gaussian_spinor(int(np.prod(SMALL_SOLVE_DIMS)), wl["rhs_seed"])
+    op = oracle.Operator(SMALL_SOLVE_DIMS, U, wl["c_sw"], wl["m0"])
     t0 = time.perf_counter()
-    for _ in range(wl["restart"] // 2 + 1):    # average Gram-Schmidt length
-        h = np.vdot(v, v)
-        v = v - h * 1e-3 * v
-    t_orth = 2 * (time.perf_counter() - t0)
-    t_iter = wl["sweeps"] * t_sweep + t_apply + t_orth
-    t_solve = iters * t_iter + (cycles + 1) * t_apply
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return dict(value=1.0 / t_solve, unit="solves/s", cores=cores, kind="oracle",
-                sample=(f"FP64 oracle on the full {'x'.join(map(str, wl['dims']))} lattice: one apply_D "
-                        f"({t_apply:.2f} s), one Schwarz sweep ({t_sweep:.2f} s), one Gram-Schmidt pass "
-                        f"({t_orth:.2f} s); scaled to {iters} iterations x ({wl['sweeps']} sweeps + apply + "
-                        f"orthogonalisation) + {cycles + 1} true residuals; operator set-up {t_setup:.1f} s "
-                        f"not counted"),
-                seconds_per_solve=t_solve)
+    x, ok, st = op.fgmres(wl["block"], b, wl["restart"], 1e-10, 2000, wl["sweeps"], wl["mr_steps"])
+    t = time.perf_counter() - t0
+    return {"lattice_TZYX": list(SMALL_SOLVE_DIMS), "seconds": t, "iterations": st["iterations"],
+            "cycles": st["cycles"], "true_rel_residual": st["rel_residual"], "converged": bool(ok),
+            "threads": host_cores()}
+
+
+def oracle_baseline(wl, U, b, iters, cycles, single_thread=True):
+    """The CPU baseline of the contract line: the FP64 oracle, as it stands, on
+    the host cores. Measured on the full workload lattice: the parts of one
+    FGMRES iteration on all cores (and apply_D and one sweep on one thread,
+    whose flop rate compares with the paper's per-core figures); a solve's
+    time is the measured iteration times the GPU solve's iteration count. A
+    whole oracle solve is measured on a 16 x 8^3 lattice beside it."""
+    op, t_setup = oracle_operator(wl, U)
+    V = int(np.prod(wl["dims"]))
+    cores = host_cores()
+    it = oracle_iteration(wl, op, b, cores, gram_schmidt_basis(wl, b))
+    t_solve, t_iter = solve_seconds(wl, it, iters, cycles)
+    out = dict(value=1.0 / t_solve, unit="solves/s", cores=it["threads"], kind="oracle", cpu_model=cpu_model(),
+               sample=(f"FP64 oracle on the full {'x'.join(map(str, wl['dims']))} lattice, {it['threads']} threads: "
+                       f"one apply_D ({it['apply_D_s']:.2f} s), one Schwarz sweep ({it['sweep_s']:.2f} s), the "
+                       f"oracle's modified Gram-Schmidt over {wl['restart'] // 2 + 1} vectors "
+                       f"({it['gram_schmidt_s']:.2f} s); one iteration {t_iter:.2f} s, a solve = {iters} iterations "
+                       f"+ {cycles + 1} true residuals; operator set-up {t_setup:.1f} s not counted"),
+               seconds_per_solve=t_solve, all_cores=it,
+               sap_gflops_all_cores=sap_flops_per_site(wl["mr_steps"]) * V / it["sweep_s"] / 1e9,
+               dslash_gbs_all_cores=DSLASH_REALS * 8 * V / it["apply_D_s"] / 1e9)
+    if single_thread:
+        one = oracle_iteration(wl, op, b, 1)
+        out["one_thread"] = one
+        out["sap_gflops_one_thread"] = sap_flops_per_site(wl["mr_steps"]) * V / one["sweep_s"] / 1e9
+        out["dslash_gbs_one_thread"] = DSLASH_REALS * 8 * V / one["apply_D_s"] / 1e9
+    del op
+    out["measured_small_solve"] = oracle_small_solve(wl)
+    return out
 
 
 # iteration / cycle counts of this workload's solve (FP32 smoother), used to
-# scale the oracle's bounded sample to one solve
+# scale the oracle's measured iteration to one solve in the reference arm
 REF_ITERS, REF_CYCLES = 62, 4
 
 
 def run_reference(args, rank):
+    """The oracle as the reference arm: one step = one FGMRES iteration of the
+    FP64 oracle on the full workload lattice (4 Schwarz sweeps, apply_D and
+    the Gram-Schmidt step of average length, all host cores), measured;
+    `value` is solves/s = 1 / (62 measured iterations + 5 true residuals),
+    the iteration count of the GPU solve of this workload."""
     if rank != 0:
         return
+    import oracle
     wl = synth.WORKLOADS[args.workload]
     U, b = setup_problem(wl)
     op, t_setup = oracle_operator(wl, U)
-    vals = []
+    basis = gram_schmidt_basis(wl, b)
+    cores = host_cores()
+    oracle.set_threads(cores)
+    steps = []
     for i in range(args.warmup + args.steps):
-        r = oracle_sample(wl, U, b, REF_ITERS, REF_CYCLES, op, t_setup)
+        t0 = time.perf_counter()
+        for _ in range(wl["sweeps"]):
+            op.sap(wl["block"], b, 1, wl["mr_steps"])
+        t1 = time.perf_counter()
+        op.apply(b)
+        t2 = time.perf_counter()
+        oracle.gram_schmidt(basis, b)
+        t3 = time.perf_counter()
         if i >= args.warmup:
-            vals.append(r)
-    v = float(np.median([r["value"] for r in vals]))
-    cb = dict(vals[-1])
-    cb["value"] = v
+            steps.append((t3 - t0, t2 - t1, (t1 - t0) / wl["sweeps"], t3 - t2))
+    t_step = float(np.mean([s_[0] for s_ in steps]))
+    t_apply = float(np.mean([s_[1] for s_ in steps]))
+    t_solve = REF_ITERS * t_step + (REF_CYCLES + 1) * t_apply
+    v = 1.0 / t_solve
+    cb = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+          "sample": (f"each step one FGMRES iteration of the FP64 oracle on the full "
+                     f"{'x'.join(map(str, wl['dims']))} lattice on {cores} threads ({wl['sweeps']} Schwarz sweeps, "
+                     f"apply_D, Gram-Schmidt over {wl['restart'] // 2 + 1} vectors), measured; value = "
+                     f"1 / ({REF_ITERS} steps + {REF_CYCLES + 1} true residuals)"),
+          "seconds_per_solve": t_solve, "sweep_s": float(np.mean([s_[2] for s_ in steps])),
+          "apply_D_s": t_apply, "gram_schmidt_s": float(np.mean([s_[3] for s_ in steps])),
+          "operator_setup_s": t_setup}
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": config_of(wl), "cpu_baseline": cb,
+           "config": config_of(wl, "f32", "df"),
+           "oracle_arithmetic": "IEEE FP64 throughout (the same workload and solver parameters)",
+           "step": "one FGMRES iteration of the oracle (value extrapolates 62 of them to a solve)",
+           "solves_per_s_extrapolated": v, "cpu_baseline": cb,
            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
-def config_of(wl):
+OUTER = {"f64": "IEEE FP64 Krylov basis, least squares and true residual",
+         "df": "double-float Krylov basis and true-residual Dslash (FP32 pairs, ~48-bit significands); "
+               "FP64 least squares, x and residual norms",
+         "f64_outer": "IEEE FP64 Krylov basis, least squares and true residual (outer_f64)"}
+
+
+def config_of(wl, smoother, outer):
+    """`smoother`: the storage precision the Schwarz smoother ran in;
+    `outer`: a key of OUTER (what the FGMRES orthogonalisation and true
+    residual computed in)."""
     return {"workload": WORKLOAD if wl is synth.WORKLOADS.get(WORKLOAD) else "custom",
             "dims_TZYX": list(wl["dims"]), "block_TZYX": list(wl["block"]), "sweeps": wl["sweeps"],
-            "mr_steps": wl["mr_steps"], "restart": wl["restart"], "tol": 1e-10, "smoother_storage": "f32",
-            "outer": "f64", "c_sw": wl["c_sw"], "m0": wl["m0"], "eps": wl["eps"], "n_stout": wl["n_stout"],
+            "mr_steps": wl["mr_steps"], "restart": wl["restart"], "tol": 1e-10, "smoother_storage": smoother,
+            "outer": OUTER[outer], "c_sw": wl["c_sw"], "m0": wl["m0"], "eps": wl["eps"], "n_stout": wl["n_stout"],
             "l2": "inputs larger than L2 (operator fields 1.8 GB, each vector 0.2-0.4 GB)"}
 
 
@@ -256,7 +367,10 @@ def run_ours(args, rank, world):
     op = dd.Op(gauge, wl["c_sw"], wl["m0"], prec)
     stream = torch.cuda.current_stream()
     L = dd.lib()
-    kw = dict(tol=1e-10, restart=wl["restart"], sweeps=wl["sweeps"], mr_steps=wl["mr_steps"], max_iter=2000)
+    kw = dict(tol=1e-10, restart=wl["restart"], sweeps=wl["sweeps"], mr_steps=wl["mr_steps"], max_iter=2000,
+              outer_f64=args.outer_f64)
+    outer = "f64" if prec == dd.F64 else ("f64_outer" if args.outer_f64 else "df")
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
 
     # kernel-level timing first (fresh device state): apply_D and one
     # Schwarz phase (launch); the first calls also run the autotuner
@@ -321,7 +435,7 @@ def run_ours(args, rank, world):
     dslash_gbs = dslash_bytes / (dslash_ms * 1e-3) / 1e9
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or peaks["sm_max_mhz"]
-    alu_peak = fp32_alu_peak_tflops(peaks["sm_max_mhz"])
+    alu_peak = fp32_alu_peak_tflops(peaks["sm_max_mhz"], sms)
     sap_flops_launch = sap_flops_per_site(wl["mr_steps"]) * V / 2
     sap_tflops = sap_flops_launch / (sap_launch_ms * 1e-3) / 1e12
     sap_bytes_launch = SAP_REALS_PER_SWEEP * real_b[prec] * V / 2
@@ -329,7 +443,7 @@ def run_ours(args, rank, world):
     roofline_sap = {"kernel": "k_sap_phase", "bound": "alu", "achieved": sap_tflops, "peak": alu_peak,
                     "unit": "TFLOP/s", "frac": sap_tflops / alu_peak,
                     "traffic": kernel_traffic("k_sap_phase"),
-                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz",
+                    "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz",
                     "algorithmic_bytes_per_launch": sap_bytes_launch,
                     "hbm_frac": sap_bytes_launch / (sap_launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                     "ms_per_launch": sap_launch_ms}
@@ -342,7 +456,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == dd.F32 else args.prec,
-        "data": "synthetic", "config": config_of(wl),
+        "data": "synthetic", "config": config_of(wl, args.prec, outer),
         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99))},
         "solve": {"iterations": int(infos[-1]["iterations"]), "cycles": int(infos[-1]["cycles"]),
                   "true_rel_residual": max(i["true_rel_residual"] for i in infos), **mean_info},
@@ -355,8 +469,10 @@ def run_ours(args, rank, world):
         "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_mixed:
+        out["mixed_96x48^3"] = mixed_kernels(dd, peaks, alu_peak, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = oracle_sample(wl, U, b, int(infos[-1]["iterations"]), int(infos[-1]["cycles"]))
+        out["cpu_baseline"] = oracle_baseline(wl, U, b, int(infos[-1]["iterations"]), int(infos[-1]["cycles"]))
     if rank == 0:
         print(json.dumps(out), flush=True)
     op.close()
@@ -364,6 +480,45 @@ def run_ours(args, rank, world):
     lat.close()
     if dist:
         dist.destroy_process_group()
+
+
+def mixed_kernels(dd, peaks, alu_peak, stream):
+    """apply_D and the Schwarz phase with FP16 and BF16 storage on the
+    mixed-precision workload's 96 x 48^3 lattice (exp(i 0.2 H), 3 stout steps,
+    c_sw 1.7, m0 0; 4^4 blocks, 4 MR steps): time, GB/s of algorithmic bytes
+    (apply_D 192 reals per site, a phase 252 reals per site of its colour)
+    and the phase's flop rate. Inputs far exceed L2 (one field 0.5 GB)."""
+    import torch
+    wl = synth.WORKLOADS["sap_fgmres_96x48^3_mixed"]
+    V = int(np.prod(wl["dims"]))
+    U = synth.gauge(wl["dims"], wl["eps"], wl["n_stout"], wl["rho"], wl["gauge_seed"])
+    lat = dd.Lattice(wl["dims"], wl["block"])
+    gauge = dd.Gauge(lat, U)
+    del U
+    b = synth.gaussian_spinor(V, wl["rhs_seed"])
+    res = {"workload": "sap_fgmres_96x48^3_mixed", "dims_TZYX": list(wl["dims"]), "block_TZYX": list(wl["block"]),
+           "mr_steps": wl["mr_steps"], "m0": wl["m0"]}
+    for name, prec in (("f16", dd.F16), ("bf16", dd.BF16)):
+        op = dd.Op(gauge, wl["c_sw"], wl["m0"], prec)
+        fin, fout = lat.to_field(b, prec), lat.new_field(prec)
+        for _ in range(5):
+            op.apply_D(prec, fin, fout)
+        ms_d = ev_time(lambda: op.apply_D(prec, fin, fout), 30, stream)
+        op.sap_smooth(fin, fout, wl["sweeps"], wl["mr_steps"])
+        ms_s = ev_time(lambda: op.sap_smooth(fin, fout, wl["sweeps"], wl["mr_steps"]), 3, stream) / (2 * wl["sweeps"])
+        gbs_d = DSLASH_REALS * 2 * V / (ms_d * 1e-3) / 1e9
+        gbs_s = SAP_REALS_PER_SWEEP * 2 * (V / 2) / (ms_s * 1e-3) / 1e9
+        tf_s = sap_flops_per_site(wl["mr_steps"]) * (V / 2) / (ms_s * 1e-3) / 1e12
+        res[name] = {"dslash": {"ms": ms_d, "GB/s": gbs_d, "frac_hbm": gbs_d / peaks["hbm_gbs"],
+                                "bytes_per_site": DSLASH_REALS * 2},
+                     "sap_phase": {"ms": ms_s, "TFLOP/s": tf_s, "frac_fp32_peak": tf_s / alu_peak, "GB/s": gbs_s,
+                                   "frac_hbm": gbs_s / peaks["hbm_gbs"]}}
+        del fin, fout
+        op.close()
+        torch.cuda.empty_cache()
+    gauge.close()
+    lat.close()
+    return res
 
 
 def run_kernels(args):
@@ -641,6 +796,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 96x48^3 FP16/BF16 kernel measurements")
+    ap.add_argument("--outer-f64", action="store_true",
+                    help="IEEE FP64 Krylov basis and true residual with a mixed-precision smoother")
     ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "batched", "serve", "mg"],
                     help="kernels: short kernel loop for profiler captures; batched: the 24-source "
                          "48^3x96 workload; serve: the Poisson request stream; mg: two-level "

@@ -203,6 +203,10 @@ typedef struct {
   int use_x0;           /* 1: x holds the initial guess; 0: start from x = 0         */
   dd_mg_t mg;           /* NULL: precondition with `sap`; else the two-level
                            preconditioner of dd_create_mg (same operator)          */
+  int outer_f64;        /* 1: with a mixed-precision op, keep the Krylov basis and
+                           the true residual's Dslash in IEEE FP64 too, instead of
+                           double-float (slower on GB300: its FP64 rate is a small
+                           fraction of FP32); not with `mg`. 0: the default        */
 } dd_solve_params;
 
 typedef struct {
@@ -219,8 +223,9 @@ typedef struct {
  * runs in the op's precision. With an FP64 op the orthogonalisation, the
  * least-squares update and the true residual are IEEE FP64; with a
  * mixed-precision op the Krylov basis and the true residual's Dslash use
- * double-float arithmetic (FP32 pairs, ~48-bit significands), the
- * least-squares update, x and the residual norms stay FP64. x receives the solutions
+ * double-float arithmetic (FP32 pairs, ~48-bit significands) unless
+ * p->outer_f64 asks for IEEE FP64, the least-squares update, x and the
+ * residual norms stay FP64. x receives the solutions
  * (and holds the initial guesses if p->use_x0). info (may be NULL) receives
  * nrhs records. Returns DD_OK when every right-hand side converged, else
  * DD_ENOTCONV (x holds the best iterates) or an error. Synchronous with
@@ -296,7 +301,14 @@ int dd_mg_precondition(dd_mg_t mg, const void *r_f32, void *x_f32, void *stream)
  * contents, and each call clears what it needs zeroed itself. The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress,
  * with that device current); make that first call before any stream capture
- * on the device. Synchronous with respect to the host; work runs on `stream`. */
+ * on the device, and do not call this entry point on a device after
+ * cudaDeviceReset in the same process (the address is kept). Nothing is
+ * tuned or captured inside the call: every kernel runs in the launch variant
+ * the autotuner already chose for this lattice and precision (e.g. by an
+ * earlier dd_solve of the same shape, or a DD_TUNE_CACHE file), else in its
+ * default variant, and the smoother's launches are enqueued one by one. The
+ * host side uses about 72 KB of the calling thread's stack. Synchronous with
+ * respect to the host; work runs on `stream`. */
 int dd_solve_noalloc(dd_op_t op, const dd_solve_params *p, const double *b_dev, double *x_dev,
                      dd_solve_info *info, void *stream);
 

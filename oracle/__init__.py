@@ -59,6 +59,8 @@ def _L():
             "or_sap": ([pi, i, pi, pd, pd, pd, pd, pd, i, i], i),
             "or_fgmres": ([pi, i, pi, pd, pd, pd, pd, pd, i, d, i, i, i, pd], i),
             "or_apply_D_sites": ([pi, i, pd, d, d, pd, P(l), l, pd], i),
+            "or_gram_schmidt": ([l, pd, i, pd, pd], i),
+            "or_set_threads": ([i], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -128,6 +130,24 @@ def apply_D_sites(dims, U, c_sw: float, m0: float, psi, sites, antiperiodic: boo
     if rc:
         raise ValueError("or_apply_D_sites")
     return out
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads for the oracle's parallel loops (n <= 0: unchanged);
+    returns the number in effect."""
+    return int(_L().or_set_threads(int(n)))
+
+
+def gram_schmidt(V, w):
+    """One modified Gram-Schmidt step as FGMRES takes it: w (complex, n) is
+    projected against the rows of V (k x n) in order. Returns (w', h)."""
+    V = _c128(V)
+    w = _c128(w).reshape(-1).copy()
+    k = V.shape[0] if V.ndim == 2 else 0
+    h = np.zeros(max(k, 1), dtype=np.complex128)
+    if _L().or_gram_schmidt(w.size, _dp(V), k, _dp(w), _dp(h)):
+        raise ValueError("or_gram_schmidt")
+    return w, h[:k]
 
 
 class Operator:

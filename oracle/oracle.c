@@ -620,6 +620,34 @@ static cd vdot(long n, const cd *a, const cd *b) {
 }
 static double vnorm(long n, const cd *a) { return sqrt(creal(vdot(n, a, a))); }
 
+/* Modified Gram-Schmidt step of the Arnoldi process: w is projected against
+ * the basis vectors v_0 .. v_{k-1} (V holds them back to back, n complex
+ * each) in order, h_i = <v_i, w> taken after the previous projections. */
+static void mgs_project(long n, const cd *V, int k, cd *w, cd *h) {
+  for (int i = 0; i < k; i++) {
+    const cd *v = V + (long)i * n;
+    h[i] = vdot(n, v, w);
+    for (long l = 0; l < n; l++) w[l] -= h[i] * v[l];
+  }
+}
+
+/* The same step on caller arrays (for timing and tests): w and h (k complex)
+ * are overwritten. */
+int or_gram_schmidt(long n, const double *V, int k, double *w, double *h) {
+  if (n < 1 || k < 0 || !V || !w || (k > 0 && !h)) return -1;
+  mgs_project(n, (const cd *)V, k, (cd *)w, (cd *)h);
+  return 0;
+}
+
+/* OpenMP threads used by the parallel loops from now on (n >= 1; n <= 0
+ * leaves the setting unchanged). Returns the number in effect. */
+int omp_get_max_threads(void);
+void omp_set_num_threads(int);
+int or_set_threads(int n) {
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+}
+
 /* FGMRES(m) right-preconditioned by SAP (nsweep sweeps, nmr MR steps, x0 = 0 per
  * application). x holds the initial guess on entry and the solution on exit.
  * stats[0] = preconditioner applications, stats[1] = restart cycles,
@@ -669,11 +697,9 @@ int or_fgmres(const int dims[4], int antiperiodic, const int bdims[4], const dou
       if (sap_run(&B, U, A, Ainv, v, z, nsweep, nmr)) { rc = -2; goto done; }
       its++;
       or_apply_D(dd, antiperiodic, U, A, (const double *)z, (double *)w);
-      for (int i = 0; i <= j; i++) {
-        cd h = vdot(n, Vb + (long)i * n, w);
-        H[i * m + j] = h;
-        for (long l = 0; l < n; l++) w[l] -= h * Vb[(long)i * n + l];
-      }
+      cd hcol[j + 1];
+      mgs_project(n, Vb, j + 1, w, hcol);
+      for (int i = 0; i <= j; i++) H[i * m + j] = hcol[i];
       double hn = vnorm(n, w);
       H[(j + 1) * m + j] = hn;
       if (hn > 0)

@@ -42,7 +42,7 @@ class SapParams(ctypes.Structure):
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("sap", SapParams), ("inner_reduction", ctypes.c_double), ("where", ctypes.c_int),
-                ("use_x0", ctypes.c_int), ("mg", ctypes.c_void_p)]
+                ("use_x0", ctypes.c_int), ("mg", ctypes.c_void_p), ("outer_f64", ctypes.c_int)]
 
 
 class MgParams(ctypes.Structure):
@@ -280,9 +280,12 @@ class Op(Handle):
                "dd_sap_smooth")
 
     def solve(self, b, x=None, tol=1e-10, restart=16, max_iter=1000, sweeps=4, mr_steps=4,
-              inner_reduction=None, use_x0=False, stream=None, raise_on_notconv=True, mg=None):
+              inner_reduction=None, use_x0=False, stream=None, raise_on_notconv=True, mg=None,
+              outer_f64=False):
         """Solve D x = b. b: numpy (host) or torch (device) canonical spinors
-        (nrhs, V, 4, 3) complex128 or their float64 view. Returns (x, infos)."""
+        (nrhs, V, 4, 3) complex128 or their float64 view. Returns (x, infos).
+        outer_f64: IEEE FP64 Krylov basis and true residual also for a
+        mixed-precision operator (default: double-float)."""
         if inner_reduction is None:
             inner_reduction = 0.0 if self.prec == F64 else 1e-5
         on_dev = not isinstance(b, np.ndarray)
@@ -295,7 +298,8 @@ class Op(Handle):
             if _count_rhs(x, self.lat.V) != nrhs:
                 raise ValueError("x and b hold different numbers of right-hand sides")
         p = SolveParams(tol, restart, max_iter, SapParams(sweeps, mr_steps, 1, 0), inner_reduction,
-                        DEVICE if on_dev else HOST, int(bool(use_x0)), mg.handle if mg is not None else None)
+                        DEVICE if on_dev else HOST, int(bool(use_x0)), mg.handle if mg is not None else None,
+                        int(bool(outer_f64)))
         infos = (SolveInfo * nrhs)()
         rc = lib().dd_solve(self._h, ctypes.byref(p), _ptr(b), _ptr(x), nrhs, infos, _stream_ptr(stream))
         if rc != 0 and not (rc == -4 and not raise_on_notconv):

@@ -22,7 +22,17 @@
 //    writes every other buffer before reading it;
 //  * the first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress (with that device current); make that first call
-//    before any stream capture on the device.
+//    before any stream capture on the device. The address is kept for the
+//    life of the process, so do not use this entry point on a device after
+//    cudaDeviceReset in the same process;
+//  * no launch-configuration tuning and no CUDA-graph capture happen inside
+//    the call: each kernel runs in the variant the tuner has already chosen
+//    for this lattice and precision (by an earlier dd_solve, dd_apply_D or
+//    dd_sap_smooth in this process, or a DD_TUNE_CACHE file), or else in
+//    its default variant, and the smoother's launches are enqueued one by
+//    one on the caller's stream;
+//  * the host side keeps its small arrays (the Hessenberg matrix of up to 64
+//    columns and the rotations, about 72 KB) on the calling thread's stack.
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -30,6 +40,7 @@
 #include <mutex>
 
 #include "dd_solver.cuh"
+#include "dd_tune.cuh"
 
 namespace dd {
 namespace {
@@ -116,10 +127,12 @@ extern "C" int dd_solve_noalloc(dd_op_t opp, const dd_solve_params *p, const dou
   }
   void *base = nullptr;
   if ((rc = scratch_address(&base))) return rc;
+  // no tuning trial launches and no graph capture below (see the header)
+  DirectLaunch direct;
 
   // carve the workspace
   const int zprec = op->prec == DD_F64 ? DD_F64 : DD_F32;
-  const bool df = zprec == DD_F32;
+  const bool df = zprec == DD_F32 && !p->outer_f64;
   const size_t n = (size_t)g.V * 12, f64 = (size_t)g.V * 24 * 8;
   const size_t fz = (size_t)g.V * 24 * real_bytes(zprec), fp = (size_t)g.V * 24 * real_bytes(op->prec);
   const size_t fz_al = (fz + 255) / 256 * 256, f64_al = (f64 + 255) / 256 * 256;
@@ -218,7 +231,10 @@ extern "C" int dd_solve_noalloc(dd_op_t opp, const dd_solve_params *p, const dou
         if ((rc = launch_convert_field(g, op->prec, tout, zprec, zj, 1, 1.0, st))) return rc;
       }
       if ((rc = launch_dirac(g, fz_ops, zj, zprec == DD_F64 ? (void *)w : zt, 1, st))) return rc;
-      if (zprec != DD_F64 && (rc = bl.field_to_df(g, DD_F32, zt, (float *)w, st))) return rc;
+      if (zprec != DD_F64) {
+        rc = df ? bl.field_to_df(g, DD_F32, zt, (float *)w, st) : launch_convert_field(g, DD_F32, zt, DD_F64, w, 1, 1.0, st);
+        if (rc) return rc;
+      }
       const int kk = j + 1;
       auto mdot = [&](double *wn2) {
         return df ? bl.df_mdot((const float *)Vb, vstride, kk, (const float *)w, n, hd, wn2, st)

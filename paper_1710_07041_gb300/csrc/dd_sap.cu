@@ -106,7 +106,8 @@ __global__ void k_wait_selftest(const uint4 *src, int expire, int *result, unsig
 // into a CUDA graph per (operator, parameters, variant, field pointers) and
 // replayed afterwards: one launch per application instead of 2 x sweeps.
 // When the caller's stream is itself being captured the launches go into the
-// caller's graph directly. DD_SAP_GRAPHS=0 disables the graphs.
+// caller's graph directly. DD_SAP_GRAPHS=0 disables the graphs, and so does
+// a DirectLaunch scope on the calling thread (dd_solve_noalloc).
 struct GraphCache {
   std::mutex mu;
   std::map<std::string, cudaGraphExec_t> execs;
@@ -118,7 +119,7 @@ int sap_launch_as_graph(const std::string &key, int variant, int nkernels, const
   const char *env = getenv("DD_SAP_GRAPHS");
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cap);
-  if ((env && env[0] == '0') || cap != cudaStreamCaptureStatusNone || st == 0) return enqueue();
+  if ((env && env[0] == '0') || cap != cudaStreamCaptureStatusNone || st == 0 || direct_launch()) return enqueue();
   std::string k = key + "|v" + std::to_string(variant) + "|" + std::to_string((uintptr_t)f.links);
   for (int i = 0; i < rp.n; i++)
     k += "|" + std::to_string((uintptr_t)rp.in[i]) + ":" + std::to_string((uintptr_t)rp.out[i]);

@@ -83,7 +83,8 @@ struct Server {
 
 static bool same_params(const dd_solve_params &a, const dd_solve_params &b) {
   return a.tol == b.tol && a.restart == b.restart && a.max_iter == b.max_iter && a.sap.sweeps == b.sap.sweeps &&
-         a.sap.mr_steps == b.sap.mr_steps && a.inner_reduction == b.inner_reduction && a.mg == b.mg;
+         a.sap.mr_steps == b.sap.mr_steps && a.inner_reduction == b.inner_reduction && a.mg == b.mg &&
+         a.outer_f64 == b.outer_f64;
 }
 
 // Called with srv->mu held: a right-hand side of r finished with `status`.

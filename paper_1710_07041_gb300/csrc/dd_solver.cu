@@ -42,9 +42,10 @@ float ev_ms(cudaEvent_t a, cudaEvent_t b) {
 
 int check_solve_params(const dd_solve_params *p) {
   if (!p || !(p->tol > 0) || p->restart < 1 || p->restart > 64 || p->max_iter < 1 || p->sap.sweeps < 1 ||
-      p->sap.mr_steps < 0 || !(p->inner_reduction >= 0) || p->inner_reduction >= 1) {
+      p->sap.mr_steps < 0 || !(p->inner_reduction >= 0) || p->inner_reduction >= 1 || p->outer_f64 < 0 ||
+      p->outer_f64 > 1 || (p->outer_f64 && p->mg)) {
     set_error("dd_solve: bad parameters (tol > 0, 1 <= restart <= 64, max_iter >= 1, sweeps >= 1, "
-              "0 <= inner_reduction < 1)");
+              "0 <= inner_reduction < 1, outer_f64 0 or 1 and not with mg)");
     return DD_EINVAL;
   }
   return DD_OK;
@@ -63,7 +64,7 @@ BatchSolver::BatchSolver(const Op *op, const dd_solve_params &p, int slots, cuda
   zprec_ = op->prec == DD_F64 ? DD_F64 : DD_F32;
   // mixed precision keeps the Krylov basis in double-float (FP32 hi/lo pairs):
   // FP64-class accuracy at FP32 ALU rate; an FP64 operator keeps native FP64
-  df_ = zprec_ == DD_F32;
+  df_ = zprec_ == DD_F32 && !p.outer_f64;
   f64_ = (size_t)g.V * 24 * 8;
   fz_ = (size_t)g.V * 24 * real_bytes(zprec_);
   fp_ = (size_t)g.V * 24 * real_bytes(op->prec);
@@ -394,6 +395,10 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
   // w = D z_j in zprec (a double-float solve keeps it in the FP32 field zt;
   // the first Gram-Schmidt pass reads it there and writes the DF w)
   if ((rc = launch_dirac(g, zprec_ == DD_F64 ? op_->f64 : op_->f32, d_ptrs, st_))) return rc;
+  // an IEEE FP64 basis with FP32 preconditioned vectors (outer_f64): w = D z_j as FP64
+  if (!df_ && zprec_ != DD_F64)
+    for (Slot *s : A)
+      if ((rc = launch_convert_field(g, zprec_, s->zt, DD_F64, s->w, 1, 1.0, st_))) return rc;
   cudaEventRecord(ev_[2], st_);
   // classical Gram-Schmidt, repeated once for slots whose norm drops below 1e-3 of its value (REORTH2)
   for (Slot *s : A) {

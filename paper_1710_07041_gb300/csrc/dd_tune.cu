@@ -89,6 +89,13 @@ std::string tune_key(const char *kind, const Geom &g, int prec, int nrhs) {
   return buf;
 }
 
+namespace {
+thread_local bool t_direct = false;
+}
+bool direct_launch() { return t_direct; }
+DirectLaunch::DirectLaunch() : prev(t_direct) { t_direct = true; }
+DirectLaunch::~DirectLaunch() { t_direct = prev; }
+
 int tuned_variant(const std::string &key, int nvariants, const std::function<int(int)> &run, cudaStream_t st,
                   int *chosen) {
   const char *force = getenv("DD_TUNE_VARIANT");
@@ -105,6 +112,10 @@ int tuned_variant(const std::string &key, int nvariants, const std::function<int
       *chosen = it->second < nvariants ? it->second : 0;
       return DD_OK;
     }
+  }
+  if (t_direct) {   // no trial launches: the default variant, not cached
+    *chosen = 0;
+    return DD_OK;
   }
   const char *off = getenv("DD_TUNE");
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;

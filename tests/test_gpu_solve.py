@@ -94,3 +94,22 @@ def test_workspace_cache_reuse_and_release():
     # scratch - at least the basis, 17 x 24 x 8 bytes per site
     assert free1 - free0 >= 17 * 24 * 8 * s.V
     s.close()
+
+
+@pytest.mark.parametrize("prec", [dd.F32, dd.F16])
+def test_outer_f64_solve_reaches_1e10(prec):
+    """The mixed-precision smoother with an IEEE FP64 Krylov basis and FP64
+    true residual (outer_f64) converges like the double-float default: same
+    target, iteration count within one or two steps."""
+    s = Setup((8, 8, 8, 8), (4, 4, 4, 4), eps=0.25, n_stout=2, c_sw=1.7, m0=-0.02, prec=prec, seed=21)
+    b = synth.gaussian_spinor(s.V, 22)
+    x, info = s.op.solve(b, tol=1e-10, outer_f64=True)
+    assert info[0]["status"] == 0, info
+    assert true_res(s, x, b) <= 1e-10
+    _, info_df = s.op.solve(b, tol=1e-10)
+    assert abs(info[0]["iterations"] - info_df[0]["iterations"]) <= 2
+    with pytest.raises(dd.DDError):   # not with the two-level preconditioner (its argument check)
+        p = dd.SolveParams(1e-10, 16, 100, dd.SapParams(4, 4, 1, 0), 1e-5, dd.HOST, 0, 1, 1)
+        dd._check(dd.lib().dd_solve(s.op.handle, dd.ctypes.byref(p), dd._ptr(b), dd._ptr(np.zeros_like(b)), 1,
+                                    None, None), "dd_solve")
+    s.close()

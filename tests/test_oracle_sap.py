@@ -181,3 +181,19 @@ def test_fgmres_max_iter_and_zero_rhs(op):
     assert not ok and st["iterations"] == 2 and 0 < st["rel_residual"] < 1
     x, ok, st = op.fgmres(BD, np.zeros_like(b), 16, 1e-10, 10, 4, 3)
     assert ok and not x.any()
+
+
+def test_gram_schmidt_step_is_orthogonal_projection():
+    """The oracle's Arnoldi projection step (the one or_fgmres uses): against
+    an orthonormal basis Q it returns h = Q^dagger w and w - Q h, which is
+    orthogonal to every basis vector (closed form of the projection)."""
+    rng = np.random.default_rng(5)
+    n, k = 120, 6
+    Q, _ = np.linalg.qr(rng.normal(size=(n, k)) + 1j * rng.normal(size=(n, k)))
+    w = rng.normal(size=n) + 1j * rng.normal(size=n)
+    w2, h = oracle.gram_schmidt(Q.T.copy(), w)
+    assert np.allclose(h, Q.conj().T @ w, rtol=0, atol=1e-13)
+    assert np.allclose(w2, w - Q @ (Q.conj().T @ w), rtol=0, atol=1e-13)
+    assert np.abs(Q.conj().T @ w2).max() < 1e-13
+    w0, h0 = oracle.gram_schmidt(np.zeros((0, n), dtype=complex), w)
+    assert h0.size == 0 and np.array_equal(w0, w)

@@ -4,9 +4,12 @@ Properties fixed by the construction, none re-typing the oracle's code:
 orthonormal interpolation, restriction = prolongation^dagger, the test
 vectors lie in range(P), gamma5-hermiticity of the Galerkin coarse operator
 (chirality-split aggregates), the Galerkin projection property of an exact
-coarse correction, gauge invariance of D_c under covariant test vectors, and
-convergence of the two-level FGMRES to a dense LU solution in fewer steps
-than the Schwarz preconditioner alone.
+coarse correction, gauge invariance of D_c under covariant test vectors, the coarse GMRES
+against a dense solve of D_c (with and without restarts) and, step by step,
+against the minimum residual over the Krylov space found by brute force
+(which also fixes its stopping rule), and convergence of the two-level
+FGMRES to a dense LU solution in fewer steps than the Schwarz
+preconditioner alone.
 """
 import numpy as np
 import pytest
@@ -83,6 +86,67 @@ def test_coarse_operator_gauge_invariant(op):
     M = _coarse_dense(TwoLevel(op, CB, tv))
     Mp = _coarse_dense(TwoLevel(opp, CB, tvp))
     assert np.allclose(M, Mp, atol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def coarse(op):
+    tl = TwoLevel(op, CB, _tv(4, 700))
+    M = _coarse_dense(tl)
+    rhs = synth.gaussian(tl.nagg * 2 * tl.N, 701).reshape(tl.nagg, 2, tl.N)
+    return tl, M, rhs
+
+
+@pytest.mark.parametrize("restart", [200, 7])
+def test_coarse_gmres_matches_dense_solve(coarse, restart):
+    """Run to 1e-12: one cycle (restart >= dimension) and many short cycles
+    (restart 7), so the restart bookkeeping (x accumulated across cycles,
+    residual recomputed from D_c) is exercised."""
+    tl, M, rhs = coarse
+    x = tl.coarse_gmres(rhs, restart=restart, max_iter=2000, tol=1e-12).reshape(-1)
+    b = rhs.reshape(-1)
+    assert np.linalg.norm(b - M @ x) <= 1e-12 * np.linalg.norm(b) * 1.01
+    xs = np.linalg.solve(M, b)
+    assert np.linalg.norm(x - xs) <= np.linalg.cond(M) * 1e-12 * np.linalg.norm(xs)
+
+
+def _krylov_min_residuals(M, b, kmax):
+    """min over x in span{b, Mb, ..., M^(k-1) b} of |b - M x|, k = 1..kmax,
+    by least squares on the explicit (column-normalised) Krylov matrix."""
+    K = [b / np.linalg.norm(b)]
+    res = []
+    for k in range(1, kmax + 1):
+        Kk = np.column_stack(K)
+        y, *_ = np.linalg.lstsq(M @ Kk, b, rcond=None)
+        res.append(np.linalg.norm(b - M @ (Kk @ y)))
+        nxt = M @ K[-1]
+        K.append(nxt / np.linalg.norm(nxt))
+    return np.array(res)
+
+
+def test_coarse_gmres_steps_are_krylov_minimisers(coarse):
+    """After k steps from zero (no restart) the iterate minimises the
+    residual over the k-dimensional Krylov space; one step is the closed form
+    x = alpha b, alpha = <M b, b> / <M b, M b>."""
+    tl, M, rhs = coarse
+    b = rhs.reshape(-1)
+    x1 = tl.coarse_gmres(rhs, restart=50, max_iter=1, tol=1e-14).reshape(-1)
+    Mb = M @ b
+    assert np.allclose(x1, np.vdot(Mb, b) / np.vdot(Mb, Mb).real * b, rtol=1e-12, atol=0)
+    rmin = _krylov_min_residuals(M, b, 6)
+    for k in range(1, 7):
+        xk = tl.coarse_gmres(rhs, restart=50, max_iter=k, tol=1e-14).reshape(-1)
+        assert np.isclose(np.linalg.norm(b - M @ xk), rmin[k - 1], rtol=1e-8), k
+
+
+def test_coarse_gmres_stops_at_first_step_below_tol(coarse):
+    """With a loose tolerance the solve stops at the first step whose
+    minimal residual reaches tol |b|, neither earlier nor later."""
+    tl, M, rhs = coarse
+    b = rhs.reshape(-1)
+    rmin = _krylov_min_residuals(M, b, 12)
+    tol = 0.5 * (rmin[4] + rmin[5]) / np.linalg.norm(b)   # between steps 5 and 6
+    x = tl.coarse_gmres(rhs, restart=50, max_iter=100, tol=tol).reshape(-1)
+    assert np.isclose(np.linalg.norm(b - M @ x), rmin[5], rtol=1e-8)
 
 
 def _smoothed_tv(op, block, n, nset, seed):
