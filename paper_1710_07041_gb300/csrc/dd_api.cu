@@ -58,6 +58,7 @@ const OpFields *fields_for(const Op *op, int prec) {
 }
 
 static void free_fields(OpFields &f) {
+  if (f.links_full != f.links) cudaFree(f.links_full);
   cudaFree(f.links);
   cudaFree(f.clov);
   cudaFree(f.cinv);
@@ -205,12 +206,15 @@ int dd_create_gauge(dd_lattice_t lat, const double *links, dd_gauge_t *out) {
 static int alloc_fields(const Geom &g, int prec, OpFields &f) {
   f.prec = prec;
   size_t pb = pair_bytes(prec);
-  if (cudaMalloc(&f.links, (size_t)g.V * 36 * pb) != cudaSuccess || cudaMalloc(&f.clov, (size_t)g.V * 36 * pb) != cudaSuccess ||
+  if (cudaMalloc(&f.links, (size_t)g.V * 4 * link_pairs_of(prec) * pb) != cudaSuccess ||
+      (link_pairs_of(prec) != 9 && cudaMalloc(&f.links_full, (size_t)g.V * 36 * pb) != cudaSuccess) ||
+      cudaMalloc(&f.clov, (size_t)g.V * 36 * pb) != cudaSuccess ||
       cudaMalloc(&f.cinv, (size_t)g.V / 2 * 36 * pb) != cudaSuccess) {
     free_fields(f);
     set_error("dd_create_op: out of device memory");
     return DD_ENOMEM;
   }
+  if (link_pairs_of(prec) == 9) f.links_full = f.links;
   return DD_OK;
 }
 
@@ -238,13 +242,15 @@ static int create_op(Gauge *ga, double c_sw, double m0, int prec, Fill fill, dd_
   cudaStream_t st = 0;
   if (rc == DD_OK) rc = cuda_fail(cudaMemsetAsync(bad, 0, sizeof(int), st), "memset");
   if (rc == DD_OK) rc = fill(g, (double *)op->f64.clov, (double *)op->f64.cinv, bad, st);
-  if (rc == DD_OK) rc = launch_pack_links(g, DD_F64, ga->links_canon, op->f64.links, st);
-  if (rc == DD_OK) rc = launch_pack_links(g, DD_F32, ga->links_canon, op->f32.links, st);
+  if (rc == DD_OK) rc = launch_pack_links(g, DD_F64, ga->links_canon, op->f64.links, bad, st);
+  if (rc == DD_OK) rc = launch_pack_links(g, DD_F32, ga->links_canon, op->f32.links, bad, st);
+  if (rc == DD_OK) rc = launch_pack_links_full(g, DD_F32, ga->links_canon, op->f32.links_full, st);
   if (rc == DD_OK) rc = launch_convert_pairs(DD_F32, (const double *)op->f64.clov, op->f32.clov, (size_t)g.V * 36, st);
   if (rc == DD_OK)
     rc = launch_convert_pairs(DD_F32, (const double *)op->f64.cinv, op->f32.cinv, (size_t)g.V / 2 * 36, st);
   if (rc == DD_OK && (prec == DD_F16 || prec == DD_BF16)) {
-    rc = launch_pack_links(g, prec, ga->links_canon, op->fp.links, st);
+    rc = launch_pack_links(g, prec, ga->links_canon, op->fp.links, bad, st);
+    if (rc == DD_OK) rc = launch_pack_links_full(g, prec, ga->links_canon, op->fp.links_full, st);
     if (rc == DD_OK) rc = launch_convert_pairs(prec, (const double *)op->f64.clov, op->fp.clov, (size_t)g.V * 36, st);
     if (rc == DD_OK)
       rc = launch_convert_pairs(prec, (const double *)op->f64.cinv, op->fp.cinv, (size_t)g.V / 2 * 36, st);
@@ -265,8 +271,12 @@ static int create_op(Gauge *ga, double c_sw, double m0, int prec, Fill fill, dd_
   int hbad = 0;
   if (rc == DD_OK) rc = cuda_fail(cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost), "dd_create_op");
   cudaFree(bad);
-  if (rc == DD_OK && hbad) {
+  if (rc == DD_OK && (hbad & 1)) {
     set_error("dd_create_op: an even-site clover block A = 4 + m0 + C is singular");
+    rc = DD_EINVAL;
+  } else if (rc == DD_OK && (hbad & 2)) {
+    set_error("dd_create_op: a link is not special unitary (row 2 differs from conj(row0 x row1) by more than "
+              "1e-6); the 32- and 16-bit operator fields store two rows per link");
     rc = DD_EINVAL;
   }
   if (rc != DD_OK) {
@@ -434,7 +444,19 @@ int dd_sap_smooth(dd_op_t opp, const dd_sap_params *p, const void *b, void *x, i
     set_error("dd_sap_smooth: bad argument");
     return DD_EINVAL;
   }
-  return launch_sap(op->lat->g, op->fp, *p, b, x, nrhs, (cudaStream_t)stream);
+  // work fields of the incremental colour residual, stream-ordered (without
+  // them, e.g. when this allocation fails, every phase forms b - D x)
+  cudaStream_t st = (cudaStream_t)stream;
+  const Geom &g = op->lat->g;
+  const size_t fb = (size_t)g.V * 24 * real_bytes(op->fp.prec);
+  void *aux = nullptr;
+  if (cudaMallocAsync(&aux, 2 * (size_t)nrhs * fb, st) != cudaSuccess) {
+    cudaGetLastError();
+    aux = nullptr;
+  }
+  int rc = launch_sap(g, op->fp, *p, b, x, nrhs, st, aux);
+  if (aux) cudaFreeAsync(aux, st);
+  return rc;
 }
 
 }  // extern "C"

@@ -78,17 +78,32 @@ __global__ void k_convert_field(Geom g, const void *in, void *out, int nrhs, dou
   store_spinor<SO, CO>((char *)out + r * bytes_out, g, b, s, w);
 }
 
-// canonical FP64 links [V][4][9] (double2) -> tile [b][36][Vb] pairs
-template <typename P>
-__global__ void k_pack_links(Geom g, const double2 *__restrict__ canon, P *out) {
+// canonical FP64 links [V][4][9] (double2) -> tile [b][4 x LP][Vb] pairs,
+// LP = 9 (all entries) or 6 (rows 0 and 1; row 2 is rebuilt on load, so the
+// link must be special unitary: a deviation of row 2 from conj(row0 x row1)
+// above 1e-6 sets bit 2 of *bad)
+template <typename P, int LP = link_pairs_of_pair<P>()>
+__global__ void k_pack_links(Geom g, const double2 *__restrict__ canon, P *out, int *bad) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= g.V) return;
   int b = (int)(t / g.Vb), s = (int)(t - (long long)b * g.Vb);
   long long n = canonical_index(g, b, s);
-#pragma unroll 4
-  for (int i = 0; i < 36; i++) {
-    double2 d = canon[n * 36 + i];
-    out[((size_t)b * 36 + i) * g.Vb + s] = to_pair<P, double>(d.x, d.y);
+  for (int mu = 0; mu < 4; mu++) {
+    const double2 *u = canon + n * 36 + 9 * mu;
+#pragma unroll
+    for (int i = 0; i < LP; i++) out[((size_t)b * 4 * LP + LP * mu + i) * g.Vb + s] = to_pair<P, double>(u[i].x, u[i].y);
+    if constexpr (LP == 6) {
+      double dev = 0;
+      for (int k = 0; k < 3; k++) {
+        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        // conj(a_k1 b_k2 - a_k2 b_k1), a = row 0, b = row 1
+        const double2 a1 = u[k1], a2 = u[k2], b1 = u[3 + k1], b2 = u[3 + k2];
+        const double re = (a1.x * b2.x - a1.y * b2.y) - (a2.x * b1.x - a2.y * b1.y);
+        const double im = -((a1.x * b2.y + a1.y * b2.x) - (a2.x * b1.y + a2.y * b1.x));
+        dev = fmax(dev, fabs(re - u[6 + k].x) + fabs(im - u[6 + k].y));
+      }
+      if (!(dev <= 1e-6) && bad) atomicOr(bad, 2);
+    }
   }
 }
 
@@ -261,7 +276,7 @@ __global__ void k_build_clover(Geom g, const double2 *__restrict__ U, double c_s
     if (st.p == 0) {
       cpx<double> A[36], Ai[36];
       for (int i = 0; i < 36; i++) A[i] = M[i];
-      if (!inv6(A, Ai)) atomicExch(bad, 1);
+      if (!inv6(A, Ai)) atomicOr(bad, 1);
       pack_herm(Ai, cinv + ((size_t)b * 36 + 18 * h) * g.Vh + s, g.Vh);
     }
   }
@@ -294,7 +309,7 @@ __global__ void k_load_clover(Geom g, const double2 *__restrict__ A_canon, doubl
           A[6 * j + i] = {A[6 * i + j].re, -A[6 * i + j].im};
         }
       }
-      if (!inv6(A, Ai)) atomicExch(bad, 1);
+      if (!inv6(A, Ai)) atomicOr(bad, 1);
       pack_herm(Ai, cinv + ((size_t)b * 36 + 18 * h) * g.Vh + s, g.Vh);
     }
   }
@@ -366,13 +381,29 @@ int launch_convert_field(const Geom &g, int pi, const void *in, int po, void *ou
   return DD_EINVAL;
 }
 
-int launch_pack_links(const Geom &g, int prec, const double *canon, void *out, cudaStream_t st) {
+int launch_pack_links(const Geom &g, int prec, const double *canon, void *out, int *bad, cudaStream_t st) {
   const double2 *c = (const double2 *)canon;
   switch (prec) {
-    case DD_F64: k_pack_links<double2><<<grid_for(g.V), TPB, 0, st>>>(g, c, (double2 *)out); break;
-    case DD_F32: k_pack_links<float2><<<grid_for(g.V), TPB, 0, st>>>(g, c, (float2 *)out); break;
-    case DD_F16: k_pack_links<__half2><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__half2 *)out); break;
-    case DD_BF16: k_pack_links<__nv_bfloat162><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__nv_bfloat162 *)out); break;
+    case DD_F64: k_pack_links<double2><<<grid_for(g.V), TPB, 0, st>>>(g, c, (double2 *)out, bad); break;
+    case DD_F32: k_pack_links<float2><<<grid_for(g.V), TPB, 0, st>>>(g, c, (float2 *)out, bad); break;
+    case DD_F16: k_pack_links<__half2><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__half2 *)out, bad); break;
+    case DD_BF16:
+      k_pack_links<__nv_bfloat162><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__nv_bfloat162 *)out, bad);
+      break;
+    default: set_error("bad precision %d", prec); return DD_EINVAL;
+  }
+  return launched("k_pack_links");
+}
+
+int launch_pack_links_full(const Geom &g, int prec, const double *canon, void *out, cudaStream_t st) {
+  const double2 *c = (const double2 *)canon;
+  switch (prec) {
+    case DD_F64: k_pack_links<double2, 9><<<grid_for(g.V), TPB, 0, st>>>(g, c, (double2 *)out, nullptr); break;
+    case DD_F32: k_pack_links<float2, 9><<<grid_for(g.V), TPB, 0, st>>>(g, c, (float2 *)out, nullptr); break;
+    case DD_F16: k_pack_links<__half2, 9><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__half2 *)out, nullptr); break;
+    case DD_BF16:
+      k_pack_links<__nv_bfloat162, 9><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__nv_bfloat162 *)out, nullptr);
+      break;
     default: set_error("bad precision %d", prec); return DD_EINVAL;
   }
   return launched("k_pack_links");

@@ -8,8 +8,10 @@
 // A spinor field of precision P is [block][chunk][Vb] with 16-byte chunks
 // (F64: 2 reals, F32: 4 reals, F16/BF16: 8 reals), so a warp reading one chunk
 // of 32 consecutive sites issues one fully coalesced 512-byte request.
-// Links and clover site blocks are [block][36 pairs][Vb] with "pairs" of two
-// reals (double2 / float2 / half2): 4 links x 18 reals = 72 reals per site,
+// Links are [block][4 x link_pairs][Vb] with "pairs" of two reals (double2 /
+// float2 / half2): in FP64 4 links x 18 reals = 72 reals per site, in 32- and
+// 16-bit storage the first two rows only, 48 reals (see link_pairs). Clover
+// site blocks are [block][36 pairs][Vb]:
 // clover 2 chirality blocks x 36 reals (6 real diagonal + 15 complex upper
 // entries, row-major) = 72 reals per site. The even-site inverse clover is
 // [block][36 pairs][Vb/2].
@@ -22,6 +24,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <type_traits>
 
 #include "../../include/dd.h"
 
@@ -286,6 +289,19 @@ template <> struct Store<dfs> {
   using comp_t = dfl;
 };
 
+// Links in 32- and 16-bit storage keep the first two rows of each SU(3)
+// matrix (6 complex = 12 reals); the third row is rebuilt on load as
+// conj(row0 x row1), which holds for every special unitary matrix (the
+// operator constructors check the gauge field for it). FP64 fields and their
+// double-float split keep all nine entries. Pairs per link:
+template <typename S> __host__ __device__ constexpr int link_pairs() {
+  return (Store<S>::prec == DD_F64 || Store<S>::prec == DD_PREC_DF) ? 9 : 6;
+}
+template <typename P> __host__ __device__ constexpr int link_pairs_of_pair() {
+  return (std::is_same<P, double2>::value || std::is_same<P, float4>::value) ? 9 : 6;
+}
+inline int link_pairs_of(int prec) { return (prec == DD_F64 || prec == DD_PREC_DF) ? 9 : 6; }
+
 inline size_t real_bytes(int prec) { return (prec == DD_F64 || prec == DD_PREC_DF) ? 8 : prec == DD_F32 ? 4 : 2; }
 inline size_t pair_bytes(int prec) { return 2 * real_bytes(prec); }
 
@@ -404,15 +420,32 @@ __device__ __forceinline__ void store_spinor(void *field, const Geom &g, int b, 
 // ------------------------------------------------------------ SU(3) hops
 template <typename C> struct Link { cpx<C> m[9]; };
 
-template <typename S, typename C>
+template <typename C> __device__ __forceinline__ cpx<C> cmul(cpx<C> a, cpx<C> b);
+
+// Third row of an SU(3) matrix from the first two: conj(row0 x row1).
+template <typename C> __device__ __forceinline__ void su3_third_row(Link<C> &u) {
+  const cpx<C> *a = u.m, *b = u.m + 3;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+    const cpx<C> p = cmul(a[k1], b[k2]), q = cmul(a[k2], b[k1]);
+    u.m[6 + k] = {p.re - q.re, q.im - p.im};
+  }
+}
+
+// Link U_mu of site (b, s) from a field of storage S with LP pairs per link,
+// [block][4 * LP][Vb]: link_pairs<S>() (the Dslash fields), or 9 (every
+// entry: the Schwarz kernel's fields, see OpFields::links_full).
+template <typename S, typename C, int LP = link_pairs<S>()>
 __device__ __forceinline__ void load_link(const void *links, const Geom &g, int b, int s, int mu, Link<C> &u) {
   using P = typename Store<S>::pair_t;
   DD_CHECK_INDEX(b, g.nblocks);
   DD_CHECK_INDEX(s, g.Vb);
   DD_CHECK_INDEX(mu, 4);
-  const P *base = (const P *)links + ((size_t)b * 36 + 9 * mu) * g.Vb + s;
+  const P *base = (const P *)links + ((size_t)b * 4 * LP + LP * mu) * g.Vb + s;
 #pragma unroll
-  for (int i = 0; i < 9; i++) u.m[i] = from_pair<C, P>(__ldg(base + (size_t)i * g.Vb));
+  for (int i = 0; i < LP; i++) u.m[i] = from_pair<C, P>(__ldg(base + (size_t)i * g.Vb));
+  if constexpr (LP == 6) su3_third_row(u);
 }
 
 template <typename C> __device__ __forceinline__ cpx<C> cmul(cpx<C> a, cpx<C> b) {
@@ -594,7 +627,12 @@ struct Gauge {
 // Operator fields in one storage precision.
 struct OpFields {
   int prec = -1;
-  void *links = nullptr;  // [nblocks][36][Vb] pairs
+  void *links = nullptr;  // [nblocks][4 * link_pairs_of(prec)][Vb] pairs (Dslash)
+  // [nblocks][36][Vb] pairs, every entry: the Schwarz kernel rebuilds no rows
+  // (its block solve reads each link about ten times per phase from L1 or
+  // shared memory, where the rebuild would cost more issue slots than the
+  // bytes it saves); the same array as `links` for FP64
+  void *links_full = nullptr;
   void *clov = nullptr;   // A, [nblocks][36][Vb] pairs
   void *cinv = nullptr;   // A^-1 on even sites, [nblocks][36][Vh] pairs
 };
@@ -632,10 +670,24 @@ struct RhsPtrs {
 // pointers of nrhs contiguous fields starting at in / out
 RhsPtrs contiguous(const void *in, void *out, int nrhs, size_t field_bytes);
 
+// Per-right-hand-side work fields of the Schwarz smoother's incremental
+// colour residual (fields of the smoother's storage precision): e[r] the
+// latest block corrections, r[r] each block's residual after its own latest
+// solve (odd sites; the even-site residual of an even-odd block solve is
+// zero).
+struct AuxPtrs {
+  void *e[MAX_RHS];
+  void *r[MAX_RHS];
+};
+
 // --------------------------------------------------------- kernel launchers
 int launch_pack(const Geom &g, int prec, const double *canon, void *field, int nrhs, double scale, cudaStream_t st);
 int launch_unpack(const Geom &g, int prec, const void *field, double *canon, int nrhs, double scale, cudaStream_t st);
-int launch_pack_links(const Geom &g, int prec, const double *links_canon, void *out, cudaStream_t st);
+// FP64 canonical links -> tile layout of `prec`; for 12-real storage raises
+// bit 2 of *bad (may be null) if a link is not special unitary to 1e-6
+int launch_pack_links(const Geom &g, int prec, const double *links_canon, void *out, int *bad, cudaStream_t st);
+// FP64 canonical links -> the full nine-pair tile layout of `prec`
+int launch_pack_links_full(const Geom &g, int prec, const double *links_canon, void *out, cudaStream_t st);
 // caller-supplied site blocks A(n) [V][2][6][6] complex (canonical order), packed and inverted like the build
 int launch_load_clover(const Geom &g, const double *A_canon, double *clov64, double *cinv64, int *bad,
                        cudaStream_t st);
@@ -650,9 +702,15 @@ int launch_dirac_df(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStre
 // n complex FP64 values -> double-float {hi, lo} pairs, same positions
 int launch_split_pairs(const double *in, void *out, size_t n, cudaStream_t st);
 // Schwarz sweeps; p.in = right-hand sides b, p.out = iterates x
-int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &sp, const RhsPtrs &p, cudaStream_t st);
+// aux (may be null): work fields for the incremental colour residual, one
+// pair per right-hand side of p; without them every phase recomputes
+// r = b - D x from x
+int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &sp, const RhsPtrs &p, cudaStream_t st,
+               const AuxPtrs *aux = nullptr);
+// nrhs contiguous fields b, x; aux_base (may be null): 2 x nrhs contiguous
+// work fields (e of every right-hand side, then r)
 int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &sp, const void *b, void *x, int nrhs,
-               cudaStream_t st);
+               cudaStream_t st, void *aux_base = nullptr);
 // DD_OK, or DD_ETIMEOUT if a bounded device wait has expired since the last
 // call (waits for the device first; clears the count)
 int device_wait_status();

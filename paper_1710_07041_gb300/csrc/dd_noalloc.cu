@@ -91,7 +91,7 @@ size_t noalloc_bytes_needed(const Geom &g, int prec, int m, int nblk) {
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   size_t f64 = (size_t)g.V * 24 * 8, fz = (size_t)g.V * 24 * real_bytes(zprec), fp = (size_t)g.V * 24 * real_bytes(prec);
   return al(sizeof(double) * (size_t)nblk * 33) + al(sizeof(double) * 256) + al(sizeof(double) * 136) +
-         al(sizeof(double) * 2 * MAXM) + (size_t)(m + 1) * al(f64) + (size_t)m * al(fz) + 4 * al(f64) + 2 * al(fp) +
+         al(sizeof(double) * 2 * MAXM) + (size_t)(m + 1) * al(f64) + (size_t)m * al(fz) + 4 * al(f64) + 4 * al(fp) +
          al(fz);
 }
 
@@ -148,6 +148,9 @@ extern "C" int dd_solve_noalloc(dd_op_t opp, const dd_solve_params *p, const dou
   double *x = cv.take<double>(f64), *b = cv.take<double>(f64), *w = cv.take<double>(f64);
   double *canon = cv.take<double>(f64);
   void *tin = cv.take<char>(fp), *tout = cv.take<char>(fp), *zt = cv.take<char>(fz);
+  AuxPtrs ax{};   // the smoother's work fields (corrections, block residuals)
+  ax.e[0] = cv.take<char>(fp);
+  ax.r[0] = cv.take<char>(fp);
   const size_t vstride = f64_al / 16;   // complex entries between basis vectors
 
   // the Blas object borrows scratch; detach it before it goes out of scope
@@ -225,9 +228,9 @@ extern "C" int dd_solve_noalloc(dd_op_t opp, const dd_solve_params *p, const dou
       sp.x_is_zero = 1;
       // z_j = SAP(sigma v_j), kept scaled by sigma as in dd_solve (H and y carry the factor)
       if (op->prec == zprec) {
-        if ((rc = launch_sap(g, op->fp, sp, tin, zj, 1, st))) return rc;
+        if ((rc = launch_sap(g, op->fp, sp, contiguous(tin, zj, 1, fp), st, &ax))) return rc;
       } else {
-        if ((rc = launch_sap(g, op->fp, sp, tin, tout, 1, st))) return rc;
+        if ((rc = launch_sap(g, op->fp, sp, contiguous(tin, tout, 1, fp), st, &ax))) return rc;
         if ((rc = launch_convert_field(g, op->prec, tout, zprec, zj, 1, 1.0, st))) return rc;
       }
       if ((rc = launch_dirac(g, fz_ops, zj, zprec == DD_F64 ? (void *)w : zt, 1, st))) return rc;

@@ -7,8 +7,14 @@
 // One CTA per block (x one right-hand side). Per phase the CTA
 //   1. stages the block's links, odd-site clover A_oo and even-site inverse
 //      A_ee^-1 into shared memory with bulk (TMA) copies (overlapping step 2),
-//   2. forms r = b - D x on its sites (neighbour x read from the other colour's
-//      blocks in HBM; skipped when x = 0),
+//   2. forms its residual: r = b - D x on its sites (neighbour x read from
+//      the other colour's blocks in HBM; skipped when x = 0), or, given work
+//      fields, incrementally: after its own solve a block's residual is zero
+//      on even sites and the MR residual rho on odd ones, and until its next
+//      phase only the neighbouring blocks' corrections e change x, so
+//      r = (stored residual, or b on the first solve from x = 0) minus the
+//      hops of e across the block faces; each phase stores its e and rho for
+//      the next phases (DD_SAP_INCR=0 turns this off),
 //   3. Schur right-hand side  bhat = r_o - D_oe A_ee^-1 r_e,
 //   4. n_MR steps on Dhat = A_oo - D_oe A_ee^-1 D_eo from e_o = 0:
 //        p = Dhat rho, alpha = <p,rho>/<p,p>, e_o += alpha rho, rho -= alpha p,
@@ -70,10 +76,14 @@ unsigned *sap_timeout_counter() {
   return (unsigned *)p;
 }
 
-int sap_run_f64(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st);
-int sap_run_f32(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st);
-int sap_run_f16(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st);
-int sap_run_bf16(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st);
+int sap_run_f64(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp,
+                const AuxPtrs *ax, cudaStream_t st);
+int sap_run_f32(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp,
+                const AuxPtrs *ax, cudaStream_t st);
+int sap_run_f16(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp,
+                const AuxPtrs *ax, cudaStream_t st);
+int sap_run_bf16(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp,
+                const AuxPtrs *ax, cudaStream_t st);
 
 namespace {
 // Self-test of the staging handshake: one 16-byte bulk copy tracked by an
@@ -115,14 +125,20 @@ struct GraphCache {
 static GraphCache g_graphs;
 
 int sap_launch_as_graph(const std::string &key, int variant, int nkernels, const OpFields &f, const RhsPtrs &rp,
-                        const std::function<int()> &enqueue, cudaStream_t st) {
+                        const AuxPtrs *ax, const std::function<int()> &enqueue, cudaStream_t st) {
   const char *env = getenv("DD_SAP_GRAPHS");
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cap);
   if ((env && env[0] == '0') || cap != cudaStreamCaptureStatusNone || st == 0 || direct_launch()) return enqueue();
-  std::string k = key + "|v" + std::to_string(variant) + "|" + std::to_string((uintptr_t)f.links);
-  for (int i = 0; i < rp.n; i++)
+  // every pointer baked into the captured launches is part of the key (a
+  // graph may only be replayed where a fresh capture would record the same
+  // arguments; the caller's key holds the geometry)
+  std::string k = key + "|v" + std::to_string(variant) + "|" + std::to_string((uintptr_t)f.links_full) + "," +
+                  std::to_string((uintptr_t)f.clov) + "," + std::to_string((uintptr_t)f.cinv);
+  for (int i = 0; i < rp.n; i++) {
     k += "|" + std::to_string((uintptr_t)rp.in[i]) + ":" + std::to_string((uintptr_t)rp.out[i]);
+    if (ax) k += ":" + std::to_string((uintptr_t)ax->e[i]) + ":" + std::to_string((uintptr_t)ax->r[i]);
+  }
   cudaGraphExec_t exec = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_graphs.mu);
@@ -188,18 +204,32 @@ size_t sap_smem_bytes(const Geom &g, int prec, bool stage) {
 }
 
 int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const void *b, void *x, int nrhs,
-               cudaStream_t st) {
+               cudaStream_t st, void *aux_base) {
   const size_t fb = (size_t)g.V * 24 * real_bytes(f.prec);
   for (int r0 = 0; r0 < nrhs; r0 += MAX_RHS) {
     int n = nrhs - r0 < MAX_RHS ? nrhs - r0 : MAX_RHS;
-    int rc = launch_sap(g, f, p, contiguous((const char *)b + r0 * fb, (char *)x + r0 * fb, n, fb), st);
+    AuxPtrs ax{};
+    for (int i = 0; aux_base && i < n; i++) {
+      ax.e[i] = (char *)aux_base + (size_t)(r0 + i) * fb;
+      ax.r[i] = (char *)aux_base + (size_t)(nrhs + r0 + i) * fb;
+    }
+    int rc = launch_sap(g, f, p, contiguous((const char *)b + r0 * fb, (char *)x + r0 * fb, n, fb), st,
+                        aux_base ? &ax : nullptr);
     if (rc) return rc;
   }
   return DD_OK;
 }
 
-int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
+int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st,
+               const AuxPtrs *ax) {
   NvtxRange range("dd:sap");
+  // DD_SAP_INCR=0: every phase forms r = b - D x from x (the incremental
+  // colour residual is off even where work fields are given)
+  static const bool incr_off = [] {
+    const char *e = getenv("DD_SAP_INCR");
+    return e && e[0] == '0';
+  }();
+  if (incr_off) ax = nullptr;
   if (rp.n < 1 || rp.n > MAX_RHS) {
     set_error("sap: 1..%d right-hand sides per launch", MAX_RHS);
     return DD_EINVAL;
@@ -213,10 +243,10 @@ int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const R
     return DD_ECUDA;
   }
   switch (f.prec) {
-    case DD_F64: return sap_run_f64(g, f, p, rp, st);
-    case DD_F32: return sap_run_f32(g, f, p, rp, st);
-    case DD_F16: return sap_run_f16(g, f, p, rp, st);
-    case DD_BF16: return sap_run_bf16(g, f, p, rp, st);
+    case DD_F64: return sap_run_f64(g, f, p, rp, ax, st);
+    case DD_F32: return sap_run_f32(g, f, p, rp, ax, st);
+    case DD_F16: return sap_run_f16(g, f, p, rp, ax, st);
+    case DD_BF16: return sap_run_bf16(g, f, p, rp, ax, st);
   }
   set_error("sap: bad precision %d", f.prec);
   return DD_EINVAL;

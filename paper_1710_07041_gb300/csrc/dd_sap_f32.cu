@@ -2,7 +2,8 @@
 #include "dd_sap_kernels.cuh"
 
 namespace dd {
-int sap_run_f32(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
-  return sap_variants<float>(g, f, p, rp, st);
+int sap_run_f32(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp,
+                const AuxPtrs *ax, cudaStream_t st) {
+  return sap_variants<float>(g, f, p, rp, ax, st);
 }
 }  // namespace dd

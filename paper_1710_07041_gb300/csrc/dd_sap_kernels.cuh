@@ -15,7 +15,16 @@ namespace dd {
 unsigned *sap_timeout_counter();
 // run `enqueue` (the launches of one smoother application) as a cached CUDA graph
 int sap_launch_as_graph(const std::string &key, int variant, int nkernels, const OpFields &f, const RhsPtrs &rp,
-                        const std::function<int()> &enqueue, cudaStream_t st);
+                        const AuxPtrs *ax, const std::function<int()> &enqueue, cudaStream_t st);
+
+// Residual modes of one colour phase (bit set `mode` of k_sap_phase).
+// Without SAP_INCR the phase forms r = b - D x on its blocks from x (b and x
+// in HBM). With it, r = (b if SAP_FROM_B, else the block's stored residual
+// after its own previous solve) minus, with SAP_HALO_E, the hops from the
+// neighbouring blocks' latest corrections e: x changed only there since.
+// SAP_WRITE_E / SAP_WRITE_R store this phase's corrections and residuals for
+// the next phases.
+enum { SAP_INCR = 1, SAP_FROM_B = 2, SAP_HALO_E = 4, SAP_WRITE_E = 8, SAP_WRITE_R = 16 };
 
 namespace {
 
@@ -81,6 +90,8 @@ template <typename P> struct Tile {
   int stride;
 };
 
+// link mu of tile site s (all nine entries: the kernel reads the full-link
+// field, OpFields::links_full)
 template <typename C, typename P>
 __device__ __forceinline__ void tile_link(const Tile<P> &t, int s, int mu, Link<C> &u) {
   DD_CHECK_INDEX(s, t.stride);
@@ -177,13 +188,13 @@ __device__ __forceinline__ void hop_global_dir(const Geom &g, const Site &t, con
   neighbour(g, t, MU, +1, &nb, &ns, &sg, &inside);
   if (inside ? !self_zero : !halo_zero) {
     load_spinor<S, C>(x, g, nb, ns, psi);
-    load_link<S, C>(links, g, t.b, t.s, MU, u);
+    load_link<S, C, 9>(links, g, t.b, t.s, MU, u);
     hop<MU, true, C, SW>(acc, u, psi, (C)(-0.5f * sg));
   }
   neighbour(g, t, MU, -1, &nb, &ns, &sg, &inside);
   if (inside ? !self_zero : !halo_zero) {
     load_spinor<S, C>(x, g, nb, ns, psi);
-    load_link<S, C>(links, g, nb, ns, MU, u);
+    load_link<S, C, 9>(links, g, nb, ns, MU, u);
     hop<MU, false, C, SW>(acc, u, psi, (C)(-0.5f * sg));
   }
 }
@@ -267,12 +278,13 @@ __device__ __forceinline__ void block_sum3(C &a, C &b, C &c, C *red) {
 template <typename S> struct SapSmem {
   using C = typename Store<S>::comp_t;
   using P = typename Store<S>::pair_t;
+  static constexpr int LT = 36;   // pairs per site of the links tile (full links)
   static size_t vec_bytes(const Geom &g) { return (size_t)12 * g.Vh * sizeof(cpx<C>); }
   // stage: 0 nothing staged, 1 links + A_oo + A_ee^-1, 2 links only
   static size_t bytes(const Geom &g, int stage) {
     size_t b = 3 * vec_bytes(g) + 96 * sizeof(C) + 16;   // + staging mbarrier
-    if (stage == 1) b += (size_t)36 * (g.Vb + 2 * g.Vh) * sizeof(P);
-    if (stage == 2) b += (size_t)36 * g.Vb * sizeof(P);
+    if (stage == 1) b += ((size_t)LT * g.Vb + (size_t)36 * 2 * g.Vh) * sizeof(P);
+    if (stage == 2) b += (size_t)LT * g.Vb * sizeof(P);
     return b;
   }
 };
@@ -284,10 +296,11 @@ template <typename S> struct SapSmem {
 template <typename S, int STAGE, int MINB, int NT, int SHAPE, bool UNROLL = false>
 __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *__restrict__ links,
                                                    const void *__restrict__ clov, const void *__restrict__ cinv,
-                                                   const RhsPtrs rp, int colour, int self_zero,
-                                                   int halo_zero, int nmr, int tile, unsigned *timeouts) {
+                                                   const RhsPtrs rp, const AuxPtrs ax, int colour, int self_zero,
+                                                   int halo_zero, int mode, int nmr, int tile, unsigned *timeouts) {
   using C = typename Store<S>::comp_t;
   using P = typename Store<S>::pair_t;
+  constexpr int LT = SapSmem<S>::LT;   // pairs per site of the links tile
   // a specialised shape is launched with one thread per site: blockDim.x == NT
   static_assert(SHAPE == 0 || (SHAPE == 1 && NT == 256) || (SHAPE == 2 && NT == 512), "shape / threads");
   extern __shared__ __align__(16) unsigned char smem[];
@@ -324,7 +337,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
   const int b = block_of(item % nbc), rt = item / nbc;
   if (threadIdx.x == 0 && item + (int)gridDim.x < nitems) {
     const int nitem = item + gridDim.x, nb = block_of(nitem % nbc), nrt = nitem / nbc;
-    prefetch_l2((const P *)links + (size_t)nb * 36 * Vb, 36u * Vb * sizeof(P));
+    prefetch_l2((const P *)links + (size_t)nb * LT * Vb, (unsigned)LT * Vb * sizeof(P));
     prefetch_l2((const P *)clov + (size_t)nb * 36 * Vb, 36u * Vb * sizeof(P));
     prefetch_l2((const P *)cinv + (size_t)nb * 36 * Vh, 36u * Vh * sizeof(P));
     constexpr int NC = spinor_chunks<S>();
@@ -338,19 +351,19 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
   }
 
   // Staging by bulk copies (the TMA engine), issued by thread 0 and tracked
-  // by the mbarrier: the links tile (36 x Vb pairs, contiguous per block),
+  // by the mbarrier: the links tile (LT x Vb pairs, contiguous per block),
   // and for STAGE 1 the odd half of every clover row (36 pieces of Vh pairs)
   // and the even-site inverse tile (36 x Vh, contiguous). Every size is a
   // multiple of 16 bytes (Vh is even) and every address 16-byte aligned.
   Tile<P> Lt, Ao, Ai;
   if constexpr (STAGE == 1) {
     P *sl = (P *)tiles;
-    P *sa = sl + (size_t)36 * Vb;
+    P *sa = sl + (size_t)LT * Vb;
     P *si = sa + (size_t)36 * Vh;
     if (threadIdx.x == 0) {
-      const P *gl = (const P *)links + (size_t)b * 36 * Vb;
+      const P *gl = (const P *)links + (size_t)b * LT * Vb;
       const P *ga = (const P *)clov + (size_t)b * 36 * Vb;
-      const unsigned lb = 36u * Vb * sizeof(P), rb = (unsigned)(Vh * sizeof(P));
+      const unsigned lb = (unsigned)LT * Vb * sizeof(P), rb = (unsigned)(Vh * sizeof(P));
       fence_proxy_async();
       mbar_arrive_expect(mbar, lb + 72u * rb);
       bulk_g2s(sl, gl, lb, mbar);
@@ -363,16 +376,16 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
   } else if constexpr (STAGE == 2) {
     P *sl = (P *)tiles;
     if (threadIdx.x == 0) {
-      const unsigned lb = 36u * Vb * sizeof(P);
+      const unsigned lb = (unsigned)LT * Vb * sizeof(P);
       fence_proxy_async();
       mbar_arrive_expect(mbar, lb);
-      bulk_g2s(sl, (const P *)links + (size_t)b * 36 * Vb, lb, mbar);
+      bulk_g2s(sl, (const P *)links + (size_t)b * LT * Vb, lb, mbar);
     }
     Lt = {sl, Vb};
     Ao = {(const P *)clov + (size_t)b * 36 * Vb + Vh, Vb};
     Ai = {(const P *)cinv + (size_t)b * 36 * Vh, Vh};
   } else {
-    Lt = {(const P *)links + (size_t)b * 36 * Vb, Vb};
+    Lt = {(const P *)links + (size_t)b * LT * Vb, Vb};
     Ao = {(const P *)clov + (size_t)b * 36 * Vb + Vh, Vb};
     Ai = {(const P *)cinv + (size_t)b * 36 * Vh, Vh};
   }
@@ -388,15 +401,39 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
     void *xf = rp.out[r];
     cpx<C> r_e[6], r_o[6];
 
-    // ---- 2. block residual r = b - D x (halves h of the even and odd site)
-    {
+    // ---- 2. block residual (halves h of the even and odd site): r = b - D x,
+    // or incrementally (SAP_INCR) from the stored residual and the hops of
+    // the neighbours' corrections across the block faces
+    if ((mode & SAP_INCR) && !(mode & SAP_FROM_B)) {
+      Spinor<C> rs;
+      load_spinor<S, C>(ax.r[r], g, b, Vh + j, rs);
+      half_of(rs, h, r_o);
+  #pragma unroll
+      for (int i = 0; i < 6; i++) r_e[i] = {0, 0};
+    } else {
       Spinor<C> bb;
       load_spinor<S, C>(bf, g, b, j, bb);
       half_of(bb, h, r_e);
       load_spinor<S, C>(bf, g, b, Vh + j, bb);
       half_of(bb, h, r_o);
     }
-    if (!(self_zero && halo_zero)) {
+    if (mode & SAP_INCR) {
+      if (mode & SAP_HALO_E) {
+  #pragma unroll 1
+        for (int par = 0; par < 2; par++) {
+          Spinor<C> part;
+          hops_global<S, C>(g, par ? so : se, h, links, ax.e[r], true, false, part);
+          cpx<C> hx[6];
+          exchange(xch, Vh, j, h, part, hx);
+  #pragma unroll
+          for (int i = 0; i < 6; i++) {
+            if (par) { r_o[i].re -= hx[i].re; r_o[i].im -= hx[i].im; }
+            else     { r_e[i].re -= hx[i].re; r_e[i].im -= hx[i].im; }
+          }
+          __syncthreads();
+        }
+      }
+    } else if (!(self_zero && halo_zero)) {
   #pragma unroll 1
       for (int par = 0; par < 2; par++) {
         const Site &t = par ? so : se;
@@ -576,11 +613,14 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
     }
 
     // ---- x += e: gather both halves through shared memory, then half 0
-    // writes the even site j and half 1 the odd site j
+    // writes the even site j and half 1 the odd site j (and, when asked,
+    // e to the corrections field and the odd-site residual rho to the
+    // residual field)
   #pragma unroll
     for (int i = 0; i < 6; i++) {
       te[(6 * h + i) * Vh + j] = ee[i];
       xch[(6 * h + i) * Vh + j] = eo[i];
+      if (mode & SAP_WRITE_R) rho[(6 * h + i) * Vh + j] = rh[i];
     }
     __syncthreads();
     {
@@ -588,6 +628,12 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
       const int s = h ? Vh + j : j;
       Spinor<C> xs, e;
       vec_load(src, Vh, j, e);
+      if (mode & SAP_WRITE_E) store_spinor<S, C>(ax.e[r], g, b, s, e);
+      if ((mode & SAP_WRITE_R) && h) {
+        Spinor<C> rs;
+        vec_load(rho, Vh, j, rs);
+        store_spinor<S, C>(ax.r[r], g, b, s, rs);
+      }
       if (self_zero) {
         xs = e;
       } else {
@@ -606,8 +652,8 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
 }
 
 template <typename S, int STAGE, int MINB, int NT, int SHAPE, bool UNROLL = false>
-int sap_k(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, int tile, bool persistent,
-          cudaStream_t st) {
+int sap_k(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, const AuxPtrs *ax, int tile,
+          bool persistent, cudaStream_t st) {
   size_t smem = SapSmem<S>::bytes(g, STAGE);
   auto kern = k_sap_phase<S, STAGE, MINB, NT, SHAPE, UNROLL>;
   // raise the kernel's dynamic shared-memory limit once (never during a capture)
@@ -630,14 +676,27 @@ int sap_k(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtr
     if (occ < 1) occ = 1;
     grid = std::min(nitems, sms * occ);
   }
+  const AuxPtrs none{};
   for (int sw = 0; sw < p.sweeps; sw++)
     for (int colour = 0; colour < 2; colour++) {
       // with x = 0 on entry: the first phase sees x = 0 everywhere, the
       // second still has x = 0 on its own (colour-1) blocks
       int self_zero = (p.x_is_zero && sw == 0) ? 1 : 0;
       int halo_zero = (p.x_is_zero && sw == 0 && colour == 0) ? 1 : 0;
-      kern<<<grid, g.Vb, smem, st>>>(g, f.links, f.clov, f.cinv, rp, colour, self_zero, halo_zero, p.mr_steps,
-                                     tile, sap_timeout_counter());
+      int mode = 0;
+      if (ax) {
+        // a block's residual: b on its first solve when x = 0 there (minus the
+        // neighbours' corrections from colour 0 when it is colour 1), the
+        // stored residual from the second sweep on; from a given x the first
+        // sweep forms b - D x. Corrections are read by the next phase,
+        // residuals by the same colour in the next sweep.
+        if (p.x_is_zero && sw == 0) mode = SAP_INCR | SAP_FROM_B | (colour ? SAP_HALO_E : 0);
+        else if (sw > 0) mode = SAP_INCR | SAP_HALO_E;
+        if (!(sw == p.sweeps - 1 && colour == 1)) mode |= SAP_WRITE_E;
+        if (sw + 1 < p.sweeps) mode |= SAP_WRITE_R;
+      }
+      kern<<<grid, g.Vb, smem, st>>>(g, f.links_full, f.clov, f.cinv, rp, ax ? *ax : none, colour, self_zero, halo_zero,
+                                     mode, p.mr_steps, tile, sap_timeout_counter());
       DD_LAUNCHED();
     }
   return DD_OK;
@@ -645,22 +704,22 @@ int sap_k(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtr
 
 // the kernel specialised for the lattice's block shape when there is one
 template <typename S, int STAGE, int MINB, int NT = 256>
-int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, int tile, bool persistent,
-          cudaStream_t st) {
+int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, const AuxPtrs *ax, int tile,
+          bool persistent, cudaStream_t st) {
   constexpr int SH = NT == 256 ? 1 : 2;   // the shape this thread count fits
-  if (shape_of(g) == SH) return sap_k<S, STAGE, MINB, NT, SH>(g, f, p, rp, tile, persistent, st);
-  return sap_k<S, STAGE, MINB, NT, 0>(g, f, p, rp, tile, persistent, st);
+  if (shape_of(g) == SH) return sap_k<S, STAGE, MINB, NT, SH>(g, f, p, rp, ax, tile, persistent, st);
+  return sap_k<S, STAGE, MINB, NT, 0>(g, f, p, rp, ax, tile, persistent, st);
 }
 // the MR loop unrolled by parity (specialised shape only)
 template <typename S, int STAGE, int MINB, int NT = 256>
-int sap_u(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, int tile, bool persistent,
-          cudaStream_t st) {
+int sap_u(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, const AuxPtrs *ax, int tile,
+          bool persistent, cudaStream_t st) {
   constexpr int SH = NT == 256 ? 1 : 2;
   if (shape_of(g) != SH) {
     set_error("sap: the unrolled MR loop exists for the specialised block shapes only");
     return DD_EINVAL;
   }
-  return sap_k<S, STAGE, MINB, NT, SH, true>(g, f, p, rp, tile, persistent, st);
+  return sap_k<S, STAGE, MINB, NT, SH, true>(g, f, p, rp, ax, tile, persistent, st);
 }
 
 template <typename S> constexpr bool sixteen_bit() { return Store<S>::prec == DD_F16 || Store<S>::prec == DD_BF16; }
@@ -674,7 +733,8 @@ template <typename S> constexpr bool sixteen_bit() { return Store<S>::prec == DD
 // With several right-hand sides a CTA also solves `tile` of them with one
 // staging of its block's operator (rhs_tile; 0 lets the autotuner choose).
 template <typename S>
-int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st) {
+int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, const AuxPtrs *ax,
+                 cudaStream_t st) {
   const size_t limit = 227 * 1024, half = 113 * 1024;
   const bool stage1 = SapSmem<S>::bytes(g, 1) <= limit;
   const bool stage2 = SapSmem<S>::bytes(g, 1) <= half;
@@ -714,24 +774,25 @@ int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const
     const int layout = layouts[k % nl], tile = tiles[(k / nl) % nt];
     const bool pers = k >= nl * nt;
     switch (layout) {
-      case 1: return sap_t<S, 1, 2>(g, f, p, rp, tile, pers, st);
-      case 2: return sap_t<S, 0, 2>(g, f, p, rp, tile, pers, st);
-      case 3: return sap_t<S, 1, 1, 512>(g, f, p, rp, tile, pers, st);
-      case 4: return sap_t<S, 0, 1, 512>(g, f, p, rp, tile, pers, st);
-      case 5: return sap_t<S, 2, 2>(g, f, p, rp, tile, pers, st);
+      case 1: return sap_t<S, 1, 2>(g, f, p, rp, ax, tile, pers, st);
+      case 2: return sap_t<S, 0, 2>(g, f, p, rp, ax, tile, pers, st);
+      case 3: return sap_t<S, 1, 1, 512>(g, f, p, rp, ax, tile, pers, st);
+      case 4: return sap_t<S, 0, 1, 512>(g, f, p, rp, ax, tile, pers, st);
+      case 5: return sap_t<S, 2, 2>(g, f, p, rp, ax, tile, pers, st);
       case 6:
       case 7:
         if constexpr (sixteen_bit<S>()) {
-          if (layout == 6) return sap_u<S, 1, 2>(g, f, p, rp, tile, pers, st);
-          return sap_u<S, 0, 2>(g, f, p, rp, tile, pers, st);
+          if (layout == 6) return sap_u<S, 1, 2>(g, f, p, rp, ax, tile, pers, st);
+          return sap_u<S, 0, 2>(g, f, p, rp, ax, tile, pers, st);
         }
         return (int)DD_EINVAL;
-      default: return sap_t<S, 1, 1>(g, f, p, rp, tile, pers, st);
+      default: return sap_t<S, 1, 1>(g, f, p, rp, ax, tile, pers, st);
     }
   };
   int k = 0;
   std::string key = tune_key("sap", g, f.prec, rp.n) + "|" + std::to_string(p.sweeps) + "," +
-                    std::to_string(p.mr_steps) + "," + std::to_string(p.rhs_tile);
+                    std::to_string(p.mr_steps) + "," + std::to_string(p.rhs_tile) + "," +
+                    std::to_string(g.antiperiodic);
   // x is pure output when x_is_zero, so trial runs leave the same result
   if (p.x_is_zero) {
     int rc = tuned_variant(key, 2 * nl * nt, run, st, &k);
@@ -740,7 +801,7 @@ int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const
     int c = tune_lookup(key);
     k = c >= 0 ? c : 0;
   }
-  return sap_launch_as_graph(key, k, 2 * p.sweeps, f, rp, [&] { return run(k); }, st);
+  return sap_launch_as_graph(key, k, 2 * p.sweeps, f, rp, ax, [&] { return run(k); }, st);
 }
 
 }  // namespace

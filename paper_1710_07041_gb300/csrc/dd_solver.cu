@@ -55,7 +55,7 @@ size_t BatchSolver::bytes_per_slot(const Geom &g, int prec, int m) {
   size_t f64 = (size_t)g.V * 24 * 8;
   int zprec = prec == DD_F64 ? DD_F64 : DD_F32;
   size_t fz = (size_t)g.V * 24 * real_bytes(zprec), fp = (size_t)g.V * 24 * real_bytes(prec);
-  return (size_t)(m + 1) * f64 + (size_t)m * fz + 4 * f64 + 2 * fp + fz;
+  return (size_t)(m + 1) * f64 + (size_t)m * fz + 4 * f64 + 4 * fp + fz;
 }
 
 BatchSolver::BatchSolver(const Op *op, const dd_solve_params &p, int slots, cudaStream_t st)
@@ -78,6 +78,7 @@ std::vector<std::pair<void **, size_t>> BatchSolver::slot_buffers(Slot &s) const
   return {{(void **)&s.Vb, (m + 1) * f64_}, {(void **)&s.Z, m * fz_},   {(void **)&s.x, f64_},
           {(void **)&s.b, f64_},           {(void **)&s.w, f64_},       {(void **)&s.canon, f64_},
           {&s.tin, fp_},                   {&s.tout, fp_},              {&s.zt, fz_},
+          {&s.se, fp_},                    {&s.sr, fp_},
           {(void **)&s.sdev, sizeof(double) * (m + 1)}};
 }
 
@@ -380,9 +381,14 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
       sp_ptrs.in[i] = s->tin;
       sp_ptrs.out[i] = direct ? (void *)(s->Z + (size_t)s->j * fz_) : s->tout;
     }
+    AuxPtrs ax;
+    for (int i = 0; i < (int)A.size(); i++) {
+      ax.e[i] = A[i]->se;
+      ax.r[i] = A[i]->sr;
+    }
     dd_sap_params sp = p_.sap;
     sp.x_is_zero = 1;
-    if ((rc = launch_sap(g, op_->fp, sp, sp_ptrs, st_))) return rc;
+    if ((rc = launch_sap(g, op_->fp, sp, sp_ptrs, st_, &ax))) return rc;
     for (int i = 0; i < (int)A.size(); i++) {
       Slot *s = A[i];
       char *zj = s->Z + (size_t)s->j * fz_;

@@ -42,6 +42,7 @@ struct Slot {
   char *Z = nullptr;     // m preconditioned fields (zprec)
   double *x = nullptr, *b = nullptr, *w = nullptr, *canon = nullptr;
   void *tin = nullptr, *tout = nullptr, *zt = nullptr;
+  void *se = nullptr, *sr = nullptr;   // smoother work fields (corrections, block residuals)
   MgWork *mgw = nullptr;   // coarse-solve workspace when preconditioning with multigrid
 };
 

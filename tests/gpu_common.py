@@ -11,6 +11,16 @@ def relerr(a, b):
     return float(np.linalg.norm((a - b).reshape(-1)) / np.linalg.norm(b.reshape(-1)))
 
 
+def worst_site(a, b):
+    """Largest per-site error against the RMS site norm of b: max_n |a_n - b_n|
+    / sqrt(mean_n |b_n|^2) over spinor sites (arrays (..., 4, 3)). A single
+    wrong site among thousands hardly moves the relative L2 error but shows
+    here at full size."""
+    d = np.linalg.norm((a - b).reshape(-1, 12), axis=1)
+    ref = np.sqrt(np.mean(np.linalg.norm(b.reshape(-1, 12), axis=1) ** 2))
+    return float(d.max() / ref)
+
+
 class Setup:
     """A lattice, gauge field and operator on both sides."""
 

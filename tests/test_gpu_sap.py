@@ -12,7 +12,7 @@ import pytest
 
 import paper_1710_07041_gb300 as dd
 import synth
-from gpu_common import Setup, relerr
+from gpu_common import Setup, relerr, worst_site
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +35,10 @@ def test_sap_matches_oracle(prec, dims, block, sweeps, nmr):
     s.op.sap_smooth(fb, fx, sweeps, nmr, x_is_zero=True)
     got = s.lat.from_field(fx, prec)
     want = s.ref.sap(block, b, sweeps, nmr)
-    assert relerr(got, want) <= TOL[prec]
+    e = relerr(got, want)
+    print(f"SAP prec={prec} dims={dims} block={block} sweeps={sweeps} nmr={nmr}: rel L2 {e:.3e}, "
+          f"worst site {worst_site(got, want):.3e}")
+    assert e <= TOL[prec]
     s.close()
 
 
