@@ -542,8 +542,12 @@ def run_kernels(args):
     fin, fout = lat.to_field(b, dd.F32), lat.new_field(dd.F32)
     fbp, fxp = lat.to_field(b, prec), lat.new_field(prec)
     res = {}
-    for name, fn, reps in (("apply_D_f32", lambda: op.apply_D(dd.F32, fin, fout), 20),
-                           ("sap", lambda: op.sap_smooth(fbp, fxp, wl["sweeps"], wl["mr_steps"]), 3)):
+    kernels = [("apply_D_f32", lambda: op.apply_D(dd.F32, fin, fout), 20),
+               ("sap", lambda: op.sap_smooth(fbp, fxp, wl["sweeps"], wl["mr_steps"]), 3)]
+    if prec != dd.F32:
+        fop = lat.new_field(prec)
+        kernels.append(("apply_D_" + args.prec, lambda: op.apply_D(prec, fbp, fop), 20))
+    for name, fn, reps in kernels:
         for _ in range(args.warmup):
             fn()
         res[name + "_ms"] = ev_time(fn, max(1, min(reps, args.steps)), stream)
@@ -643,6 +647,22 @@ def run_batched(args):
 # smoothing iterations, coarse GMRES steps and tolerance, Schwarz post-smoother
 MG = {"n_vectors": 16, "setup_iters": 6, "coarse_max_iter": 24, "coarse_tol": 0.05, "sweeps": 3, "mr_steps": 4,
       "tv_seed": 7000}
+
+
+def run_mma(args):
+    """The tensor-core question for the 12-source link product: time the
+    FP32 CUDA-core form, the warp-MMA form (FP16 operands, two
+    site-directions block-diagonal per m16n8k16 tile) and the FP16-operand
+    CUDA-core form on the same products (dd_bench_link_product), in useful
+    flops (1728 per site-direction: a 6x6 real matrix times 24 columns)."""
+    import paper_1710_07041_gb300 as dd
+    ctas, reps = 152 * 8, 200
+    out = {"mode": "mma", "sites_x_directions": ctas * 64, "reps": reps, "rhs_tile": 12}
+    for method, name in ((0, "fp32_cuda_cores"), (1, "fp16_mma_sync"), (2, "fp16_operands_cuda_cores")):
+        ms, n, diff = dd.bench_link_product(method, ctas, reps)
+        out[name] = {"ms": ms, "useful_TFLOP/s": 1728.0 * n * reps / (ms * 1e-3) / 1e12,
+                     "rel_diff_vs_fp32": diff}
+    print(json.dumps(out), flush=True)
 
 
 def run_mg(args):
@@ -803,10 +823,11 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the 96x48^3 FP16/BF16 kernel measurements")
     ap.add_argument("--outer-f64", action="store_true",
                     help="IEEE FP64 Krylov basis and true residual with a mixed-precision smoother")
-    ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "batched", "serve", "mg"],
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "batched", "serve", "mg", "mma"],
                     help="kernels: short kernel loop for profiler captures; batched: the 24-source "
                          "48^3x96 workload; serve: the Poisson request stream; mg: two-level "
-                         "preconditioner against SAP alone (no contract line)")
+                         "preconditioner against SAP alone; mma: tensor-core link-product "
+                         "measurement (no contract line)")
     ap.add_argument("--requests", type=int, default=40, help="requests in --mode serve")
     ap.add_argument("--rate", type=float, default=200.0, help="offered requests/s in --mode serve")
     ap.add_argument("--solve-iters", type=int, default=20, help="iteration cap of the solve in --mode kernels")
@@ -823,6 +844,8 @@ def main():
         run_serve(args)
     elif args.mode == "mg":
         run_mg(args)
+    elif args.mode == "mma":
+        run_mma(args)
     elif args.impl == "reference":
         run_reference(args, rank)
     else:

@@ -113,6 +113,20 @@ int dd_device_status(void);
  * expiry was observed and the context is still usable. Synchronous. */
 int dd_selftest_wait(int expire);
 
+/* Measurement of the tensor-core question (no counterpart in the paper): the
+ * link product of a Schwarz block with a tile of 12 right-hand sides - a
+ * 3x3 complex link times 24 complex colour vectors, i.e. a real 6x6 by 6x24
+ * product per site and direction - for `ctas` thread blocks of 64
+ * site-directions, `reps` times from shared memory. method 0: FP32 operands,
+ * FP32 CUDA-core arithmetic; 1: FP16 operands, warp-level tensor-core
+ * products (mma.sync m16n8k16, two site-directions block-diagonal in one
+ * 16x16 operand, FP32 accumulation); 2: FP16 operands, FP32 CUDA-core
+ * arithmetic. *ms receives the time of the `reps` passes (CUDA events, legacy
+ * stream); rel_diff (may be NULL) the largest difference of one pass's
+ * products from method 0's on the same inputs (exact in FP16), relative to
+ * the largest product. Allocates its buffers; synchronous. */
+int dd_bench_link_product(int method, int ctas, int reps, double *ms, double *rel_diff);
+
 /* ------------------------------------------------------------------ setup */
 
 /* Lattice geometry and storage tiling. dims {T,Z,Y,X} >= 2 each; block as in

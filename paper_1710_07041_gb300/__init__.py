@@ -82,6 +82,8 @@ EXPORTS = {
     "dd_kernel_launches": ([], ctypes.c_uint64),
     "dd_device_status": ([], ctypes.c_int),
     "dd_selftest_wait": ([ctypes.c_int], ctypes.c_int),
+    "dd_bench_link_product": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "dd_release_workspace": ([], ctypes.c_int),
     "dd_create_lattice": ([ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                            ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
@@ -474,6 +476,15 @@ def release_workspace():
     """dd_release_workspace: free the cached solver workspaces (device and
     pinned host buffers) that finished solves left for reuse."""
     _check(lib().dd_release_workspace(), "dd_release_workspace")
+
+
+def bench_link_product(method: int, ctas: int = 1216, reps: int = 200):
+    """dd_bench_link_product: (ms for `reps` passes, products per pass,
+    relative difference from the FP32 CUDA-core method)."""
+    ms, diff = ctypes.c_double(), ctypes.c_double()
+    _check(lib().dd_bench_link_product(int(method), int(ctas), int(reps), ctypes.byref(ms), ctypes.byref(diff)),
+           "dd_bench_link_product")
+    return ms.value, ctas * 64, diff.value
 
 
 def selftest_wait(expire: bool):

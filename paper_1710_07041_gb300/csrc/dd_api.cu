@@ -245,15 +245,13 @@ static int create_op(Gauge *ga, double c_sw, double m0, int prec, Fill fill, dd_
   if (rc == DD_OK) rc = launch_pack_links(g, DD_F64, ga->links_canon, op->f64.links, bad, st);
   if (rc == DD_OK) rc = launch_pack_links(g, DD_F32, ga->links_canon, op->f32.links, bad, st);
   if (rc == DD_OK) rc = launch_pack_links_full(g, DD_F32, ga->links_canon, op->f32.links_full, st);
-  if (rc == DD_OK) rc = launch_convert_pairs(DD_F32, (const double *)op->f64.clov, op->f32.clov, (size_t)g.V * 36, st);
-  if (rc == DD_OK)
-    rc = launch_convert_pairs(DD_F32, (const double *)op->f64.cinv, op->f32.cinv, (size_t)g.V / 2 * 36, st);
+  if (rc == DD_OK) rc = launch_convert_clover(DD_F32, (const double *)op->f64.clov, op->f32.clov, g.nblocks, g.Vb, st);
+  if (rc == DD_OK) rc = launch_convert_clover(DD_F32, (const double *)op->f64.cinv, op->f32.cinv, g.nblocks, g.Vh, st);
   if (rc == DD_OK && (prec == DD_F16 || prec == DD_BF16)) {
     rc = launch_pack_links(g, prec, ga->links_canon, op->fp.links, bad, st);
     if (rc == DD_OK) rc = launch_pack_links_full(g, prec, ga->links_canon, op->fp.links_full, st);
-    if (rc == DD_OK) rc = launch_convert_pairs(prec, (const double *)op->f64.clov, op->fp.clov, (size_t)g.V * 36, st);
-    if (rc == DD_OK)
-      rc = launch_convert_pairs(prec, (const double *)op->f64.cinv, op->fp.cinv, (size_t)g.V / 2 * 36, st);
+    if (rc == DD_OK) rc = launch_convert_clover(prec, (const double *)op->f64.clov, op->fp.clov, g.nblocks, g.Vb, st);
+    if (rc == DD_OK) rc = launch_convert_clover(prec, (const double *)op->f64.cinv, op->fp.cinv, g.nblocks, g.Vh, st);
   }
   if (rc == DD_OK && prec != DD_F64) {
     // double-float copies of the FP64 links and site blocks (the true residual of mixed-precision solves)

@@ -78,12 +78,14 @@ __global__ void k_convert_field(Geom g, const void *in, void *out, int nrhs, dou
   store_spinor<SO, CO>((char *)out + r * bytes_out, g, b, s, w);
 }
 
-// canonical FP64 links [V][4][9] (double2) -> tile [b][4 x LP][Vb] pairs,
-// LP = 9 (all entries) or 6 (rows 0 and 1; row 2 is rebuilt on load, so the
-// link must be special unitary: a deviation of row 2 from conj(row0 x row1)
-// above 1e-6 sets bit 2 of *bad)
-template <typename P, int LP = link_pairs_of_pair<P>()>
+// canonical FP64 links [V][4][9] (double2) -> tiles of LP pairs per link:
+// LP = 6 (rows 0 and 1; row 2 is rebuilt on load, so the link must be special
+// unitary: a deviation of row 2 from conj(row0 x row1) above 1e-6 sets bit 2
+// of *bad) or 9 (all entries). CHUNKED: the chunked tile layout (link_slot),
+// else pair-major [b][36][Vb].
+template <typename P, int LP = link_pairs_of_pair<P>(), bool CHUNKED = true>
 __global__ void k_pack_links(Geom g, const double2 *__restrict__ canon, P *out, int *bad) {
+  constexpr int CP = chunk_pairs<P>(), NCH = 4 * LP / CP;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= g.V) return;
   int b = (int)(t / g.Vb), s = (int)(t - (long long)b * g.Vb);
@@ -91,7 +93,12 @@ __global__ void k_pack_links(Geom g, const double2 *__restrict__ canon, P *out, 
   for (int mu = 0; mu < 4; mu++) {
     const double2 *u = canon + n * 36 + 9 * mu;
 #pragma unroll
-    for (int i = 0; i < LP; i++) out[((size_t)b * 4 * LP + LP * mu + i) * g.Vb + s] = to_pair<P, double>(u[i].x, u[i].y);
+    for (int i = 0; i < LP; i++) {
+      const int q = link_slot<CP, LP>(mu, i);
+      const size_t at = CHUNKED ? (((size_t)b * NCH + q / CP) * g.Vb + s) * CP + q % CP
+                                : ((size_t)b * 4 * LP + LP * mu + i) * g.Vb + s;
+      out[at] = to_pair<P, double>(u[i].x, u[i].y);
+    }
     if constexpr (LP == 6) {
       double dev = 0;
       for (int k = 0; k < 3; k++) {
@@ -107,14 +114,20 @@ __global__ void k_pack_links(Geom g, const double2 *__restrict__ canon, P *out, 
   }
 }
 
+// FP64 clover tiles [tile][36][n] (pair-major) -> chunked tiles (clover_slot)
 template <typename P>
-__global__ void k_convert_pairs(const double2 *__restrict__ in, P *out, size_t n) {
-  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i < n) {
-    double2 d = in[i];
-    out[i] = to_pair<P, double>(d.x, d.y);
-  }
+__global__ void k_convert_clover(const double2 *__restrict__ in, P *out, size_t ntiles, int n) {
+  constexpr int CP = chunk_pairs<P>();
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= ntiles * 36 * (size_t)n) return;
+  const size_t site = i % n, r = i / n;
+  const int pair = (int)(r % 36);
+  const size_t tile = r / 36;
+  const int q = clover_slot<CP>(pair / 18, pair % 18);
+  const double2 d = in[i];
+  out[((tile * (36 / CP) + q / CP) * n + site) * CP + q % CP] = to_pair<P, double>(d.x, d.y);
 }
+
 
 // -------------------------------------------------------------- clover
 struct M3 { cpx<double> a[9]; };
@@ -369,6 +382,20 @@ int launch_unpack(const Geom &g, int prec, const void *field, double *canon, int
   return DD_EINVAL;
 }
 
+int launch_convert_clover(int prec, const double *in, void *out, size_t ntiles, int n, cudaStream_t st) {
+  const double2 *c = (const double2 *)in;
+  const size_t total = ntiles * 36 * (size_t)n;
+  const unsigned grid = (unsigned)((total + TPB - 1) / TPB);
+  switch (prec) {
+    case DD_F64: k_convert_clover<double2><<<grid, TPB, 0, st>>>(c, (double2 *)out, ntiles, n); break;
+    case DD_F32: k_convert_clover<float2><<<grid, TPB, 0, st>>>(c, (float2 *)out, ntiles, n); break;
+    case DD_F16: k_convert_clover<__half2><<<grid, TPB, 0, st>>>(c, (__half2 *)out, ntiles, n); break;
+    case DD_BF16: k_convert_clover<__nv_bfloat162><<<grid, TPB, 0, st>>>(c, (__nv_bfloat162 *)out, ntiles, n); break;
+    default: set_error("bad precision %d", prec); return DD_EINVAL;
+  }
+  return launched("k_convert_clover");
+}
+
 int launch_convert_field(const Geom &g, int pi, const void *in, int po, void *out, int nrhs, double scale,
                          cudaStream_t st) {
   switch (pi) {
@@ -398,28 +425,17 @@ int launch_pack_links(const Geom &g, int prec, const double *canon, void *out, i
 int launch_pack_links_full(const Geom &g, int prec, const double *canon, void *out, cudaStream_t st) {
   const double2 *c = (const double2 *)canon;
   switch (prec) {
-    case DD_F64: k_pack_links<double2, 9><<<grid_for(g.V), TPB, 0, st>>>(g, c, (double2 *)out, nullptr); break;
-    case DD_F32: k_pack_links<float2, 9><<<grid_for(g.V), TPB, 0, st>>>(g, c, (float2 *)out, nullptr); break;
-    case DD_F16: k_pack_links<__half2, 9><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__half2 *)out, nullptr); break;
+    case DD_F64: k_pack_links<double2, 9, false><<<grid_for(g.V), TPB, 0, st>>>(g, c, (double2 *)out, nullptr); break;
+    case DD_F32: k_pack_links<float2, 9, false><<<grid_for(g.V), TPB, 0, st>>>(g, c, (float2 *)out, nullptr); break;
+    case DD_F16: k_pack_links<__half2, 9, false><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__half2 *)out, nullptr); break;
     case DD_BF16:
-      k_pack_links<__nv_bfloat162, 9><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__nv_bfloat162 *)out, nullptr);
+      k_pack_links<__nv_bfloat162, 9, false><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__nv_bfloat162 *)out, nullptr);
       break;
     default: set_error("bad precision %d", prec); return DD_EINVAL;
   }
   return launched("k_pack_links");
 }
 
-int launch_convert_pairs(int prec, const double *in, void *out, size_t n, cudaStream_t st) {
-  const double2 *c = (const double2 *)in;
-  int gr = grid_for((long long)n);
-  switch (prec) {
-    case DD_F32: k_convert_pairs<float2><<<gr, TPB, 0, st>>>(c, (float2 *)out, n); break;
-    case DD_F16: k_convert_pairs<__half2><<<gr, TPB, 0, st>>>(c, (__half2 *)out, n); break;
-    case DD_BF16: k_convert_pairs<__nv_bfloat162><<<gr, TPB, 0, st>>>(c, (__nv_bfloat162 *)out, n); break;
-    default: set_error("bad precision %d", prec); return DD_EINVAL;
-  }
-  return launched("k_convert_pairs");
-}
 
 // FP64 complex -> double-float: hi = RN(v), lo = RN(v - hi) (v - hi is exact)
 __global__ void k_split_pairs(const double2 *__restrict__ in, float4 *out, size_t n) {

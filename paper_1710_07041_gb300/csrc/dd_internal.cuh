@@ -8,13 +8,14 @@
 // A spinor field of precision P is [block][chunk][Vb] with 16-byte chunks
 // (F64: 2 reals, F32: 4 reals, F16/BF16: 8 reals), so a warp reading one chunk
 // of 32 consecutive sites issues one fully coalesced 512-byte request.
-// Links are [block][4 x link_pairs][Vb] with "pairs" of two reals (double2 /
-// float2 / half2): in FP64 4 links x 18 reals = 72 reals per site, in 32- and
-// 16-bit storage the first two rows only, 48 reals (see link_pairs). Clover
-// site blocks are [block][36 pairs][Vb]:
-// clover 2 chirality blocks x 36 reals (6 real diagonal + 15 complex upper
-// entries, row-major) = 72 reals per site. The even-site inverse clover is
-// [block][36 pairs][Vb/2].
+// Links and clover site blocks are tiles of "pairs" of two reals (double2 /
+// float2 / half2). The Dslash's links: 4 links x 18 reals = 72 reals per site
+// in FP64, the first two rows only (48 reals) in 32- and 16-bit storage (see
+// link_pairs), in the chunked tile layout (see chunk_pairs); the Schwarz
+// kernel's links: all 72 reals, pair-major [block][36][Vb]. Clover: 2
+// chirality blocks x 36 reals (6 real diagonal + 15 complex upper entries,
+// row-major) = 72 reals per site, chunked tiles of Vb sites; the even-site
+// inverse clover, chunked tiles of Vb/2 sites.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -289,6 +290,8 @@ template <> struct Store<dfs> {
   using comp_t = dfl;
 };
 
+constexpr size_t real_bytes_of(int prec) { return (prec == DD_F64 || prec == DD_PREC_DF) ? 8 : prec == DD_F32 ? 4 : 2; }
+
 // Links in 32- and 16-bit storage keep the first two rows of each SU(3)
 // matrix (6 complex = 12 reals); the third row is rebuilt on load as
 // conj(row0 x row1), which holds for every special unitary matrix (the
@@ -301,6 +304,31 @@ template <typename P> __host__ __device__ constexpr int link_pairs_of_pair() {
   return (std::is_same<P, double2>::value || std::is_same<P, float4>::value) ? 9 : 6;
 }
 inline int link_pairs_of(int prec) { return (prec == DD_F64 || prec == DD_PREC_DF) ? 9 : 6; }
+
+// Chunked pair tiles (the Dslash's links, and the clover site blocks of every
+// kernel): the pairs of one site are grouped into 16-byte chunks of
+// CP = 16 / sizeof(pair) pairs (FP64 and double-float 1, FP32 2, FP16/BF16
+// 4), [tile][chunk][tile sites][CP], so that a thread reads its pairs with
+// 16-byte loads and a warp's load of one chunk over 32 consecutive sites is
+// one contiguous 512-byte request. With CP = 1 this is the pair-major layout
+// [tile][pair][tile sites]. A site's pairs take slots 0 .. 4 LP - 1 (links)
+// or 0 .. 35 (clover); slot q lies in chunk q / CP at position q % CP.
+template <typename P> __host__ __device__ constexpr int chunk_pairs() { return 16 / (int)sizeof(P); }
+inline int chunk_pairs_of(int prec) { return 16 / (int)(2 * real_bytes_of(prec)); }
+// Slot of entry i of link mu. With CP = 4 and two-row links (6 pairs) the
+// first four pairs of link mu fill chunk mu and the last two share chunk
+// 4 + mu / 2 with the next link's (so a link is one 16- and one 8-byte
+// load); otherwise in order.
+template <int CP, int LP> __host__ __device__ constexpr int link_slot(int mu, int i) {
+  return (CP == 4 && LP == 6) ? (i < 4 ? 4 * mu + i : 16 + 2 * mu + (i - 4)) : LP * mu + i;
+}
+// Slot of entry k (0..17) of clover chirality block h. With CP = 4 the first
+// sixteen entries of block h fill chunks 4h .. 4h+3 and the last two of both
+// blocks share chunk 8, so either block is four 16-byte loads and one 8-byte
+// load for a run-time h; otherwise in order.
+template <int CP> __host__ __device__ constexpr int clover_slot(int h, int k) {
+  return CP == 4 ? (k < 16 ? 16 * h + k : 32 + 2 * h + (k - 16)) : 18 * h + k;
+}
 
 inline size_t real_bytes(int prec) { return (prec == DD_F64 || prec == DD_PREC_DF) ? 8 : prec == DD_F32 ? 4 : 2; }
 inline size_t pair_bytes(int prec) { return 2 * real_bytes(prec); }
@@ -433,18 +461,42 @@ template <typename C> __device__ __forceinline__ void su3_third_row(Link<C> &u) 
   }
 }
 
-// Link U_mu of site (b, s) from a field of storage S with LP pairs per link,
-// [block][4 * LP][Vb]: link_pairs<S>() (the Dslash fields), or 9 (every
-// entry: the Schwarz kernel's fields, see OpFields::links_full).
-template <typename S, typename C, int LP = link_pairs<S>()>
+// Link U_mu of site (b, s) from a field of storage S with LP pairs per link:
+// the Dslash fields (LP = link_pairs<S>(), CHUNKED: the chunked tile layout
+// with link_slot), or the Schwarz kernel's (LP = 9, pair-major
+// [block][36][Vb], see OpFields::links_full).
+template <typename S, typename C, int LP = link_pairs<S>(), bool CHUNKED = true>
 __device__ __forceinline__ void load_link(const void *links, const Geom &g, int b, int s, int mu, Link<C> &u) {
   using P = typename Store<S>::pair_t;
+  constexpr int CP = chunk_pairs<P>();
   DD_CHECK_INDEX(b, g.nblocks);
   DD_CHECK_INDEX(s, g.Vb);
   DD_CHECK_INDEX(mu, 4);
-  const P *base = (const P *)links + ((size_t)b * 4 * LP + LP * mu) * g.Vb + s;
+  if constexpr (CHUNKED) {
+    const uint4 *q = (const uint4 *)links + (size_t)b * (4 * LP / CP) * g.Vb + s;   // chunk c at q[c * Vb]
+    if constexpr (CP == 4 && LP == 6) {
+      const uint4 v = __ldg(q + (size_t)mu * g.Vb);
+      const uint2 w = __ldg((const uint2 *)(q + (size_t)(4 + (mu >> 1)) * g.Vb) + (mu & 1));
+      const P *pv = (const P *)&v, *pw = (const P *)&w;
 #pragma unroll
-  for (int i = 0; i < LP; i++) u.m[i] = from_pair<C, P>(__ldg(base + (size_t)i * g.Vb));
+      for (int i = 0; i < 4; i++) u.m[i] = from_pair<C, P>(pv[i]);
+      u.m[4] = from_pair<C, P>(pw[0]);
+      u.m[5] = from_pair<C, P>(pw[1]);
+    } else {
+      static_assert(LP % CP == 0, "whole chunks per link");
+#pragma unroll
+      for (int c = 0; c < LP / CP; c++) {
+        const uint4 v = __ldg(q + (size_t)(mu * (LP / CP) + c) * g.Vb);
+        const P *pv = (const P *)&v;
+#pragma unroll
+        for (int k = 0; k < CP; k++) u.m[c * CP + k] = from_pair<C, P>(pv[k]);
+      }
+    }
+  } else {
+    const P *base = (const P *)links + ((size_t)b * 4 * LP + LP * mu) * g.Vb + s;
+#pragma unroll
+    for (int i = 0; i < LP; i++) u.m[i] = from_pair<C, P>(__ldg(base + (size_t)i * g.Vb));
+  }
   if constexpr (LP == 6) su3_third_row(u);
 }
 
@@ -456,6 +508,26 @@ template <typename C> __device__ __forceinline__ cpx<C> cmulc(cpx<C> a, cpx<C> b
   return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
 }
 
+// Fused multiply-add of the real type: fma for float and double (one
+// rounding per term); the double-float type forms the product and adds it.
+template <typename C> __device__ __forceinline__ C mad(C a, C b, C c) {
+  if constexpr (std::is_same<C, dfl>::value) return a * b + c;
+  else return fma(a, b, c);
+}
+// acc += a b and acc += conj(a) b (complex), as chains of fused multiply-adds
+template <typename C> __device__ __forceinline__ void cmac(cpx<C> &acc, cpx<C> a, cpx<C> b) {
+  acc.re = mad(a.re, b.re, acc.re);
+  acc.re = mad(-a.im, b.im, acc.re);
+  acc.im = mad(a.re, b.im, acc.im);
+  acc.im = mad(a.im, b.re, acc.im);
+}
+template <typename C> __device__ __forceinline__ void cmacc(cpx<C> &acc, cpx<C> a, cpx<C> b) {
+  acc.re = mad(a.re, b.re, acc.re);
+  acc.re = mad(a.im, b.im, acc.re);
+  acc.im = mad(a.re, b.im, acc.im);
+  acc.im = mad(-a.im, b.re, acc.im);
+}
+
 // h = U chi (two spin components of colour vectors)
 template <typename C>
 __device__ __forceinline__ void su3_mul(const Link<C> &u, const cpx<C> *chi, cpx<C> *h) {
@@ -465,11 +537,7 @@ __device__ __forceinline__ void su3_mul(const Link<C> &u, const cpx<C> *chi, cpx
     for (int r = 0; r < 3; r++) {
       cpx<C> a = {0, 0};
 #pragma unroll
-      for (int k = 0; k < 3; k++) {
-        cpx<C> p = cmul(u.m[3 * r + k], chi[3 * sp + k]);
-        a.re += p.re;
-        a.im += p.im;
-      }
+      for (int k = 0; k < 3; k++) cmac(a, u.m[3 * r + k], chi[3 * sp + k]);
       h[3 * sp + r] = a;
     }
 }
@@ -482,11 +550,7 @@ __device__ __forceinline__ void su3_dmul(const Link<C> &u, const cpx<C> *chi, cp
     for (int r = 0; r < 3; r++) {
       cpx<C> a = {0, 0};
 #pragma unroll
-      for (int k = 0; k < 3; k++) {
-        cpx<C> p = cmulc(u.m[3 * k + r], chi[3 * sp + k]);
-        a.re += p.re;
-        a.im += p.im;
-      }
+      for (int k = 0; k < 3; k++) cmacc(a, u.m[3 * k + r], chi[3 * sp + k]);
       h[3 * sp + r] = a;
     }
 }
@@ -522,27 +586,27 @@ __device__ __forceinline__ void project(const Spinor<C> &p, cpx<C> *chi) {
 template <int MU, bool FWD, typename C, bool SW = false>
 __device__ __forceinline__ void accum_recon(Spinor<C> &acc, const cpx<C> *h, C sgn) {
   constexpr int UP = SW ? 6 : 0, LO = SW ? 0 : 6;
+  // lower spins: acc -= sgn A^+ h (FWD) or += (the entries of A^+ h are
+  // entries of h up to sign, so every update is one fused multiply-add)
+  const C s = FWD ? -sgn : sgn;
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    cpx<C> h0 = {sgn * h[c].re, sgn * h[c].im}, h1 = {sgn * h[3 + c].re, sgn * h[3 + c].im};
-    acc.c[UP + c].re += h0.re; acc.c[UP + c].im += h0.im;
-    acc.c[UP + 3 + c].re += h1.re; acc.c[UP + 3 + c].im += h1.im;
-    cpx<C> l0, l1;
+    const cpx<C> h0 = h[c], h1 = h[3 + c];
+    cpx<C> &u0 = acc.c[UP + c], &u1 = acc.c[UP + 3 + c], &l0 = acc.c[LO + c], &l1 = acc.c[LO + 3 + c];
+    u0.re = mad(sgn, h0.re, u0.re); u0.im = mad(sgn, h0.im, u0.im);
+    u1.re = mad(sgn, h1.re, u1.re); u1.im = mad(sgn, h1.im, u1.im);
     if constexpr (MU == 0) {        // A^+ h = (i h1, i h0)
-      l0 = {-h1.im, h1.re}; l1 = {-h0.im, h0.re};
+      l0.re = mad(-s, h1.im, l0.re); l0.im = mad(s, h1.re, l0.im);
+      l1.re = mad(-s, h0.im, l1.re); l1.im = mad(s, h0.re, l1.im);
     } else if constexpr (MU == 1) { // A^+ h = (h1, -h0)
-      l0 = h1; l1 = {-h0.re, -h0.im};
+      l0.re = mad(s, h1.re, l0.re); l0.im = mad(s, h1.im, l0.im);
+      l1.re = mad(-s, h0.re, l1.re); l1.im = mad(-s, h0.im, l1.im);
     } else if constexpr (MU == 2) { // A^+ h = (i h0, -i h1)
-      l0 = {-h0.im, h0.re}; l1 = {h1.im, -h1.re};
+      l0.re = mad(-s, h0.im, l0.re); l0.im = mad(s, h0.re, l0.im);
+      l1.re = mad(s, h1.im, l1.re); l1.im = mad(-s, h1.re, l1.im);
     } else {                        // A^+ h = h
-      l0 = h0; l1 = h1;
-    }
-    if (FWD) {
-      acc.c[LO + c].re -= l0.re; acc.c[LO + c].im -= l0.im;
-      acc.c[LO + 3 + c].re -= l1.re; acc.c[LO + 3 + c].im -= l1.im;
-    } else {
-      acc.c[LO + c].re += l0.re; acc.c[LO + c].im += l0.im;
-      acc.c[LO + 3 + c].re += l1.re; acc.c[LO + 3 + c].im += l1.im;
+      l0.re = mad(s, h0.re, l0.re); l0.im = mad(s, h0.im, l0.im);
+      l1.re = mad(s, h1.re, l1.re); l1.im = mad(s, h1.im, l1.im);
     }
   }
 }
@@ -576,24 +640,51 @@ __device__ __forceinline__ void herm6_mv(const cpx<C> *m, const cpx<C> *x, cpx<C
   for (int i = 0; i < 6; i++)
 #pragma unroll
     for (int j = i + 1; j < 6; j++) {
-      cpx<C> a = m[herm_off(i, j)];
-      // y_i += a x_j ; y_j += conj(a) x_i
-      y[i].re += a.re * x[j].re - a.im * x[j].im;
-      y[i].im += a.re * x[j].im + a.im * x[j].re;
-      y[j].re += a.re * x[i].re + a.im * x[i].im;
-      y[j].im += a.re * x[i].im - a.im * x[i].re;
+      const cpx<C> a = m[herm_off(i, j)];
+      cmac(y[i], a, x[j]);    // y_i += a x_j
+      cmacc(y[j], a, x[i]);   // y_j += conj(a) x_i
     }
+}
+
+// Chirality block h (18 pairs) of site s from a chunked clover tile whose
+// first pair is at tile (n sites per tile; see clover_slot); h may be a
+// run-time value. LDG: read through the read-only path (global memory only).
+template <bool LDG, typename C, typename P>
+__device__ __forceinline__ void clover_block_chunked(const P *tile, size_t n, int s, int h, cpx<C> *m) {
+  constexpr int CP = chunk_pairs<P>();
+  DD_CHECK_INDEX(s, n);
+  DD_CHECK_INDEX(h, 2);
+  const uint4 *q = (const uint4 *)tile + s;   // chunk c of site s at q[c * n]
+  auto ld4 = [](const uint4 *a) { if constexpr (LDG) return __ldg(a); else return *a; };
+  auto ld2 = [](const uint2 *a) { if constexpr (LDG) return __ldg(a); else return *a; };
+  if constexpr (CP == 4) {
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const uint4 v = ld4(q + (size_t)(4 * h + c) * n);
+      const P *pv = (const P *)&v;
+#pragma unroll
+      for (int k = 0; k < 4; k++) m[4 * c + k] = from_pair<C, P>(pv[k]);
+    }
+    const uint2 w = ld2((const uint2 *)(q + (size_t)8 * n) + h);
+    const P *pw = (const P *)&w;
+    m[16] = from_pair<C, P>(pw[0]);
+    m[17] = from_pair<C, P>(pw[1]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 18 / CP; c++) {
+      const uint4 v = ld4(q + (size_t)((18 / CP) * h + c) * n);
+      const P *pv = (const P *)&v;
+#pragma unroll
+      for (int k = 0; k < CP; k++) m[CP * c + k] = from_pair<C, P>(pv[k]);
+    }
+  }
 }
 
 template <typename S, typename C>
 __device__ __forceinline__ void load_clover_block(const void *clov, size_t tile_sites, int b, int s, int h,
                                                   cpx<C> *m) {
-  DD_CHECK_INDEX(s, tile_sites);
-  DD_CHECK_INDEX(h, 2);
   using P = typename Store<S>::pair_t;
-  const P *base = (const P *)clov + ((size_t)b * 36 + 18 * h) * tile_sites + s;
-#pragma unroll
-  for (int i = 0; i < 18; i++) m[i] = from_pair<C, P>(__ldg(base + (size_t)i * tile_sites));
+  clover_block_chunked<true, C, P>((const P *)clov + (size_t)b * 36 * tile_sites, tile_sites, s, h, m);
 }
 
 // out = A psi for a full site (both chirality blocks)
@@ -633,8 +724,8 @@ struct OpFields {
   // shared memory, where the rebuild would cost more issue slots than the
   // bytes it saves); the same array as `links` for FP64
   void *links_full = nullptr;
-  void *clov = nullptr;   // A, [nblocks][36][Vb] pairs
-  void *cinv = nullptr;   // A^-1 on even sites, [nblocks][36][Vh] pairs
+  void *clov = nullptr;   // A, chunked tiles of 36 pairs x Vb sites per block (clover_slot)
+  void *cinv = nullptr;   // A^-1 on even sites, chunked tiles of 36 pairs x Vh sites
 };
 
 struct Op {
@@ -693,7 +784,8 @@ int launch_load_clover(const Geom &g, const double *A_canon, double *clov64, dou
                        cudaStream_t st);
 int launch_build_clover(const Geom &g, const double *links_canon, double c_sw, double m0, double *clov64,
                         double *cinv64, int *bad, cudaStream_t st);
-int launch_convert_pairs(int prec, const double *in, void *out, size_t npairs, cudaStream_t st);
+// FP64 clover tiles ([tile][36][n] pairs) -> chunked tiles of `prec`
+int launch_convert_clover(int prec, const double *in, void *out, size_t ntiles, int n, cudaStream_t st);
 int launch_dirac(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st);
 int launch_dirac(const Geom &g, const OpFields &f, const void *in, void *out, int nrhs, cudaStream_t st);
 // y = D x with double-float fields (f = op->fdf) and double-float inputs p.in

@@ -84,7 +84,9 @@ __device__ __noinline__ void wait_expired(unsigned *timeouts, unsigned mbar, uns
   }
 }
 
-// Strided view of one block's pair tile: element (i, site) at p[i * stride + site].
+// Strided view of one block's pair tile: pair-major (the links: element
+// (i, site) at p[i * stride + site]) or chunked (the clover: see
+// clover_block_chunked, stride = sites per chunk row).
 template <typename P> struct Tile {
   const P *p;
   int stride;
@@ -98,12 +100,10 @@ __device__ __forceinline__ void tile_link(const Tile<P> &t, int s, int mu, Link<
 #pragma unroll
   for (int i = 0; i < 9; i++) u.m[i] = from_pair<C, P>(t.p[(9 * mu + i) * t.stride + s]);
 }
+// chirality block h of site s of a chunked clover tile (shared or global memory)
 template <typename C, typename P>
 __device__ __forceinline__ void tile_block(const Tile<P> &t, int s, int h, cpx<C> *m) {
-  DD_CHECK_INDEX(s, t.stride);
-  DD_CHECK_INDEX(h, 2);
-#pragma unroll
-  for (int i = 0; i < 18; i++) m[i] = from_pair<C, P>(t.p[(18 * h + i) * t.stride + s]);
+  clover_block_chunked<false, C, P>(t.p, (size_t)t.stride, s, h, m);
 }
 
 // shared-memory vector: [12][Vh] complex, one parity of the block
@@ -188,13 +188,13 @@ __device__ __forceinline__ void hop_global_dir(const Geom &g, const Site &t, con
   neighbour(g, t, MU, +1, &nb, &ns, &sg, &inside);
   if (inside ? !self_zero : !halo_zero) {
     load_spinor<S, C>(x, g, nb, ns, psi);
-    load_link<S, C, 9>(links, g, t.b, t.s, MU, u);
+    load_link<S, C, 9, false>(links, g, t.b, t.s, MU, u);
     hop<MU, true, C, SW>(acc, u, psi, (C)(-0.5f * sg));
   }
   neighbour(g, t, MU, -1, &nb, &ns, &sg, &inside);
   if (inside ? !self_zero : !halo_zero) {
     load_spinor<S, C>(x, g, nb, ns, psi);
-    load_link<S, C, 9>(links, g, nb, ns, MU, u);
+    load_link<S, C, 9, false>(links, g, nb, ns, MU, u);
     hop<MU, false, C, SW>(acc, u, psi, (C)(-0.5f * sg));
   }
 }
@@ -352,23 +352,25 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
 
   // Staging by bulk copies (the TMA engine), issued by thread 0 and tracked
   // by the mbarrier: the links tile (LT x Vb pairs, contiguous per block),
-  // and for STAGE 1 the odd half of every clover row (36 pieces of Vh pairs)
-  // and the even-site inverse tile (36 x Vh, contiguous). Every size is a
-  // multiple of 16 bytes (Vh is even) and every address 16-byte aligned.
+  // and for STAGE 1 the odd half of every clover chunk row (36 / CP pieces of
+  // Vh chunks) and the even-site inverse tile (contiguous). Every size is a
+  // multiple of 16 bytes and every address 16-byte aligned.
   Tile<P> Lt, Ao, Ai;
   if constexpr (STAGE == 1) {
     P *sl = (P *)tiles;
     P *sa = sl + (size_t)LT * Vb;
     P *si = sa + (size_t)36 * Vh;
     if (threadIdx.x == 0) {
+      constexpr int CP = chunk_pairs<P>();
       const P *gl = (const P *)links + (size_t)b * LT * Vb;
       const P *ga = (const P *)clov + (size_t)b * 36 * Vb;
-      const unsigned lb = (unsigned)LT * Vb * sizeof(P), rb = (unsigned)(Vh * sizeof(P));
+      const unsigned lb = (unsigned)LT * Vb * sizeof(P), rb = (unsigned)(Vh * 16);
       fence_proxy_async();
-      mbar_arrive_expect(mbar, lb + 72u * rb);
+      mbar_arrive_expect(mbar, lb + 2u * (36 / CP) * rb);
       bulk_g2s(sl, gl, lb, mbar);
-      for (int i = 0; i < 36; i++) bulk_g2s(sa + (size_t)i * Vh, ga + (size_t)i * Vb + Vh, rb, mbar);
-      bulk_g2s(si, (const P *)cinv + (size_t)b * 36 * Vh, 36u * rb, mbar);
+      for (int c = 0; c < 36 / CP; c++)
+        bulk_g2s(sa + (size_t)c * Vh * CP, ga + ((size_t)c * Vb + Vh) * CP, rb, mbar);
+      bulk_g2s(si, (const P *)cinv + (size_t)b * 36 * Vh, (36u / CP) * rb, mbar);
     }
     Lt = {sl, Vb};
     Ao = {sa, Vh};
@@ -382,11 +384,11 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
       bulk_g2s(sl, (const P *)links + (size_t)b * LT * Vb, lb, mbar);
     }
     Lt = {sl, Vb};
-    Ao = {(const P *)clov + (size_t)b * 36 * Vb + Vh, Vb};
+    Ao = {(const P *)clov + (size_t)b * 36 * Vb + (size_t)Vh * chunk_pairs<P>(), Vb};
     Ai = {(const P *)cinv + (size_t)b * 36 * Vh, Vh};
   } else {
     Lt = {(const P *)links + (size_t)b * LT * Vb, Vb};
-    Ao = {(const P *)clov + (size_t)b * 36 * Vb + Vh, Vb};
+    Ao = {(const P *)clov + (size_t)b * 36 * Vb + (size_t)Vh * chunk_pairs<P>(), Vb};
     Ai = {(const P *)cinv + (size_t)b * 36 * Vh, Vh};
   }
 

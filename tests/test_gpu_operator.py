@@ -161,3 +161,59 @@ def test_apply_D_double_float_matches_oracle(nrhs):
     with pytest.raises(dd.DDError):
         s64.op.apply_D(dd.F64_DF, f, s64.lat.new_field(dd.F64))
     s64.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(dd.F32, 1e-6), (dd.F16, 2e-3), (dd.BF16, 2e-2)])
+def test_links_rebuilt_third_row(prec, tol):
+    """The Dslash fields of 32- and 16-bit operators store two rows of each
+    SU(3) link and rebuild the third as conj(row0 x row1). A point source
+    psi = delta(n + mu) e_{spin 0, colour c} gives, at site n, the spin-0
+    entries -1/2 U_mu(n)[a][c] (the forward hop; gamma_mu has no diagonal
+    entry in the chiral basis; times -1 across the antiperiodic time edge):
+    every column of U_mu(n), including the rebuilt row, against the FP64
+    input link."""
+    import torch
+    dims = (8, 8, 8, 8)
+    s = Setup(dims, (4, 4, 4, 4), eps=0.3, n_stout=1, prec=prec, seed=31)
+    L = {0: dims[3], 1: dims[2], 2: dims[1], 3: dims[0]}   # extent by direction (x, y, z, t)
+
+    def site(c):   # canonical index of coordinates (x, y, z, t)
+        return c[0] + dims[3] * (c[1] + dims[2] * (c[2] + dims[1] * c[3]))
+
+    worst = 0.0
+    for n_c in ((1, 2, 3, 4), (3, 0, 5, 7)):
+        n = site(n_c)
+        for mu in range(4):
+            m_c = list(n_c)
+            m_c[mu] = (m_c[mu] + 1) % L[mu]
+            m = site(m_c)
+            for c in range(3):
+                psi = np.zeros((s.V, 4, 3), dtype=np.complex128)
+                psi[m, 0, c] = 1.0
+                fin, fout = s.lat.to_field(psi, prec), s.lat.new_field(prec)
+                s.op.apply_D(prec, fin, fout)
+                col = -2.0 * s.lat.from_field(fout, prec)[n, 0, :]
+                # a hop across the time edge carries the antiperiodic sign
+                sign = -1.0 if (mu == 3 and n_c[3] == L[3] - 1) else 1.0
+                want = sign * s.U[n, mu, :, c]
+                worst = max(worst, float(np.abs(col - want).max()))
+    torch.cuda.synchronize()
+    assert worst <= tol, worst
+    s.close()
+
+
+def test_non_su3_links_refused():
+    """Two-row link storage needs special unitary links: a gauge field with
+    one link multiplied by a phase (unitary, determinant != 1) is refused at
+    operator creation, for every storage precision."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge(dims, 0.3, 0, 0.1, seed=5)
+    U[17, 2] *= np.exp(0.5j)
+    lat = dd.Lattice(dims, (2, 2, 2, 2))
+    gauge = dd.Gauge(lat, U)
+    for prec in (dd.F64, dd.F32, dd.F16):
+        with pytest.raises(dd.DDError) as e:
+            dd.Op(gauge, 1.0, 0.1, prec)
+        assert e.value.code == -1 and "special unitary" in str(e.value)
+    gauge.close()
+    lat.close()
