@@ -649,6 +649,34 @@ MG = {"n_vectors": 16, "setup_iters": 6, "coarse_max_iter": 24, "coarse_tol": 0.
       "tv_seed": 7000}
 
 
+def run_oracle(args):
+    """The FP64 oracle's apply_D and one Schwarz sweep on the full 64 x 32^3
+    and 96 x 48^3 lattices of the benchmark and mixed-precision workloads, on
+    one host thread and on all host cores (OpenMP), with the host CPU named:
+    time, GB/s of algorithmic bytes (192 reals of 8 bytes per site for
+    apply_D) and GFlop/s of the sweep (9868 flops per site at 4 MR steps).
+    Needs about 80 GB of host memory for the 96 x 48^3 site matrices."""
+    import oracle
+    out = {"mode": "oracle", "cpu_model": cpu_model(), "cores": host_cores()}
+    for name in ("sap_fgmres_64x32^3_fp32", "sap_fgmres_96x48^3_mixed"):
+        wl = synth.WORKLOADS[name]
+        V = int(np.prod(wl["dims"]))
+        U, b = setup_problem(wl)
+        op, t_setup = oracle_operator(wl, U)
+        del U
+        res = {"dims_TZYX": list(wl["dims"]), "operator_setup_s": t_setup}
+        for threads in (host_cores(), 1):
+            it = oracle_iteration(wl, op, b, threads)
+            res[f"threads_{it['threads']}"] = {
+                "apply_D_s": it["apply_D_s"], "sweep_s": it["sweep_s"],
+                "dslash_GB/s": DSLASH_REALS * 8 * V / it["apply_D_s"] / 1e9,
+                "sweep_GFlop/s": sap_flops_per_site(wl["mr_steps"]) * V / it["sweep_s"] / 1e9}
+        out[name] = res
+        del op
+    oracle.set_threads(host_cores())
+    print(json.dumps(out), flush=True)
+
+
 def run_mma(args):
     """The tensor-core question for the 12-source link product: time the
     FP32 CUDA-core form, the warp-MMA form (FP16 operands, two
@@ -761,9 +789,7 @@ def run_serve(args):
         fi = [i for i, (d, _) in enumerate(fields) if d == sizes[size]][int(u[2 * nreq + k] * 8) % (3 if size < 2 else 2)]
         nrhs = 1 + int(u[3 * nreq + k] * 12) % 12
         mi = k % len(m0s)
-        V = int(np.prod(fields[fi][0]))
-        b = synth.gaussian(12 * V * nrhs, 1000 + k).reshape(nrhs, V, 4, 3)
-        reqs.append((arrivals[k], fi, mi, nrhs, b))
+        reqs.append((arrivals[k], fi, mi, nrhs, 1000 + k))
     for _, fi, mi, _, _ in reqs:   # resident operators before the stream starts
         op_for(fi, mi)
     srv = dd.Server(max_slots=8, max_batch_rhs=12)
@@ -776,16 +802,21 @@ def run_serve(args):
     srv = dd.Server(max_slots=8, max_batch_rhs=12)
     tickets = []
     t0 = time.perf_counter()
-    for at, fi, mi, nrhs, b in reqs:
+    for at, fi, mi, nrhs, seed in reqs:
         now = time.perf_counter() - t0
         if at > now:
             time.sleep(at - now)
+        # the right-hand sides are drawn at submission (the server copies them)
+        V = int(np.prod(fields[fi][0]))
+        b = synth.gaussian(12 * V * nrhs, seed).reshape(nrhs, V, 4, 3)
         tickets.append((srv.submit(op_for(fi, mi), b if nrhs > 1 else b[0]), nrhs))
+        del b
     worst, nrhs_done = 0.0, 0
     for t, nrhs in tickets:
         st, x, info = srv.wait(t, timeout=3600)
         if st != dd.DONE:
             raise RuntimeError(f"request {t} ended in state {st}")
+        del x
         worst = max(worst, max(i["true_rel_residual"] for i in info))
         nrhs_done += nrhs
     wall = time.perf_counter() - t0
@@ -823,11 +854,13 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the 96x48^3 FP16/BF16 kernel measurements")
     ap.add_argument("--outer-f64", action="store_true",
                     help="IEEE FP64 Krylov basis and true residual with a mixed-precision smoother")
-    ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "batched", "serve", "mg", "mma"],
+    ap.add_argument("--mode", default="bench",
+                    choices=["bench", "kernels", "batched", "serve", "mg", "mma", "oracle"],
                     help="kernels: short kernel loop for profiler captures; batched: the 24-source "
                          "48^3x96 workload; serve: the Poisson request stream; mg: two-level "
                          "preconditioner against SAP alone; mma: tensor-core link-product "
-                         "measurement (no contract line)")
+                         "measurement; oracle: the FP64 oracle's apply_D and sweep at 64x32^3 and "
+                         "96x48^3 on 1 thread and all cores (no contract line)")
     ap.add_argument("--requests", type=int, default=40, help="requests in --mode serve")
     ap.add_argument("--rate", type=float, default=200.0, help="offered requests/s in --mode serve")
     ap.add_argument("--solve-iters", type=int, default=20, help="iteration cap of the solve in --mode kernels")
@@ -846,6 +879,8 @@ def main():
         run_mg(args)
     elif args.mode == "mma":
         run_mma(args)
+    elif args.mode == "oracle":
+        run_oracle(args)
     elif args.impl == "reference":
         run_reference(args, rank)
     else:

@@ -206,6 +206,18 @@ typedef struct {
 int dd_sap_smooth(dd_op_t op, const dd_sap_params *p, const void *b_dev, void *x_dev, int nrhs,
                   void *stream);
 
+/* The Schwarz smoother of dd_sap_smooth for right-hand sides of several
+ * operators at once - on lattices of different sizes too - in one launch per
+ * colour phase (the batched form of Sec. 3.1's Schwarz method): operator k
+ * smooths nrhs[k] fields, contiguous from b[k] and x[k] (internal layout of
+ * its smoother precision). All operators need the same smoother precision
+ * and Schwarz block shape; 1 <= nops <= 8 and at most 64 right-hand sides in
+ * all (DD_EINVAL otherwise). Each right-hand side's result is the one
+ * dd_sap_smooth gives it. Asynchronous on `stream` (its work fields are
+ * stream-ordered allocations). */
+int dd_sap_smooth_multi(int nops, const dd_op_t *ops, const int *nrhs, const dd_sap_params *p,
+                        const void *const *b_dev, void *const *x_dev, void *stream);
+
 typedef struct {
   double tol;           /* target true relative residual ||b - D x|| / ||b||        */
   int restart;          /* FGMRES restart length m (1..64)                          */

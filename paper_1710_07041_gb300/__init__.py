@@ -104,6 +104,9 @@ EXPORTS = {
                     ctypes.c_void_p], ctypes.c_int),
     "dd_sap_smooth": ([ctypes.c_void_p, ctypes.POINTER(SapParams), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                        ctypes.c_void_p], ctypes.c_int),
+    "dd_sap_smooth_multi": ([ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(SapParams), ctypes.POINTER(ctypes.c_void_p),
+                             ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p], ctypes.c_int),
     "dd_solve": ([ctypes.c_void_p, ctypes.POINTER(SolveParams), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                   ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "dd_solve_noalloc": ([ctypes.c_void_p, ctypes.POINTER(SolveParams), ctypes.c_void_p, ctypes.c_void_p,
@@ -307,6 +310,20 @@ class Op(Handle):
         if rc != 0 and not (rc == -4 and not raise_on_notconv):
             _check(rc, "dd_solve")
         return x, [i.as_dict() for i in infos]
+
+
+def sap_smooth_multi(items, sweeps: int, mr_steps: int, x_is_zero: bool = True, rhs_tile: int = 0, stream=None):
+    """dd_sap_smooth_multi: items = [(op, b_field, x_field, nrhs), ...], the
+    Schwarz smoother of every operator's right-hand sides in one launch per
+    colour phase."""
+    n = len(items)
+    ops = (ctypes.c_void_p * n)(*[op.handle for op, _, _, _ in items])
+    nrhs = (ctypes.c_int * n)(*[int(k) for _, _, _, k in items])
+    bs = (ctypes.c_void_p * n)(*[_ptr(b).value for _, b, _, _ in items])
+    xs = (ctypes.c_void_p * n)(*[_ptr(x).value for _, _, x, _ in items])
+    p = SapParams(sweeps, mr_steps, int(bool(x_is_zero)), rhs_tile)
+    _check(lib().dd_sap_smooth_multi(n, ops, nrhs, ctypes.byref(p), bs, xs, _stream_ptr(stream)),
+           "dd_sap_smooth_multi")
 
 
 NOALLOC_SCRATCH_BYTES = 64 << 20

@@ -457,4 +457,50 @@ int dd_sap_smooth(dd_op_t opp, const dd_sap_params *p, const void *b, void *x, i
   return rc;
 }
 
+int dd_sap_smooth_multi(int nops, const dd_op_t *ops, const int *nrhs, const dd_sap_params *p,
+                        const void *const *b, void *const *x, void *stream) {
+  if (nops < 1 || nops > MAX_SAP_GROUPS || !ops || !nrhs || !p || !b || !x || p->sweeps < 1 || p->mr_steps < 0) {
+    set_error("dd_sap_smooth_multi: bad argument (1 <= nops <= %d)", MAX_SAP_GROUPS);
+    return DD_EINVAL;
+  }
+  SapLattice lats[MAX_SAP_GROUPS];
+  RhsPtrs rp;
+  rp.n = 0;
+  size_t aux_bytes = 0;
+  for (int k = 0; k < nops; k++) {
+    const Op *op = (const Op *)ops[k];
+    if (!op || op->magic != MAGIC_OP || nrhs[k] < 1 || !b[k] || !x[k] || b[k] == x[k] ||
+        rp.n + nrhs[k] > MAX_RHS) {
+      set_error("dd_sap_smooth_multi: bad operator %d or right-hand sides (at most %d in all)", k, MAX_RHS);
+      return DD_EINVAL;
+    }
+    const size_t fb = (size_t)op->lat->g.V * 24 * real_bytes(op->fp.prec);
+    for (int r = 0; r < nrhs[k]; r++, rp.n++) {
+      rp.in[rp.n] = (const char *)b[k] + r * fb;
+      rp.out[rp.n] = (char *)x[k] + r * fb;
+    }
+    lats[k] = SapLattice{op->lat->g, op->fp, nrhs[k]};
+    aux_bytes += 2 * (size_t)nrhs[k] * fb;
+  }
+  // work fields of the incremental colour residual, stream-ordered
+  cudaStream_t st = (cudaStream_t)stream;
+  char *aux = nullptr;
+  if (cudaMallocAsync((void **)&aux, aux_bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    aux = nullptr;
+  }
+  AuxPtrs ax{};
+  for (int k = 0, i = 0; aux && k < nops; k++) {
+    const size_t fb = (size_t)lats[k].g.V * 24 * real_bytes(lats[k].f.prec);
+    for (int r = 0; r < nrhs[k]; r++, i++) {
+      ax.e[i] = aux;
+      ax.r[i] = aux + fb;
+      aux += 2 * fb;
+    }
+  }
+  int rc = launch_sap_lattices(lats, nops, *p, rp, st, ax.e[0] ? &ax : nullptr);
+  if (ax.e[0]) cudaFreeAsync(ax.e[0], st);
+  return rc;
+}
+
 }  // extern "C"

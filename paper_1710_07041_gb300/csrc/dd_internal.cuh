@@ -794,6 +794,32 @@ int launch_dirac_df(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStre
 // n complex FP64 values -> double-float {hi, lo} pairs, same positions
 int launch_split_pairs(const double *in, void *out, size_t n, cudaStream_t st);
 // Schwarz sweeps; p.in = right-hand sides b, p.out = iterates x
+// One launch of the Schwarz kernel may cover the right-hand sides of several
+// lattices (operators) that share the block shape and storage precision:
+// group k is a lattice with its operator's fields and the right-hand sides
+// rhs0 .. rhs0 + nrhs - 1 of the launch's pointer arrays; its work items are
+// item0 .. item0 + (blocks / 2) x ceil(nrhs / tile) - 1.
+constexpr int MAX_SAP_GROUPS = 8;
+struct SapGroup {
+  Geom g;
+  const void *links, *clov, *cinv;
+  int rhs0, nrhs, item0;
+};
+struct SapGroups {
+  SapGroup grp[MAX_SAP_GROUPS];
+  int n, nitems;
+};
+// A lattice of a multi-lattice smoother launch: geometry, operator fields of
+// the smoother precision, and its number of right-hand sides (consecutive in
+// the launch's pointer arrays, in the order of the lattices).
+struct SapLattice {
+  Geom g;
+  OpFields f;
+  int nrhs;
+};
+int launch_sap_lattices(const SapLattice *lats, int nlat, const dd_sap_params &sp, const RhsPtrs &p,
+                        cudaStream_t st, const AuxPtrs *aux);
+
 // aux (may be null): work fields for the incremental colour residual, one
 // pair per right-hand side of p; without them every phase recomputes
 // r = b - D x from x

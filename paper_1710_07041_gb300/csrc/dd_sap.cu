@@ -76,13 +76,13 @@ unsigned *sap_timeout_counter() {
   return (unsigned *)p;
 }
 
-int sap_run_f64(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp,
+int sap_run_f64(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp,
                 const AuxPtrs *ax, cudaStream_t st);
-int sap_run_f32(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp,
+int sap_run_f32(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp,
                 const AuxPtrs *ax, cudaStream_t st);
-int sap_run_f16(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp,
+int sap_run_f16(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp,
                 const AuxPtrs *ax, cudaStream_t st);
-int sap_run_bf16(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp,
+int sap_run_bf16(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp,
                 const AuxPtrs *ax, cudaStream_t st);
 
 namespace {
@@ -124,17 +124,16 @@ struct GraphCache {
 };
 static GraphCache g_graphs;
 
-int sap_launch_as_graph(const std::string &key, int variant, int nkernels, const OpFields &f, const RhsPtrs &rp,
-                        const AuxPtrs *ax, const std::function<int()> &enqueue, cudaStream_t st) {
+int sap_launch_as_graph(const std::string &key, int variant, int nkernels, const RhsPtrs &rp, const AuxPtrs *ax,
+                        const std::function<int()> &enqueue, cudaStream_t st) {
   const char *env = getenv("DD_SAP_GRAPHS");
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cap);
   if ((env && env[0] == '0') || cap != cudaStreamCaptureStatusNone || st == 0 || direct_launch()) return enqueue();
   // every pointer baked into the captured launches is part of the key (a
   // graph may only be replayed where a fresh capture would record the same
-  // arguments; the caller's key holds the geometry)
-  std::string k = key + "|v" + std::to_string(variant) + "|" + std::to_string((uintptr_t)f.links_full) + "," +
-                  std::to_string((uintptr_t)f.clov) + "," + std::to_string((uintptr_t)f.cinv);
+  // arguments; the caller's key holds the geometry and the operator fields)
+  std::string k = key + "|v" + std::to_string(variant);
   for (int i = 0; i < rp.n; i++) {
     k += "|" + std::to_string((uintptr_t)rp.in[i]) + ":" + std::to_string((uintptr_t)rp.out[i]);
     if (ax) k += ":" + std::to_string((uintptr_t)ax->e[i]) + ":" + std::to_string((uintptr_t)ax->r[i]);
@@ -222,7 +221,33 @@ int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const v
 
 int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st,
                const AuxPtrs *ax) {
+  const SapLattice L{g, f, rp.n};
+  return launch_sap_lattices(&L, 1, p, rp, st, ax);
+}
+
+int launch_sap_lattices(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp, cudaStream_t st,
+                        const AuxPtrs *ax) {
   NvtxRange range("dd:sap");
+  if (nl < 1 || nl > MAX_SAP_GROUPS) {
+    set_error("sap: 1..%d lattices per launch", MAX_SAP_GROUPS);
+    return DD_EINVAL;
+  }
+  int total = 0;
+  for (int k = 0; k < nl; k++) {
+    total += L[k].nrhs;
+    bool same = L[k].f.prec == L[0].f.prec && L[k].nrhs >= 1;
+    for (int mu = 0; mu < 4; mu++) same = same && L[k].g.bd[mu] == L[0].g.bd[mu];
+    if (!same) {
+      set_error("sap: the lattices of one launch need the same block shape and precision, and right-hand sides");
+      return DD_EINVAL;
+    }
+  }
+  if (total != rp.n) {
+    set_error("sap: %d right-hand sides given for %d in the lattices", rp.n, total);
+    return DD_EINVAL;
+  }
+  const Geom &g = L[0].g;
+  const OpFields &f = L[0].f;
   // DD_SAP_INCR=0: every phase forms r = b - D x from x (the incremental
   // colour residual is off even where work fields are given)
   static const bool incr_off = [] {
@@ -243,10 +268,10 @@ int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const R
     return DD_ECUDA;
   }
   switch (f.prec) {
-    case DD_F64: return sap_run_f64(g, f, p, rp, ax, st);
-    case DD_F32: return sap_run_f32(g, f, p, rp, ax, st);
-    case DD_F16: return sap_run_f16(g, f, p, rp, ax, st);
-    case DD_BF16: return sap_run_bf16(g, f, p, rp, ax, st);
+    case DD_F64: return sap_run_f64(L, nl, p, rp, ax, st);
+    case DD_F32: return sap_run_f32(L, nl, p, rp, ax, st);
+    case DD_F16: return sap_run_f16(L, nl, p, rp, ax, st);
+    case DD_BF16: return sap_run_bf16(L, nl, p, rp, ax, st);
   }
   set_error("sap: bad precision %d", f.prec);
   return DD_EINVAL;

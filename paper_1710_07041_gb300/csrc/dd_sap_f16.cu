@@ -2,8 +2,8 @@
 #include "dd_sap_kernels.cuh"
 
 namespace dd {
-int sap_run_f16(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp,
+int sap_run_f16(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp,
                 const AuxPtrs *ax, cudaStream_t st) {
-  return sap_variants<__half>(g, f, p, rp, ax, st);
+  return sap_variants<__half>(L, nl, p, rp, ax, st);
 }
 }  // namespace dd

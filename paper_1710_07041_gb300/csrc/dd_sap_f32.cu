@@ -2,8 +2,8 @@
 #include "dd_sap_kernels.cuh"
 
 namespace dd {
-int sap_run_f32(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp,
+int sap_run_f32(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp,
                 const AuxPtrs *ax, cudaStream_t st) {
-  return sap_variants<float>(g, f, p, rp, ax, st);
+  return sap_variants<float>(L, nl, p, rp, ax, st);
 }
 }  // namespace dd

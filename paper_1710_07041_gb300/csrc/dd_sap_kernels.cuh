@@ -14,8 +14,8 @@ namespace dd {
 // device counter of expired bounded waits (resolved before any capture)
 unsigned *sap_timeout_counter();
 // run `enqueue` (the launches of one smoother application) as a cached CUDA graph
-int sap_launch_as_graph(const std::string &key, int variant, int nkernels, const OpFields &f, const RhsPtrs &rp,
-                        const AuxPtrs *ax, const std::function<int()> &enqueue, cudaStream_t st);
+int sap_launch_as_graph(const std::string &key, int variant, int nkernels, const RhsPtrs &rp, const AuxPtrs *ax,
+                        const std::function<int()> &enqueue, cudaStream_t st);
 
 // Residual modes of one colour phase (bit set `mode` of k_sap_phase).
 // Without SAP_INCR the phase forms r = b - D x on its blocks from x (b and x
@@ -289,23 +289,38 @@ template <typename S> struct SapSmem {
   }
 };
 
+// The group of work item `item` (groups in item order).
+__device__ __forceinline__ int sap_group_of(const SapGroups &G, int item) {
+  int k = 0;
+#pragma unroll 1
+  while (k + 1 < G.n && item >= G.grp[k + 1].item0) k++;
+  return k;
+}
+// the i-th block of colour `colour`: blocks 2i and 2i+1 differ in colour
+__device__ __forceinline__ int sap_block_of(const Geom &g, int colour, int bi) {
+  int bb = 2 * bi, bc[4];
+  block_coords(g, bb, bc);
+  return (((bc[0] + bc[1] + bc[2] + bc[3]) & 1) != colour) ? bb + 1 : bb;
+}
+
 // STAGE: 0 operator tiles read through L1/L2; 1 links, A_oo and A_ee^-1 staged
 // in shared memory; 2 links staged, the clover blocks (each read by one
 // thread only) through L1/L2, which halves the footprint. UNROLL (specialised
 // shapes only): the MR loop's even and odd half-steps as separate code.
-template <typename S, int STAGE, int MINB, int NT, int SHAPE, bool UNROLL = false>
-__global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *__restrict__ links,
-                                                   const void *__restrict__ clov, const void *__restrict__ cinv,
-                                                   const RhsPtrs rp, const AuxPtrs ax, int colour, int self_zero,
-                                                   int halo_zero, int mode, int nmr, int tile, unsigned *timeouts) {
+// MULTI: the launch covers several lattice groups (without it, group 0 only,
+// whose fields the compiler reads at constant offsets).
+template <typename S, int STAGE, int MINB, int NT, int SHAPE, bool UNROLL = false, bool MULTI = false>
+__global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const RhsPtrs rp, const AuxPtrs ax,
+                                                   int colour, int self_zero, int halo_zero, int mode, int nmr,
+                                                   int tile, unsigned *timeouts) {
   using C = typename Store<S>::comp_t;
   using P = typename Store<S>::pair_t;
   constexpr int LT = SapSmem<S>::LT;   // pairs per site of the links tile
   // a specialised shape is launched with one thread per site: blockDim.x == NT
   static_assert(SHAPE == 0 || (SHAPE == 1 && NT == 256) || (SHAPE == 2 && NT == 512), "shape / threads");
   extern __shared__ __align__(16) unsigned char smem[];
-  const Geom g = block_shape<SHAPE>(g_in);
-  const int Vh = g.Vh, Vb = g.Vb;
+  // every group of a launch has the same block shape (checked on the host)
+  const int Vh = block_shape<SHAPE>(G.grp[0].g).Vh, Vb = block_shape<SHAPE>(G.grp[0].g).Vb;
   const int h = threadIdx.x / Vh, j = threadIdx.x - h * Vh;
 
   cpx<C> *rho = (cpx<C> *)smem;   // MR residual on odd sites (then e_o)
@@ -321,32 +336,38 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
   }
   const unsigned mbar_s = smem_u32(mbar);
 
-  // Work items: (block of this colour, right-hand-side tile), block fastest.
-  // A CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...; while it works
+  // Work items: (lattice group, block of this colour, right-hand-side tile),
+  // block fastest within a group; group k holds items G.grp[k].item0 ... A
+  // CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...; while it works
   // on one, the next one's operator tiles and fields are prefetched into L2.
-  const int nbc = g.nblocks / 2;
-  const int nitems = nbc * ((rp.n + tile - 1) / tile);
-  // the i-th block of this colour: blocks 2i and 2i+1 differ in colour
-  auto block_of = [&](int bi) {
-    int bb = 2 * bi, bc[4];
-    block_coords(g, bb, bc);
-    return (((bc[0] + bc[1] + bc[2] + bc[3]) & 1) != colour) ? bb + 1 : bb;
-  };
+  // one lattice: its geometry and fields once, outside the item loop
+  const Geom g0 = block_shape<SHAPE>(G.grp[0].g);
 #pragma unroll 1
-  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-  const int b = block_of(item % nbc), rt = item / nbc;
-  if (threadIdx.x == 0 && item + (int)gridDim.x < nitems) {
-    const int nitem = item + gridDim.x, nb = block_of(nitem % nbc), nrt = nitem / nbc;
-    prefetch_l2((const P *)links + (size_t)nb * LT * Vb, (unsigned)LT * Vb * sizeof(P));
-    prefetch_l2((const P *)clov + (size_t)nb * 36 * Vb, 36u * Vb * sizeof(P));
-    prefetch_l2((const P *)cinv + (size_t)nb * 36 * Vh, 36u * Vh * sizeof(P));
+  for (int item = blockIdx.x; item < G.nitems; item += gridDim.x) {
+  const int k = MULTI ? sap_group_of(G, item) : 0;
+  const Geom g = MULTI ? block_shape<SHAPE>(G.grp[k].g) : g0;
+  const void *__restrict__ links = G.grp[k].links;
+  const void *__restrict__ clov = G.grp[k].clov;
+  const void *__restrict__ cinv = G.grp[k].cinv;
+  const int nbc = g.nblocks / 2, rhs0 = MULTI ? G.grp[k].rhs0 : 0, nrhs = MULTI ? G.grp[k].nrhs : rp.n;
+  const int loc = MULTI ? item - G.grp[k].item0 : item;
+  const int b = sap_block_of(g, colour, loc % nbc), rt = loc / nbc;
+  if (threadIdx.x == 0 && item + (int)gridDim.x < G.nitems) {
+    const int nitem = item + gridDim.x, nk = MULTI ? sap_group_of(G, nitem) : 0;
+    const Geom ng = MULTI ? block_shape<SHAPE>(G.grp[nk].g) : g0;
+    const int nnbc = ng.nblocks / 2, nloc = MULTI ? nitem - G.grp[nk].item0 : nitem;
+    const int nb = sap_block_of(ng, colour, nloc % nnbc), nrt = nloc / nnbc;
+    prefetch_l2((const P *)G.grp[nk].links + (size_t)nb * LT * Vb, (unsigned)LT * Vb * sizeof(P));
+    prefetch_l2((const P *)G.grp[nk].clov + (size_t)nb * 36 * Vb, 36u * Vb * sizeof(P));
+    prefetch_l2((const P *)G.grp[nk].cinv + (size_t)nb * 36 * Vh, 36u * Vh * sizeof(P));
     constexpr int NC = spinor_chunks<S>();
+    const int nrhs0 = MULTI ? G.grp[nk].rhs0 : 0, nnrhs = MULTI ? G.grp[nk].nrhs : rp.n;
     for (int q = 0; q < tile; q++) {
       const int r = nrt * tile + q;
-      if (r >= rp.n) break;
+      if (r >= nnrhs) break;
       const size_t off = (size_t)nb * NC * Vb * 16;
-      prefetch_l2((const char *)rp.in[r] + off, NC * Vb * 16u);
-      if (!self_zero) prefetch_l2((const char *)rp.out[r] + off, NC * Vb * 16u);
+      prefetch_l2((const char *)rp.in[nrhs0 + r] + off, NC * Vb * 16u);
+      if (!self_zero) prefetch_l2((const char *)rp.out[nrhs0 + r] + off, NC * Vb * 16u);
     }
   }
 
@@ -397,8 +418,8 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
   // right-hand sides blockIdx.y * tile ... share the staged tiles
 #pragma unroll 1
   for (int rr = 0; rr < tile; rr++) {
-    const int r = rt * tile + rr;
-    if (r >= rp.n) break;
+    if (rt * tile + rr >= nrhs) break;
+    const int r = rhs0 + rt * tile + rr;
     const void *bf = rp.in[r];
     void *xf = rp.out[r];
     cpx<C> r_e[6], r_o[6];
@@ -653,11 +674,16 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(Geom g_in, const void *_
   }  // work items
 }
 
-template <typename S, int STAGE, int MINB, int NT, int SHAPE, bool UNROLL = false>
-int sap_k(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, const AuxPtrs *ax, int tile,
+template <typename S, int STAGE, int MINB, int NT, int SHAPE, bool UNROLL = false, bool MULTI = false>
+int sap_k(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp, const AuxPtrs *ax, int tile,
           bool persistent, cudaStream_t st) {
+  if (nl > 1 && !MULTI) {
+    set_error("sap: this launch variant covers one lattice");
+    return DD_EINVAL;
+  }
+  const Geom &g = L[0].g;   // every lattice of the launch has this block shape
   size_t smem = SapSmem<S>::bytes(g, STAGE);
-  auto kern = k_sap_phase<S, STAGE, MINB, NT, SHAPE, UNROLL>;
+  auto kern = k_sap_phase<S, STAGE, MINB, NT, SHAPE, UNROLL, MULTI>;
   // raise the kernel's dynamic shared-memory limit once (never during a capture)
   static std::mutex mu;
   static int raised = 0;
@@ -668,7 +694,15 @@ int sap_k(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtr
       raised = 227 * 1024;
     }
   }
-  const int nitems = g.nblocks / 2 * ((rp.n + tile - 1) / tile);
+  SapGroups G{};
+  G.n = nl;
+  int nitems = 0;
+  for (int k = 0, rhs0 = 0; k < nl; k++) {
+    G.grp[k] = SapGroup{L[k].g, L[k].f.links_full, L[k].f.clov, L[k].f.cinv, rhs0, L[k].nrhs, nitems};
+    nitems += L[k].g.nblocks / 2 * ((L[k].nrhs + tile - 1) / tile);
+    rhs0 += L[k].nrhs;
+  }
+  G.nitems = nitems;
   int grid = nitems;
   if (persistent) {
     int dev = 0, sms = 0, occ = 0;
@@ -697,8 +731,8 @@ int sap_k(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtr
         if (!(sw == p.sweeps - 1 && colour == 1)) mode |= SAP_WRITE_E;
         if (sw + 1 < p.sweeps) mode |= SAP_WRITE_R;
       }
-      kern<<<grid, g.Vb, smem, st>>>(g, f.links_full, f.clov, f.cinv, rp, ax ? *ax : none, colour, self_zero, halo_zero,
-                                     mode, p.mr_steps, tile, sap_timeout_counter());
+      kern<<<grid, g.Vb, smem, st>>>(G, rp, ax ? *ax : none, colour, self_zero, halo_zero, mode, p.mr_steps, tile,
+                                     sap_timeout_counter());
       DD_LAUNCHED();
     }
   return DD_OK;
@@ -706,22 +740,25 @@ int sap_k(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtr
 
 // the kernel specialised for the lattice's block shape when there is one
 template <typename S, int STAGE, int MINB, int NT = 256>
-int sap_t(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, const AuxPtrs *ax, int tile,
+int sap_t(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp, const AuxPtrs *ax, int tile,
           bool persistent, cudaStream_t st) {
   constexpr int SH = NT == 256 ? 1 : 2;   // the shape this thread count fits
-  if (shape_of(g) == SH) return sap_k<S, STAGE, MINB, NT, SH>(g, f, p, rp, ax, tile, persistent, st);
-  return sap_k<S, STAGE, MINB, NT, 0>(g, f, p, rp, ax, tile, persistent, st);
+  if (shape_of(L[0].g) == SH)
+    return nl > 1 ? sap_k<S, STAGE, MINB, NT, SH, false, true>(L, nl, p, rp, ax, tile, persistent, st)
+                  : sap_k<S, STAGE, MINB, NT, SH>(L, nl, p, rp, ax, tile, persistent, st);
+  return nl > 1 ? sap_k<S, STAGE, MINB, NT, 0, false, true>(L, nl, p, rp, ax, tile, persistent, st)
+                : sap_k<S, STAGE, MINB, NT, 0>(L, nl, p, rp, ax, tile, persistent, st);
 }
 // the MR loop unrolled by parity (specialised shape only)
 template <typename S, int STAGE, int MINB, int NT = 256>
-int sap_u(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, const AuxPtrs *ax, int tile,
+int sap_u(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp, const AuxPtrs *ax, int tile,
           bool persistent, cudaStream_t st) {
   constexpr int SH = NT == 256 ? 1 : 2;
-  if (shape_of(g) != SH) {
+  if (shape_of(L[0].g) != SH) {
     set_error("sap: the unrolled MR loop exists for the specialised block shapes only");
     return DD_EINVAL;
   }
-  return sap_k<S, STAGE, MINB, NT, SH, true>(g, f, p, rp, ax, tile, persistent, st);
+  return sap_k<S, STAGE, MINB, NT, SH, true>(L, nl, p, rp, ax, tile, persistent, st);
 }
 
 template <typename S> constexpr bool sixteen_bit() { return Store<S>::prec == DD_F16 || Store<S>::prec == DD_BF16; }
@@ -735,8 +772,9 @@ template <typename S> constexpr bool sixteen_bit() { return Store<S>::prec == DD
 // With several right-hand sides a CTA also solves `tile` of them with one
 // staging of its block's operator (rhs_tile; 0 lets the autotuner choose).
 template <typename S>
-int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const RhsPtrs &rp, const AuxPtrs *ax,
+int sap_variants(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp, const AuxPtrs *ax,
                  cudaStream_t st) {
+  const Geom &g = L[0].g;
   const size_t limit = 227 * 1024, half = 113 * 1024;
   const bool stage1 = SapSmem<S>::bytes(g, 1) <= limit;
   const bool stage2 = SapSmem<S>::bytes(g, 1) <= half;
@@ -746,21 +784,21 @@ int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const
     set_error("sap: block of %d sites needs more shared memory than available", g.Vb);
     return DD_EINVAL;
   }
-  int layouts[6], nl = 0;
+  int layouts[6], nlay = 0;
   if (g.Vb > 256) {
     // 512-site blocks (e.g. 8 x 4^3): 512 threads, one CTA per SM
-    layouts[nl++] = stage1 ? 3 : 4;
+    layouts[nlay++] = stage1 ? 3 : 4;
   } else {
-    if (stage1) layouts[nl++] = 0;
-    if (stage2) layouts[nl++] = 1;
-    if (links2) layouts[nl++] = 5;
-    if (nost2 || !stage1) layouts[nl++] = 2;
+    if (stage1) layouts[nlay++] = 0;
+    if (stage2) layouts[nlay++] = 1;
+    if (links2) layouts[nlay++] = 5;
+    if (nost2 || !stage1) layouts[nlay++] = 2;
     // 16-bit storage on the 4^4 shape with one right-hand side: the two-CTA
     // layouts also with the MR loop unrolled by parity (measured faster
     // there, slower in multi-source tiles and for FP32)
     if (sixteen_bit<S>() && shape_of(g) == 1 && rp.n == 1) {
-      if (stage2) layouts[nl++] = 6;
-      if (nost2 || !stage1) layouts[nl++] = 7;
+      if (stage2) layouts[nlay++] = 6;
+      if (nost2 || !stage1) layouts[nlay++] = 7;
     }
   }
   int tiles[6], nt = 0;
@@ -771,39 +809,62 @@ int sap_variants(const Geom &g, const OpFields &f, const dd_sap_params &p, const
     for (int c : cand)
       if (c <= rp.n) tiles[nt++] = c;
   }
-  // variant k: layout k % nl, RHS tile (k / nl) % nt, persistent grid if k >= nl * nt
+  // variant k: layout k % nlay, RHS tile (k / nlay) % nt, persistent grid if k >= nlay * nt
   auto run = [&](int k) {
-    const int layout = layouts[k % nl], tile = tiles[(k / nl) % nt];
-    const bool pers = k >= nl * nt;
+    const int layout = layouts[k % nlay], tile = tiles[(k / nlay) % nt];
+    const bool pers = k >= nlay * nt;
     switch (layout) {
-      case 1: return sap_t<S, 1, 2>(g, f, p, rp, ax, tile, pers, st);
-      case 2: return sap_t<S, 0, 2>(g, f, p, rp, ax, tile, pers, st);
-      case 3: return sap_t<S, 1, 1, 512>(g, f, p, rp, ax, tile, pers, st);
-      case 4: return sap_t<S, 0, 1, 512>(g, f, p, rp, ax, tile, pers, st);
-      case 5: return sap_t<S, 2, 2>(g, f, p, rp, ax, tile, pers, st);
+      case 1: return sap_t<S, 1, 2>(L, nl, p, rp, ax, tile, pers, st);
+      case 2: return sap_t<S, 0, 2>(L, nl, p, rp, ax, tile, pers, st);
+      case 3: return sap_t<S, 1, 1, 512>(L, nl, p, rp, ax, tile, pers, st);
+      case 4: return sap_t<S, 0, 1, 512>(L, nl, p, rp, ax, tile, pers, st);
+      case 5: return sap_t<S, 2, 2>(L, nl, p, rp, ax, tile, pers, st);
       case 6:
       case 7:
         if constexpr (sixteen_bit<S>()) {
-          if (layout == 6) return sap_u<S, 1, 2>(g, f, p, rp, ax, tile, pers, st);
-          return sap_u<S, 0, 2>(g, f, p, rp, ax, tile, pers, st);
+          if (layout == 6) return sap_u<S, 1, 2>(L, nl, p, rp, ax, tile, pers, st);
+          return sap_u<S, 0, 2>(L, nl, p, rp, ax, tile, pers, st);
         }
         return (int)DD_EINVAL;
-      default: return sap_t<S, 1, 1>(g, f, p, rp, ax, tile, pers, st);
+      default: return sap_t<S, 1, 1>(L, nl, p, rp, ax, tile, pers, st);
     }
   };
   int k = 0;
-  std::string key = tune_key("sap", g, f.prec, rp.n) + "|" + std::to_string(p.sweeps) + "," +
-                    std::to_string(p.mr_steps) + "," + std::to_string(p.rhs_tile) + "," +
-                    std::to_string(g.antiperiodic);
+  // the tuner's key: lattice, precision, right-hand-side count, smoother
+  // parameters and boundary; a launch over several lattices is tuned once
+  // per block shape, precision and total right-hand-side count (a served
+  // stream meets ever new mixes of lattices, each would otherwise be tuned)
+  std::string key;
+  if (nl == 1) {
+    key = tune_key("sap", g, L[0].f.prec, rp.n) + "|" + std::to_string(p.sweeps) + "," +
+          std::to_string(p.mr_steps) + "," + std::to_string(p.rhs_tile) + "," + std::to_string(g.antiperiodic);
+  } else {
+    Geom gb = g;   // the block shape only
+    for (int mu = 0; mu < 4; mu++) gb.L[mu] = 0;
+    key = tune_key("sap-lattices", gb, L[0].f.prec, rp.n) + "|" + std::to_string(p.sweeps) + "," +
+          std::to_string(p.mr_steps) + "," + std::to_string(p.rhs_tile);
+  }
+  // the graph cache's key adds every lattice's extents, boundary and right-hand sides
+  std::string shape;
+  for (int k = 0; k < nl; k++)
+    shape += "|" + std::to_string(L[k].g.L[0]) + "," + std::to_string(L[k].g.L[1]) + "," +
+             std::to_string(L[k].g.L[2]) + "," + std::to_string(L[k].g.L[3]) + "," + std::to_string(L[k].nrhs) + "," +
+             std::to_string(L[k].g.antiperiodic);
+  // a graph may only replay where a fresh capture records the same arguments:
+  // every lattice's field pointers are part of its key
+  std::string fields;
+  for (int k = 0; k < nl; k++)
+    fields += std::to_string((uintptr_t)L[k].f.links_full) + "," + std::to_string((uintptr_t)L[k].f.clov) + "," +
+              std::to_string((uintptr_t)L[k].f.cinv) + ";";
   // x is pure output when x_is_zero, so trial runs leave the same result
   if (p.x_is_zero) {
-    int rc = tuned_variant(key, 2 * nl * nt, run, st, &k);
+    int rc = tuned_variant(key, 2 * nlay * nt, run, st, &k);
     if (rc) return rc;
   } else {
     int c = tune_lookup(key);
     k = c >= 0 ? c : 0;
   }
-  return sap_launch_as_graph(key, k, 2 * p.sweeps, f, rp, ax, [&] { return run(k); }, st);
+  return sap_launch_as_graph(key + shape + "|" + fields, k, 2 * p.sweeps, rp, ax, [&] { return run(k); }, st);
 }
 
 }  // namespace

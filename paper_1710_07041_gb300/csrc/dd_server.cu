@@ -4,14 +4,23 @@
 // GB300 holds many lattices at once, so requests are served concurrently:
 //   * a scheduler thread admits queued requests while the device-memory
 //     budget and the worker count allow, FIFO;
-//   * requests on the same operator with the same solver parameters share a
-//     worker: one host thread, one CUDA stream and one BatchSolver whose
-//     slots hold individual right-hand sides;
+//   * requests with the same solver parameters on operators with the same
+//     smoother precision and Schwarz block shape share a worker - one host
+//     thread, one CUDA stream and one BatchSolver whose slots hold individual
+//     right-hand sides, on any of those operators and lattices: every
+//     Arnoldi step runs the Schwarz smoother of all its slots as one launch
+//     per colour phase, lattices of different sizes included (the two-level
+//     preconditioner keeps one operator per worker);
 //   * a slot retires its right-hand side as soon as it converges and takes
 //     the next waiting one at the following Arnoldi step, so requests that
 //     arrive while others run join the batch without waiting for it to end;
-//   * workers on different operators run on separate streams and overlap on
-//     the device; an idle worker frees its memory after a short grace time.
+//   * a request joins a compatible worker that has free slots for it, else a
+//     new worker starts (up to max_slots workers, which run on separate
+//     streams and overlap on the device), else the least loaded compatible
+//     worker queues it;
+//   * a worker reserves its slot count times the workspace of the largest
+//     lattice it has admitted; an idle worker frees its memory after a
+//     short grace time.
 // Each right-hand side's arithmetic does not depend on its batch mates, so a
 // result is the same alone and in any mix.
 #include <algorithm>
@@ -51,10 +60,11 @@ struct Server;
 
 struct Worker {
   Server *srv = nullptr;
-  Op *op = nullptr;
+  Op *op = nullptr;        // the operator of its first request (defines its class)
   dd_solve_params params{};
   int slots = 0;
-  size_t bytes = 0;
+  size_t per = 0;          // reserved device bytes per slot
+  size_t bytes = 0;        // slots x per
   cudaStream_t stream = nullptr;
   std::deque<Request *> queue;  // admitted requests with right-hand sides left to start
   std::thread th;
@@ -80,6 +90,14 @@ struct Server {
   clk::time_point t_first, t_last;
   bool any = false;
 };
+
+// whether a worker created for operator a can take right-hand sides on b
+static bool same_class(const Op *a, const Op *b, const dd_solve_params &p) {
+  if (p.mg) return a == b;
+  bool same = a->prec == b->prec;
+  for (int mu = 0; mu < 4; mu++) same = same && a->lat->g.bd[mu] == b->lat->g.bd[mu];
+  return same;
+}
 
 static bool same_params(const dd_solve_params &a, const dd_solve_params &b) {
   return a.tol == b.tol && a.restart == b.restart && a.max_iter == b.max_iter && a.sap.sweeps == b.sap.sweeps &&
@@ -132,6 +150,7 @@ static void worker_main(Worker *w) {
       int k = r->next_rhs++;
       r->state = DD_RUNNING;
       const size_t fs = (size_t)r->op->lat->g.V * 24;
+      job.op = r->op;
       job.b = r->b.data() + k * fs;
       job.x = r->x.data() + k * fs;
       job.b_on_device = job.x_on_device = 0;
@@ -209,14 +228,41 @@ static void scheduler_main(Server *srv) {
         continue;
       }
       Worker *target = nullptr;
-      for (auto &w : srv->workers)
-        if (!w->exited && w->op == r->op && same_params(w->params, r->params)) target = w.get();
+      const Geom &g = r->op->lat->g;
+      size_t per = BatchSolver::bytes_per_slot(g, r->op->prec, r->params.restart);
+      if (r->params.mg)
+        per += MgWork::bytes(g, r->op->prec, ((Mg *)r->params.mg)->N, ((Mg *)r->params.mg)->p.coarse_max_iter);
+      size_t room = srv->budget > srv->in_use ? srv->budget - srv->in_use : 0;
+      // a compatible worker with free slots for this request's right-hand
+      // sides takes it (its reservation grown to a larger lattice if the
+      // budget allows); otherwise a new worker starts while the worker count
+      // allows; otherwise the least loaded compatible worker queues it
+      auto pending_rhs = [](const Worker *w) {
+        int n = 0;
+        for (const Request *q : w->queue) n += q->nrhs - q->next_rhs;
+        return n;
+      };
+      auto take = [&](Worker *w) {
+        if (per <= w->per) return true;
+        const size_t extra = (size_t)w->slots * (per - w->per);
+        if (extra > room) return false;
+        srv->in_use += extra;   // a larger lattice: grow the worker's reservation to it
+        room -= extra;
+        w->bytes += extra;
+        w->per = per;
+        return true;
+      };
+      Worker *least = nullptr;
+      for (auto &w : srv->workers) {
+        if (w->exited || !same_class(w->op, r->op, r->params) || !same_params(w->params, r->params)) continue;
+        if (pending_rhs(w.get()) + r->nrhs <= w->slots && take(w.get())) {
+          target = w.get();
+          break;
+        }
+        if (!least || pending_rhs(w.get()) < pending_rhs(least)) least = w.get();
+      }
+      if (!target && (int)srv->workers.size() >= srv->p.max_slots && least && take(least)) target = least;
       if (!target && (int)srv->workers.size() < srv->p.max_slots) {
-        const Geom &g = r->op->lat->g;
-        size_t per = BatchSolver::bytes_per_slot(g, r->op->prec, r->params.restart);
-        if (r->params.mg)
-          per += MgWork::bytes(g, r->op->prec, ((Mg *)r->params.mg)->N, ((Mg *)r->params.mg)->p.coarse_max_iter);
-        size_t room = srv->budget > srv->in_use ? srv->budget - srv->in_use : 0;
         int slots = (int)std::min<size_t>((size_t)srv->p.max_batch_rhs, room / per);
         if (slots >= 1) {
           auto w = std::make_unique<Worker>();
@@ -224,6 +270,7 @@ static void scheduler_main(Server *srv) {
           w->op = r->op;
           w->params = r->params;
           w->slots = slots;
+          w->per = per;
           w->bytes = (size_t)slots * per;
           if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) == cudaSuccess) {
             srv->in_use += w->bytes;
@@ -234,6 +281,18 @@ static void scheduler_main(Server *srv) {
         }
       }
       if (target) {
+        // the solution buffer is allocated on admission (pending requests
+        // hold only their right-hand sides)
+        try {
+          r->x.assign((size_t)r->op->lat->g.V * 24 * r->nrhs, 0.0);
+        } catch (...) {
+          for (auto &i : r->info) i.status = DD_ENOMEM;
+          r->remaining = 1;
+          r->worst = DD_ENOMEM;
+          rhs_finished(srv, r, DD_ENOMEM);
+          it = srv->pending.erase(it);
+          continue;
+        }
         target->queue.push_back(r);
         it = srv->pending.erase(it);
         srv->cv.notify_all();
@@ -320,7 +379,6 @@ int dd_submit(dd_server_t sh, const dd_request *req, uint64_t *ticket) {
   const size_t fs = (size_t)g.V * 24;
   try {
     r->b.assign(req->b_host, req->b_host + fs * req->nrhs);
-    r->x.assign(fs * req->nrhs, 0.0);
     r->info.assign(req->nrhs, dd_solve_info{});
   } catch (...) {
     set_error("dd_submit: out of host memory");

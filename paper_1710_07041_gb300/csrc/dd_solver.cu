@@ -60,26 +60,68 @@ size_t BatchSolver::bytes_per_slot(const Geom &g, int prec, int m) {
 
 BatchSolver::BatchSolver(const Op *op, const dd_solve_params &p, int slots, cudaStream_t st)
     : op_(op), p_(p), st_(st), slots_(slots), caller_(st) {
-  const Geom &g = op->lat->g;
   zprec_ = op->prec == DD_F64 ? DD_F64 : DD_F32;
   // mixed precision keeps the Krylov basis in double-float (FP32 hi/lo pairs):
   // FP64-class accuracy at FP32 ALU rate; an FP64 operator keeps native FP64
   df_ = zprec_ == DD_F32 && !p.outer_f64;
-  f64_ = (size_t)g.V * 24 * 8;
-  fz_ = (size_t)g.V * 24 * real_bytes(zprec_);
-  fp_ = (size_t)g.V * 24 * real_bytes(op->prec);
-  sigma_ = std::sqrt(24.0 * (double)g.V);  // unit-norm vector -> unit RMS entries
 }
 
 // The device buffers of one slot with their sizes (allocation and release
 // walk the same list).
-std::vector<std::pair<void **, size_t>> BatchSolver::slot_buffers(Slot &s) const {
+std::vector<std::pair<void **, size_t>> BatchSolver::slot_buffers(Slot &s, long long V) const {
   const size_t m = (size_t)m_alloc_;
-  return {{(void **)&s.Vb, (m + 1) * f64_}, {(void **)&s.Z, m * fz_},   {(void **)&s.x, f64_},
-          {(void **)&s.b, f64_},           {(void **)&s.w, f64_},       {(void **)&s.canon, f64_},
-          {&s.tin, fp_},                   {&s.tout, fp_},              {&s.zt, fz_},
-          {&s.se, fp_},                    {&s.sr, fp_},
+  const size_t f64 = (size_t)V * 24 * 8, fz = (size_t)V * 24 * real_bytes(zprec_),
+               fp = (size_t)V * 24 * real_bytes(op_->prec);
+  return {{(void **)&s.Vb, (m + 1) * f64}, {(void **)&s.Z, m * fz},   {(void **)&s.x, f64},
+          {(void **)&s.b, f64},           {(void **)&s.w, f64},       {(void **)&s.canon, f64},
+          {&s.tin, fp},                   {&s.tout, fp},              {&s.zt, fz},
+          {&s.se, fp},                    {&s.sr, fp},
           {(void **)&s.sdev, sizeof(double) * (m + 1)}};
+}
+
+// Release slot s's field buffers (to the workspace cache, or to the device).
+int BatchSolver::free_slot(Slot &s) {
+  if (!s.vol) return DD_OK;
+  if (cache_) {
+    DD_CUDA(cudaStreamSynchronize(st_));   // queued work may still use them
+    for (auto &pb : slot_buffers(s, s.vol)) pool_dev_free(*pb.first, pb.second);
+  } else {
+    for (auto &pb : slot_buffers(s, s.vol))
+      if (*pb.first) cudaFree(*pb.first);
+  }
+  for (auto &pb : slot_buffers(s, s.vol)) *pb.first = nullptr;
+  s.vol = 0;
+  return DD_OK;
+}
+
+// Give slot s buffers for right-hand sides of op. Buffers only grow: a
+// lattice no larger than the slot's allocation reuses it (releasing device
+// memory synchronises the whole device, which would stall the other
+// workers' streams at every change of lattice).
+int BatchSolver::size_slot(Slot &s, const Op *op) {
+  bool same_shape = op->prec == op_->prec;
+  for (int mu = 0; mu < 4; mu++) same_shape = same_shape && op->lat->g.bd[mu] == op_->lat->g.bd[mu];
+  if (!same_shape || (p_.mg && op != op_)) {
+    set_error("solver: a batch mixes operators of different smoother precision or block shape");
+    return DD_EINVAL;
+  }
+  const Geom &g = op->lat->g;
+  s.op = op;
+  s.f64 = (size_t)g.V * 24 * 8;
+  s.fz = (size_t)g.V * 24 * real_bytes(zprec_);
+  s.fp = (size_t)g.V * 24 * real_bytes(op->prec);
+  s.sigma = std::sqrt(24.0 * (double)g.V);  // unit-norm vector -> unit RMS entries
+  if (s.vol >= g.V) return DD_OK;
+  int rc = free_slot(s);
+  if (rc) return rc;
+  s.vol = g.V;
+  for (auto &pb : slot_buffers(s, s.vol))
+    if (!(*pb.first = pool_dev_alloc(pb.second))) {
+      set_error("solver: out of device memory for an FGMRES(%d) slot (%zu bytes)", m_alloc_,
+                bytes_per_slot(g, op->prec, m_alloc_));
+      return DD_ENOMEM;
+    }
+  return DD_OK;
 }
 
 BatchSolver::~BatchSolver() {
@@ -88,7 +130,8 @@ BatchSolver::~BatchSolver() {
     cudaStreamSynchronize(st_);
     const size_t n = slots_.size();
     for (auto &s : slots_)
-      for (auto &pb : slot_buffers(s)) pool_dev_free(*pb.first, pb.second);
+      if (s.vol)
+        for (auto &pb : slot_buffers(s, s.vol)) pool_dev_free(*pb.first, pb.second);
     pool_dev_free(hdev_, sizeof(double) * HSTRIDE * n);
     pool_dev_free(ydev_, sizeof(double) * 2 * 64 * n);
     pool_host_free(hpin_, sizeof(double) * HSTRIDE * n);
@@ -96,8 +139,9 @@ BatchSolver::~BatchSolver() {
     blas_.release_to_pool();
   } else {
     for (auto &s : slots_)
-      for (auto &pb : slot_buffers(s))
-        if (*pb.first) cudaFree(*pb.first);
+      if (s.vol)
+        for (auto &pb : slot_buffers(s, s.vol))
+          if (*pb.first) cudaFree(*pb.first);
     if (hdev_) cudaFree(hdev_);
     if (ydev_) cudaFree(ydev_);
     if (hpin_) cudaFreeHost(hpin_);
@@ -117,15 +161,14 @@ int BatchSolver::init() {
     return DD_EINVAL;
   }
   for (auto &s : slots_) {
-    bool ok = true;
-    for (auto &pb : slot_buffers(s))
-      if (ok) ok = (*pb.first = pool_dev_alloc(pb.second)) != nullptr;
+    // buffers for the solver's own operator up front (a slot is resized when
+    // it takes a right-hand side on a lattice of another volume)
+    int rc = size_slot(s, op_);
     s.scl.assign(m + 1, 1.0);
-    if (!ok) {
+    if (rc == DD_ENOMEM)
       set_error("solver: out of device memory for %d FGMRES(%d) slots (%zu bytes each)", n, m,
                 bytes_per_slot(op_->lat->g, op_->prec, m));
-      return DD_ENOMEM;
-    }
+    if (rc) return rc;
     if (p_.mg) {
       s.mgw = new (std::nothrow) MgWork;
       int rc = s.mgw ? s.mgw->init((const Mg *)p_.mg) : DD_ENOMEM;
@@ -165,8 +208,10 @@ int BatchSolver::sync_h() {
 
 // Load a job into a slot: b and x0 into the FP64 field layout.
 int BatchSolver::start(Slot &s) {
-  const Geom &g = op_->lat->g;
-  int rc;
+  int rc = size_slot(s, s.job.op ? s.job.op : op_);
+  if (rc) return rc;
+  const Geom &g = s.op->lat->g;
+  const size_t f64_ = s.f64;
   s.busy = true;
   s.need_restart = true;
   s.j = s.its = s.cycles = 0;
@@ -189,7 +234,8 @@ int BatchSolver::start(Slot &s) {
 }
 
 int BatchSolver::retire(Slot &s, int status) {
-  const Geom &g = op_->lat->g;
+  const Geom &g = s.op->lat->g;
+  const size_t f64_ = s.f64;
   int rc;
   if ((rc = launch_unpack(g, DD_F64, s.x, s.canon, 1, 1.0, st_))) return rc;
   DD_CUDA(cudaMemcpyAsync(s.job.x, s.canon, f64_, s.job.x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -214,31 +260,47 @@ int BatchSolver::retire(Slot &s, int status) {
 }
 
 // True residual r = b - D x (FP64) for the slots in R; retire or begin a cycle.
+// The slots of S grouped by operator, groups in order of first appearance.
+static std::vector<std::vector<Slot *>> by_operator(const std::vector<Slot *> &S) {
+  std::vector<std::vector<Slot *>> groups;
+  for (Slot *s : S) {
+    size_t k = 0;
+    while (k < groups.size() && groups[k][0]->op != s->op) k++;
+    if (k == groups.size()) groups.emplace_back();
+    groups[k].push_back(s);
+  }
+  return groups;
+}
+
 int BatchSolver::restart_phase(std::vector<Slot *> &R) {
   NvtxRange range("dd:true_residual");
-  const Geom &g = op_->lat->g;
-  const size_t n = (size_t)g.V * 12;
   int rc;
   // D x for the slots whose x is not known to be zero (w = 0 for the others,
-  // so that w = b - w below gives r = b)
+  // so that w = b - w below gives r = b), one launch per operator.
   // In a mixed-precision solve the Dslash runs in double-float arithmetic on
   // the operator's pre-split fields: x is split into the slot's staging
   // buffer (free at this point; FP64 field size); the result stays FP64.
-  RhsPtrs rp;
-  rp.n = 0;
   cudaEventRecord(ev_[0], st_);
-  for (Slot *s : R) {
-    if (s->x_zero) {
-      DD_CUDA(cudaMemsetAsync(s->w, 0, f64_, st_));
-      s->x_zero = false;
-      continue;
+  for (auto &grp : by_operator(R)) {
+    const Op *op = grp[0]->op;
+    const Geom &g = op->lat->g;
+    const size_t n = (size_t)g.V * 12;
+    RhsPtrs rp;
+    rp.n = 0;
+    for (Slot *s : grp) {
+      if (s->x_zero) {
+        DD_CUDA(cudaMemsetAsync(s->w, 0, s->f64, st_));
+        s->x_zero = false;
+        continue;
+      }
+      if (df_ && (rc = launch_split_pairs(s->x, s->canon, n, st_))) return rc;
+      rp.in[rp.n] = df_ ? (const void *)s->canon : (const void *)s->x;
+      rp.out[rp.n++] = s->w;
     }
-    if (df_ && (rc = launch_split_pairs(s->x, s->canon, n, st_))) return rc;
-    rp.in[rp.n] = df_ ? (const void *)s->canon : (const void *)s->x;
-    rp.out[rp.n++] = s->w;
+    if (rp.n && (rc = df_ ? launch_dirac_df(g, op->fdf, rp, st_) : launch_dirac(g, op->f64, rp, st_))) return rc;
   }
-  if (rp.n && (rc = df_ ? launch_dirac_df(g, op_->fdf, rp, st_) : launch_dirac(g, op_->f64, rp, st_))) return rc;
   for (Slot *s : R) {
+    const size_t n = (size_t)s->op->lat->g.V * 12;
     double *hd = hdev_ + HSTRIDE * (s - slots_.data());
     if ((rc = blas_.xmy(s->b, s->w, n, st_))) return rc;
     if ((rc = blas_.norm2(s->w, n, hd + RN, st_))) return rc;
@@ -254,7 +316,7 @@ int BatchSolver::restart_phase(std::vector<Slot *> &R) {
     s->beta = std::sqrt(hp[RN]);
     s->rel = s->bnorm > 0 ? s->beta / s->bnorm : 0.0;
     if (s->bnorm == 0) {
-      DD_CUDA(cudaMemsetAsync(s->x, 0, f64_, st_));
+      DD_CUDA(cudaMemsetAsync(s->x, 0, s->f64, st_));
       s->est = 0;
       if ((rc = retire(*s, DD_OK))) return rc;
       continue;
@@ -282,6 +344,7 @@ int BatchSolver::restart_phase(std::vector<Slot *> &R) {
     std::fill(s->g.begin(), s->g.end(), cd(0));
     s->g[0] = s->beta;
     s->target = std::max(p_.tol * s->bnorm, p_.inner_reduction * s->beta);
+    const size_t n = (size_t)s->op->lat->g.V * 12;
     if (df_) {
       rc = blas_.f64_to_df((float *)s->Vb, s->w, 1.0 / s->beta, n, st_);
       s->scl[0] = 1.0;
@@ -295,7 +358,7 @@ int BatchSolver::restart_phase(std::vector<Slot *> &R) {
 }
 
 int BatchSolver::end_cycle(Slot &s) {
-  const Geom &g = op_->lat->g;
+  const Geom &g = s.op->lat->g;
   const int m = p_.restart, k = s.j + 1;
   for (int i = k - 1; i >= 0; i--) {
     cd t = s.g[i];
@@ -310,7 +373,7 @@ int BatchSolver::end_cycle(Slot &s) {
     yp[2 * i + 1] = s.y[i].imag();
   }
   DD_CUDA(cudaMemcpyAsync(yd, yp, sizeof(double) * 2 * k, cudaMemcpyHostToDevice, st_));
-  int rc = blas_.update_x(g, s.x, zprec_, s.Z, fz_, k, yd, st_);
+  int rc = blas_.update_x(g, s.x, zprec_, s.Z, s.fz, k, yd, st_);
   s.need_restart = true;
   return rc;
 }
@@ -322,7 +385,7 @@ int BatchSolver::end_cycle(Slot &s) {
 // (unnormalised) vectors; the Hessenberg entry is scl[i] h_i and the update
 // w -= <v_i, w> v_i applies scl[i]^2 h_i to Vb_i (sdev). FP64 solves use s->w.
 int BatchSolver::mdot(Slot *s, int kk, double *h, double *wn2, bool from32) {
-  const Geom &g = op_->lat->g;
+  const Geom &g = s->op->lat->g;
   const size_t n = (size_t)g.V * 12;
   const int lvb = g.lbd[0] + g.lbd[1] + g.lbd[2] + g.lbd[3];
   if (df_)
@@ -332,7 +395,7 @@ int BatchSolver::mdot(Slot *s, int kk, double *h, double *wn2, bool from32) {
 }
 
 int BatchSolver::maxpy(Slot *s, int kk, const double *h, double *wn2, bool from32) {
-  const Geom &g = op_->lat->g;
+  const Geom &g = s->op->lat->g;
   const size_t n = (size_t)g.V * 12;
   const int lvb = g.lbd[0] + g.lbd[1] + g.lbd[2] + g.lbd[3];
   if (df_)
@@ -344,67 +407,86 @@ int BatchSolver::maxpy(Slot *s, int kk, const double *h, double *wn2, bool from3
 // One preconditioned Arnoldi step for every slot in A.
 int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
   NvtxRange range("dd:arnoldi_step");
-  const Geom &g = op_->lat->g;
-  const size_t n = (size_t)g.V * 12;
   const int m = p_.restart;
   int rc;
+  // the slots by operator (lattice): each group is one lattice of the
+  // smoother's launch and one Dslash launch
+  const std::vector<std::vector<Slot *>> groups = by_operator(A);
   // z_j = SAP(sigma v_j) in zprec. z_j is kept scaled by sigma (the smoother
   // input's scale): then w = D z_j, the Hessenberg column and y carry the same
   // factor and x += Z y is unchanged, with no rescaling pass.
   cudaEventRecord(ev_[0], st_);
-  RhsPtrs sp_ptrs, d_ptrs;
-  sp_ptrs.n = d_ptrs.n = (int)A.size();
   if (p_.mg) {
     // two-level preconditioner per slot (FP32): z_j = M (sigma v_j) / sigma
-    for (int i = 0; i < (int)A.size(); i++) {
-      Slot *s = A[i];
-      char *zj = s->Z + (size_t)s->j * fz_;
-      if ((rc = blas_.df_to_field(g, (const float *)(s->Vb + 2 * n * s->j), DD_F32, s->zt, sigma_ * s->scl[s->j],
+    for (Slot *s : A) {
+      const Geom &g = s->op->lat->g;
+      const size_t n = (size_t)g.V * 12;
+      char *zj = s->Z + (size_t)s->j * s->fz;
+      if ((rc = blas_.df_to_field(g, (const float *)(s->Vb + 2 * n * s->j), DD_F32, s->zt, s->sigma * s->scl[s->j],
                                   st_)))
         return rc;
       if ((rc = mg_apply((const Mg *)p_.mg, *s->mgw, (const float *)s->zt, (float *)zj, st_, 1.f))) return rc;
-      d_ptrs.in[i] = zj;
-      d_ptrs.out[i] = s->zt;
     }
   } else {
     const bool direct = op_->prec == zprec_ && A.size() == 1;
-    for (int i = 0; i < (int)A.size(); i++) {
-      Slot *s = A[i];
-      if (df_)
-        rc = blas_.df_to_field(g, (const float *)(s->Vb + 2 * n * s->j), op_->prec, s->tin, sigma_ * s->scl[s->j], st_);
-      else rc = launch_convert_field(g, DD_F64, s->Vb + 2 * n * s->j, op_->prec, s->tin, 1, sigma_, st_);
-      if (rc) return rc;
-      // a single slot's smoother writes z_j straight into Z when it works in
-      // Z's precision (with several slots the fixed output buffers keep the
-      // smoother's graph cache to one entry per slot set; the copy below is
-      // exact, so results are the same either way)
-      sp_ptrs.in[i] = s->tin;
-      sp_ptrs.out[i] = direct ? (void *)(s->Z + (size_t)s->j * fz_) : s->tout;
-    }
+    RhsPtrs sp_ptrs;
     AuxPtrs ax;
-    for (int i = 0; i < (int)A.size(); i++) {
-      ax.e[i] = A[i]->se;
-      ax.r[i] = A[i]->sr;
-    }
+    SapLattice lats[MAX_SAP_GROUPS];
+    int nlat = 0;
+    sp_ptrs.n = 0;
     dd_sap_params sp = p_.sap;
     sp.x_is_zero = 1;
-    if ((rc = launch_sap(g, op_->fp, sp, sp_ptrs, st_, &ax))) return rc;
-    for (int i = 0; i < (int)A.size(); i++) {
-      Slot *s = A[i];
-      char *zj = s->Z + (size_t)s->j * fz_;
-      if (!direct && (rc = launch_convert_field(g, op_->prec, s->tout, zprec_, zj, 1, 1.0, st_))) return rc;
-      d_ptrs.in[i] = zj;
-      d_ptrs.out[i] = zprec_ == DD_F64 ? (void *)s->w : s->zt;
+    for (size_t k = 0; k < groups.size(); k++) {
+      for (Slot *s : groups[k]) {
+        const Geom &g = s->op->lat->g;
+        const size_t n = (size_t)g.V * 12;
+        if (df_)
+          rc = blas_.df_to_field(g, (const float *)(s->Vb + 2 * n * s->j), s->op->prec, s->tin,
+                                 s->sigma * s->scl[s->j], st_);
+        else rc = launch_convert_field(g, DD_F64, s->Vb + 2 * n * s->j, s->op->prec, s->tin, 1, s->sigma, st_);
+        if (rc) return rc;
+        // a single slot's smoother writes z_j straight into Z when it works in
+        // Z's precision (with several slots the fixed output buffers keep the
+        // smoother's graph cache to one entry per slot set; the copy below is
+        // exact, so results are the same either way)
+        const int i = sp_ptrs.n++;
+        sp_ptrs.in[i] = s->tin;
+        sp_ptrs.out[i] = direct ? (void *)(s->Z + (size_t)s->j * s->fz) : s->tout;
+        ax.e[i] = s->se;
+        ax.r[i] = s->sr;
+      }
+      lats[nlat++] = SapLattice{groups[k][0]->op->lat->g, groups[k][0]->op->fp, (int)groups[k].size()};
+      // one launch per MAX_SAP_GROUPS lattices
+      if (nlat == MAX_SAP_GROUPS || k + 1 == groups.size()) {
+        if ((rc = launch_sap_lattices(lats, nlat, sp, sp_ptrs, st_, &ax))) return rc;
+        nlat = 0;
+        sp_ptrs.n = 0;
+      }
+    }
+    for (Slot *s : A) {
+      char *zj = s->Z + (size_t)s->j * s->fz;
+      if (!direct && (rc = launch_convert_field(s->op->lat->g, s->op->prec, s->tout, zprec_, zj, 1, 1.0, st_)))
+        return rc;
     }
   }
   cudaEventRecord(ev_[1], st_);
-  // w = D z_j in zprec (a double-float solve keeps it in the FP32 field zt;
-  // the first Gram-Schmidt pass reads it there and writes the DF w)
-  if ((rc = launch_dirac(g, zprec_ == DD_F64 ? op_->f64 : op_->f32, d_ptrs, st_))) return rc;
+  // w = D z_j in zprec, one launch per operator (a double-float solve keeps it
+  // in the FP32 field zt; the first Gram-Schmidt pass reads it there and
+  // writes the DF w)
+  for (auto &grp : groups) {
+    const Op *op = grp[0]->op;
+    RhsPtrs d_ptrs;
+    d_ptrs.n = 0;
+    for (Slot *s : grp) {
+      d_ptrs.in[d_ptrs.n] = s->Z + (size_t)s->j * s->fz;
+      d_ptrs.out[d_ptrs.n++] = (zprec_ == DD_F64 && !p_.mg) ? (void *)s->w : s->zt;
+    }
+    if ((rc = launch_dirac(op->lat->g, zprec_ == DD_F64 ? op->f64 : op->f32, d_ptrs, st_))) return rc;
+  }
   // an IEEE FP64 basis with FP32 preconditioned vectors (outer_f64): w = D z_j as FP64
   if (!df_ && zprec_ != DD_F64)
     for (Slot *s : A)
-      if ((rc = launch_convert_field(g, zprec_, s->zt, DD_F64, s->w, 1, 1.0, st_))) return rc;
+      if ((rc = launch_convert_field(s->op->lat->g, zprec_, s->zt, DD_F64, s->w, 1, 1.0, st_))) return rc;
   cudaEventRecord(ev_[2], st_);
   // classical Gram-Schmidt, repeated once for slots whose norm drops below 1e-3 of its value (REORTH2)
   for (Slot *s : A) {
@@ -452,6 +534,7 @@ int BatchSolver::arnoldi_step(std::vector<Slot *> &A) {
     s.its++;
     const int j = s.j;
     const double hn = std::sqrt(std::max(hp[W1], 0.0));
+    const size_t n = (size_t)s.op->lat->g.V * 12;
     for (int q = 0; q <= j; q++) s.H[(size_t)q * m + j] = hcol[i][q];
     if (hn > 0) {
       if (df_) {   // v_{j+1} = Vb_{j+1} / hn, kept as a scale

@@ -12,6 +12,9 @@ namespace dd {
 
 // One right-hand side to solve.
 struct RhsJob {
+  // operator of this right-hand side (null: the solver's own); any operator
+  // with the solver operator's smoother precision and block shape
+  const Op *op = nullptr;
   const double *b = nullptr;  // canonical FP64 right-hand side [V][4][3][2]
   int b_on_device = 0;
   double *x = nullptr;        // canonical FP64 solution (initial guess if use_x0)
@@ -24,6 +27,10 @@ struct RhsJob {
 
 // Device buffers and FGMRES state of one batch slot.
 struct Slot {
+  const Op *op = nullptr;   // operator of the right-hand side in the slot
+  size_t f64 = 0, fz = 0, fp = 0;   // its field sizes (FP64, preconditioned vectors, smoother)
+  long long vol = 0;        // lattice volume the slot's buffers were allocated for (0: none)
+  double sigma = 1;         // smoother-input scale sqrt(24 V)
   bool busy = false, need_restart = true;
   bool x_zero = false;   // x is exactly zero (first cycle without an initial guess): r = b, no Dslash
   RhsJob job;
@@ -46,11 +53,14 @@ struct Slot {
   MgWork *mgw = nullptr;   // coarse-solve workspace when preconditioning with multigrid
 };
 
-// FGMRES(m) right-preconditioned by SAP over a batch of right-hand sides that
-// share one operator: the slots' Schwarz sweeps and Dslash products run as
-// single batched launches, orthogonalisation and Givens rotations per slot.
-// Slots retire when their right-hand side converges and are refilled from
-// the job source at the next Arnoldi step (continuous batching).
+// FGMRES(m) right-preconditioned by SAP over a batch of right-hand sides:
+// the slots' Schwarz sweeps run as single launches (also across operators
+// on different lattices, as long as they share the smoother precision and
+// block shape), the Dslash products as one launch per operator,
+// orthogonalisation and Givens rotations per slot. Slots retire when their
+// right-hand side converges and are refilled from the job source at the next
+// Arnoldi step (continuous batching); a slot's buffers are resized when it
+// takes a right-hand side on a lattice of another size.
 class BatchSolver {
  public:
   BatchSolver(const Op *op, const dd_solve_params &p, int slots, cudaStream_t st);
@@ -69,12 +79,16 @@ class BatchSolver {
 
  private:
   int start(Slot &s);
+  int size_slot(Slot &s, const Op *op);   // buffers of slot s for right-hand sides of op
+  int free_slot(Slot &s);
   int restart_phase(std::vector<Slot *> &R);
   int arnoldi_step(std::vector<Slot *> &A);
   int end_cycle(Slot &s);
   int retire(Slot &s, int status);
   int sync_h();
-  std::vector<std::pair<void **, size_t>> slot_buffers(Slot &s) const;
+  // the slot's buffers with their sizes for lattice volume V (allocation and
+  // release walk the same list)
+  std::vector<std::pair<void **, size_t>> slot_buffers(Slot &s, long long V) const;
   int mdot(Slot *s, int kk, double *h, double *wn2, bool from32 = false);
   int maxpy(Slot *s, int kk, const double *h, double *wn2, bool from32 = false);
 
@@ -84,8 +98,7 @@ class BatchSolver {
   std::vector<Slot> slots_;
   int zprec_;
   bool df_;  // Krylov basis and w in double-float
-  size_t f64_, fz_, fp_;
-  double sigma_;
+
   Blas blas_;
   double *hdev_ = nullptr;   // [slots][HSTRIDE]
   double *hpin_ = nullptr;   // pinned mirror [slots][HSTRIDE]

@@ -1,7 +1,8 @@
 """Batched and served solves: every right-hand side gets the same solution
 alone and in a mixed batch (bit-identical: its reductions and decisions do
 not depend on its batch mates), requests on lattices of different sizes
-overlap on the device, and the server admits by memory budget and cancels."""
+are served at the same time - in one worker whose Schwarz launches cover
+all their lattices - and the server admits by memory budget and cancels."""
 import time
 
 import numpy as np
@@ -72,3 +73,49 @@ def test_server_budget_and_cancel():
     assert dd.lib().dd_cancel(srv.handle, 999999) == -8   # DD_ENOTFOUND
     srv.close()
     s.close()
+
+
+def test_server_lattices_share_one_worker_and_overlap():
+    """Requests on three lattices of different sizes (same smoother
+    precision and block shape) are served by one worker: their right-hand
+    sides sit in its slots together, each Arnoldi step smoothing all of them
+    in one launch per colour phase. The polling below sees the requests
+    RUNNING at overlapping times; every result is bit for bit the solo
+    solve's and reaches 1e-10 by the oracle's operator."""
+    sizes = [((8, 8, 8, 8), 61), ((8, 8, 8, 16), 62), ((16, 8, 8, 8), 63)]
+    setups = [Setup(d, (4, 4, 4, 4), eps=0.25, n_stout=2, c_sw=1.7, m0=-0.01, prec=dd.F16, seed=sd)
+              for d, sd in sizes]
+    srv = dd.Server(max_slots=8, max_batch_rhs=8)
+    jobs = []
+    for k, s in enumerate(setups):
+        b = np.stack([synth.gaussian_spinor(s.V, 200 + 10 * k + r) for r in range(2)])
+        jobs.append((s, b, srv.submit(s.op, b, tol=1e-10)))
+    running = {t: None for _, _, t in jobs}
+    done, xs = {}, {t: np.zeros(b.shape, dtype=np.complex128) for _, b, t in jobs}
+    t0 = time.perf_counter()
+    state = dd.ctypes.c_int()
+    while len(done) < len(jobs) and time.perf_counter() - t0 < 600:
+        now = time.perf_counter() - t0
+        for s, b, t in jobs:
+            if t in done:
+                continue
+            # x is written (and the ticket released) once the request is done
+            assert dd.lib().dd_poll(srv.handle, t, dd.ctypes.byref(state), dd._ptr(xs[t]), None) == 0
+            if state.value == dd.RUNNING and running[t] is None:
+                running[t] = now
+            if state.value in (dd.DONE, dd.FAILED, dd.CANCELLED):
+                done[t] = (state.value, now)
+        time.sleep(0.0005)
+    assert len(done) == len(jobs) and all(v[0] == dd.DONE for v in done.values()), done
+    ivals = [(running[t] if running[t] is not None else done[t][1], done[t][1]) for _, _, t in jobs]
+    overlaps = sum(1 for i in range(len(ivals)) for j in range(i + 1, len(ivals))
+                   if max(ivals[i][0], ivals[j][0]) < min(ivals[i][1], ivals[j][1]))
+    assert overlaps >= 1, ivals
+    srv.close()
+    for s, b, t in jobs:
+        for r in range(2):
+            assert relerr(s.ref.apply(xs[t][r]), b[r]) <= 1e-10
+            x1, _ = s.op.solve(b[r], tol=1e-10)
+            assert np.array_equal(x1, xs[t][r])
+    for s in setups:
+        s.close()

@@ -69,7 +69,7 @@ def test_bench_workload_sap_sweep(bench_problem):
     want = ref.sap(W2["block"], b, 1, W2["mr_steps"])
     e, w = relerr(got, want), worst_site(got, want)
     print(f"64x32^3 SAP sweep FP32: rel L2 {e:.3e}, worst site {w:.3e}")
-    assert e <= 1e-5 and w <= 1e-4
+    assert e <= 5e-7 and w <= 5e-6   # observed 1.1e-7 and 3.4e-7 (see test_gpu_sap.py)
 
 
 def test_bench_workload_solve_true_residual(bench_problem):

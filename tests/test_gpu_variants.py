@@ -18,7 +18,7 @@ from gpu_common import Setup, relerr
 
 pytestmark = pytest.mark.gpu
 
-SAP_TOL = {dd.F64: 1e-12, dd.F32: 1e-5, dd.F16: 1e-2, dd.BF16: 5e-2}
+SAP_TOL = {dd.F64: 1e-12, dd.F32: 5e-7, dd.F16: 1.5e-3, dd.BF16: 1.2e-2}
 DSLASH_TOL = {dd.F64: 1e-13, dd.F32: 1e-6, dd.F16: 1e-3, dd.BF16: 1e-2}
 
 
