@@ -133,3 +133,15 @@ def test_two_level_through_server():
     srv.close()
     mg.close()
     s.close()
+
+
+def test_two_level_refuses_512_site_aggregates():
+    """Aggregates are the Schwarz blocks and the set-up kernels take one
+    thread per site of a block, at most 256: an operator on 8 x 4^3 blocks is
+    refused with DD_EINVAL and a message naming the limit."""
+    s = Setup((16, 8, 8, 8), (8, 4, 4, 4), prec=dd.F32, seed=71)
+    tv = np.stack([synth.gaussian_spinor(s.V, 72 + k) for k in range(4)])
+    with pytest.raises(dd.DDError) as e:
+        dd.Multigrid(s.op, tv, setup_iters=0, coarse_max_iter=8)
+    assert e.value.code == -1 and "256" in str(e.value)
+    s.close()
