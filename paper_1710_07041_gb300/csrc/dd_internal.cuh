@@ -508,10 +508,25 @@ template <typename C> __device__ __forceinline__ cpx<C> cmulc(cpx<C> a, cpx<C> b
   return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
 }
 
+// c + a b for double-float numbers, accumulated lazily: the product's high
+// part is added to c.hi with an error-free TwoSum, its exact rounding error
+// (one FMA), the cross terms a.hi b.lo + a.lo b.hi and the sum's error go into
+// the low word, which is not renormalised (every consumer reads hi + lo as a
+// whole). About 13 FP32 operations instead of a full double-float product
+// and sum (~18); the error stays a few units of 2^-44 of the terms.
+__device__ __forceinline__ dfl df_mad(dfl a, dfl b, dfl c) {
+  const float p = a.hi * b.hi;
+  const float pe = fmaf(a.hi, b.hi, -p);
+  const float cross = fmaf(a.hi, b.lo, a.lo * b.hi);
+  const float s = c.hi + p;
+  const float z = s - c.hi;
+  const float e = (c.hi - (s - z)) + (p - z);
+  return dfl(s, c.lo + (e + (pe + cross)), 0);
+}
 // Fused multiply-add of the real type: fma for float and double (one
-// rounding per term); the double-float type forms the product and adds it.
+// rounding per term); df_mad for double-float numbers.
 template <typename C> __device__ __forceinline__ C mad(C a, C b, C c) {
-  if constexpr (std::is_same<C, dfl>::value) return a * b + c;
+  if constexpr (std::is_same<C, dfl>::value) return df_mad(a, b, c);
   else return fma(a, b, c);
 }
 // acc += a b and acc += conj(a) b (complex), as chains of fused multiply-adds
