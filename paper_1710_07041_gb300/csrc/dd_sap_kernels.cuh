@@ -84,6 +84,72 @@ __device__ __noinline__ void wait_expired(unsigned *timeouts, unsigned mbar, uns
   }
 }
 
+// ---- tensor memory (TMEM) as a per-thread store of the block's clover
+// blocks (STAGE 3). TMEM has 128 lanes x 512 columns of 32 bits per SM; a
+// warp reaches only the 32 lanes of its sub-partition (warp % 4), so thread
+// t of the CTA owns lane t % 128 and a column range chosen by t / 128. Each
+// clover block a thread multiplies with is read by that thread alone, which
+// is the access TMEM allows. Allocation is per CTA (a power of two of at
+// least 32 columns); the launch keeps at most 512 / NCOLS CTAs of TMEM
+// kernels on an SM through their shared-memory size, so an allocation never
+// waits for columns.
+template <int NCOLS> __device__ __forceinline__ void tmem_alloc(unsigned dst_smem) {
+  static_assert(NCOLS >= 32 && NCOLS <= 512 && (NCOLS & (NCOLS - 1)) == 0, "TMEM columns");
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst_smem), "n"(NCOLS)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+template <int NCOLS> __device__ __forceinline__ void tmem_dealloc(uint32_t taddr) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "n"(NCOLS) : "memory");
+}
+// a CTA barrier that orders the threads' tensor-memory operations around it
+__device__ __forceinline__ void tmem_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+// the 36 reals of a clover block (m[0..17], real and imaginary parts in
+// turn) to columns taddr ... taddr + 35 of the thread's lane (warp-collective)
+__device__ __forceinline__ void tmem_st36(uint32_t taddr, const cpx<float> *m) {
+  const float *f = (const float *)m;
+  unsigned u[36];
+#pragma unroll
+  for (int i = 0; i < 36; i++) u[i] = __float_as_uint(f[i]);
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n" ::"r"(taddr),
+      "r"(u[0]), "r"(u[1]), "r"(u[2]), "r"(u[3]), "r"(u[4]), "r"(u[5]), "r"(u[6]), "r"(u[7]), "r"(u[8]), "r"(u[9]),
+      "r"(u[10]), "r"(u[11]), "r"(u[12]), "r"(u[13]), "r"(u[14]), "r"(u[15]), "r"(u[16]), "r"(u[17]), "r"(u[18]),
+      "r"(u[19]), "r"(u[20]), "r"(u[21]), "r"(u[22]), "r"(u[23]), "r"(u[24]), "r"(u[25]), "r"(u[26]), "r"(u[27]),
+      "r"(u[28]), "r"(u[29]), "r"(u[30]), "r"(u[31])
+      : "memory");
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(taddr + 32), "r"(u[32]),
+               "r"(u[33]), "r"(u[34]), "r"(u[35])
+               : "memory");
+}
+// the stores of this thread have landed (before the columns are read)
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+// the inverse of tmem_st36 (warp-collective). Both loads and their wait are
+// one asm statement: the destination registers are defined only after it.
+__device__ __forceinline__ void tmem_ld36(uint32_t taddr, cpx<float> *m) {
+  unsigned u[36];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%36];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%32, %33, %34, %35}, [%37];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
+        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]),
+        "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]),
+        "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31]), "=r"(u[32]),
+        "=r"(u[33]), "=r"(u[34]), "=r"(u[35])
+      : "r"(taddr), "r"(taddr + 32)
+      : "memory");
+  float *f = (float *)m;
+#pragma unroll
+  for (int i = 0; i < 36; i++) f[i] = __uint_as_float(u[i]);
+}
+
 // Strided view of one block's pair tile: pair-major (the links: element
 // (i, site) at p[i * stride + site]) or chunked (the clover: see
 // clover_block_chunked, stride = sites per chunk row).
@@ -104,6 +170,14 @@ __device__ __forceinline__ void tile_link(const Tile<P> &t, int s, int mu, Link<
 template <typename C, typename P>
 __device__ __forceinline__ void tile_block(const Tile<P> &t, int s, int h, cpx<C> *m) {
   clover_block_chunked<false, C, P>(t.p, (size_t)t.stride, s, h, m);
+}
+
+// chirality block h of tile site s: from the thread's TMEM columns at taddr
+// (STAGE 3, which stored exactly this block there) or from the tile
+template <int STAGE, typename C, typename P>
+__device__ __forceinline__ void clover_of(const Tile<P> &t, uint32_t taddr, int s, int h, cpx<C> *m) {
+  if constexpr (STAGE == 3) tmem_ld36(taddr, m);
+  else tile_block(t, s, h, m);
 }
 
 // shared-memory vector: [12][Vh] complex, one parity of the block
@@ -280,11 +354,18 @@ template <typename S> struct SapSmem {
   using P = typename Store<S>::pair_t;
   static constexpr int LT = 36;   // pairs per site of the links tile (full links)
   static size_t vec_bytes(const Geom &g) { return (size_t)12 * g.Vh * sizeof(cpx<C>); }
-  // stage: 0 nothing staged, 1 links + A_oo + A_ee^-1, 2 links only
+  // TMEM columns of a STAGE-3 CTA: 128 per group of 128 threads (its A_ee^-1
+  // block at +0, its A_oo block at +64)
+  static int tmem_cols(const Geom &g) { return g.Vb > 256 ? 512 : 256; }
+  // stage: 0 nothing staged, 1 links + A_oo + A_ee^-1, 2 links only, 3 links
+  // staged and the clover blocks in TMEM (at least 80 KB, or 150 KB with 512
+  // columns: of an SM's 228 KB, two 256-column CTAs fit, three do not, nor
+  // a 512-column CTA beside any other)
   static size_t bytes(const Geom &g, int stage) {
-    size_t b = 3 * vec_bytes(g) + 96 * sizeof(C) + 16;   // + staging mbarrier
+    size_t b = 3 * vec_bytes(g) + 96 * sizeof(C) + 16;   // + staging mbarrier, TMEM address
     if (stage == 1) b += ((size_t)LT * g.Vb + (size_t)36 * 2 * g.Vh) * sizeof(P);
-    if (stage == 2) b += (size_t)LT * g.Vb * sizeof(P);
+    if (stage == 2 || stage == 3) b += (size_t)LT * g.Vb * sizeof(P);
+    if (stage == 3) b = std::max(b, (size_t)(tmem_cols(g) > 256 ? 150 : 80) * 1024);
     return b;
   }
 };
@@ -318,6 +399,9 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
   constexpr int LT = SapSmem<S>::LT;   // pairs per site of the links tile
   // a specialised shape is launched with one thread per site: blockDim.x == NT
   static_assert(SHAPE == 0 || (SHAPE == 1 && NT == 256) || (SHAPE == 2 && NT == 512), "shape / threads");
+  // TMEM holds FP32 clover blocks, one thread per lane: specialised shapes only
+  static_assert(STAGE != 3 || (SHAPE != 0 && sizeof(C) == 4), "TMEM clover: FP32 arithmetic, fixed shape");
+  constexpr int TCOLS = NT > 256 ? 512 : 256;
   extern __shared__ __align__(16) unsigned char smem[];
   // every group of a launch has the same block shape (checked on the host)
   const int Vh = block_shape<SHAPE>(G.grp[0].g).Vh, Vb = block_shape<SHAPE>(G.grp[0].g).Vb;
@@ -328,13 +412,25 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
   cpx<C> *xch = te + 12 * Vh;     // partial-sum exchange between thread halves
   C *red = (C *)(xch + 12 * Vh);
   uint64_t *mbar = (uint64_t *)(red + 96);   // staging barrier (16 bytes reserved)
+  uint32_t *tmem_at = (uint32_t *)(mbar + 1);  // TMEM base address (STAGE 3)
   unsigned char *tiles = (unsigned char *)(red + 96) + 16;
   unsigned phase = 0;                        // parity of the staging barrier's current phase
   if constexpr (STAGE != 0) {
     if (threadIdx.x == 0) mbar_init(mbar);
-    __syncthreads();
+    if constexpr (STAGE == 3) {
+      if (threadIdx.x < 32) tmem_alloc<TCOLS>(smem_u32(tmem_at));
+      tmem_sync();
+    } else {
+      __syncthreads();
+    }
   }
   const unsigned mbar_s = smem_u32(mbar);
+  // this thread's TMEM columns: lane threadIdx.x % 128 (the warp's
+  // sub-partition), 128 columns per group of 128 threads
+  uint32_t tm = 0;
+  if constexpr (STAGE == 3)
+    tm = *tmem_at + ((uint32_t)(32 * ((threadIdx.x / 32) % 4)) << 16) + (uint32_t)(threadIdx.x / 128) * 128u;
+  bool quit = false;   // a staging wait expired: leave through the common exit
 
   // Work items: (lattice group, block of this colour, right-hand-side tile),
   // block fastest within a group; group k holds items G.grp[k].item0 ... A
@@ -357,16 +453,28 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
     const Geom ng = MULTI ? block_shape<SHAPE>(G.grp[nk].g) : g0;
     const int nnbc = ng.nblocks / 2, nloc = MULTI ? nitem - G.grp[nk].item0 : nitem;
     const int nb = sap_block_of(ng, colour, nloc % nnbc), nrt = nloc / nnbc;
+    // exactly what the item reads: the incremental modes read the clover
+    // only on odd sites (A_oo) and, after the first sweep, the stored
+    // residual on odd sites instead of b (16-byte pieces of Vh sites per
+    // chunk row)
+    const bool incr = mode & SAP_INCR, from_b = !incr || (mode & SAP_FROM_B);
+    constexpr int CP = chunk_pairs<P>(), NC = spinor_chunks<S>();
     prefetch_l2((const P *)G.grp[nk].links + (size_t)nb * LT * Vb, (unsigned)LT * Vb * sizeof(P));
-    prefetch_l2((const P *)G.grp[nk].clov + (size_t)nb * 36 * Vb, 36u * Vb * sizeof(P));
+    const P *nclov = (const P *)G.grp[nk].clov + (size_t)nb * 36 * Vb;
+    if (incr) {
+      for (int c = 0; c < 36 / CP; c++) prefetch_l2(nclov + ((size_t)c * Vb + Vh) * CP, Vh * 16u);
+    } else {
+      prefetch_l2(nclov, 36u * Vb * sizeof(P));
+    }
     prefetch_l2((const P *)G.grp[nk].cinv + (size_t)nb * 36 * Vh, 36u * Vh * sizeof(P));
-    constexpr int NC = spinor_chunks<S>();
     const int nrhs0 = MULTI ? G.grp[nk].rhs0 : 0, nnrhs = MULTI ? G.grp[nk].nrhs : rp.n;
     for (int q = 0; q < tile; q++) {
       const int r = nrt * tile + q;
       if (r >= nnrhs) break;
       const size_t off = (size_t)nb * NC * Vb * 16;
-      prefetch_l2((const char *)rp.in[nrhs0 + r] + off, NC * Vb * 16u);
+      if (from_b) prefetch_l2((const char *)rp.in[nrhs0 + r] + off, NC * Vb * 16u);
+      else
+        for (int c = 0; c < NC; c++) prefetch_l2((const char *)ax.r[nrhs0 + r] + off + ((size_t)c * Vb + Vh) * 16, Vh * 16u);
       if (!self_zero) prefetch_l2((const char *)rp.out[nrhs0 + r] + off, NC * Vb * 16u);
     }
   }
@@ -396,7 +504,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
     Lt = {sl, Vb};
     Ao = {sa, Vh};
     Ai = {si, Vh};
-  } else if constexpr (STAGE == 2) {
+  } else if constexpr (STAGE == 2 || STAGE == 3) {
     P *sl = (P *)tiles;
     if (threadIdx.x == 0) {
       const unsigned lb = (unsigned)LT * Vb * sizeof(P);
@@ -413,6 +521,18 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
     Ai = {(const P *)cinv + (size_t)b * 36 * Vh, Vh};
   }
 
+  if constexpr (STAGE == 3) {
+    // this thread's two clover blocks (A_ee^-1 of even site j, A_oo of odd
+    // site j, chirality h) into its TMEM columns; the previous item's reads
+    // of them completed (tmem_ld36 waits). Both blocks are loaded before the
+    // first store (one round trip to L2 per item, not two).
+    cpx<C> mi[18], mo[18];
+    tile_block(Ai, j, h, mi);
+    tile_block(Ao, j, h, mo);
+    tmem_st36(tm, mi);
+    tmem_st36(tm + 64, mo);
+    tmem_wait_st();
+  }
   const Site se = decode(g, b, j), so = decode(g, b, Vh + j);
   const uint2 nbr_e = inner_neighbours(g, se, h), nbr_o = inner_neighbours(g, so, h);
   // right-hand sides blockIdx.y * tile ... share the staged tiles
@@ -487,7 +607,8 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
         const bool ok = mbar_wait(mbar_s, phase);
         if (__syncthreads_or(!ok)) {
           wait_expired(timeouts, mbar_s, phase);
-          return;
+          quit = true;
+          break;
         }
         phase ^= 1u;
       }
@@ -499,7 +620,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
     // te = A_ee^-1 D_eo rho, then p = A_oo rho - D_oe te and the MR update.
     // Last step: e_e = A_ee^-1 (r_e - D_eo e_o).
     cpx<C> m[18], tmp[6], rh[6], eo[6], ee[6];
-    tile_block(Ai, j, h, m);
+    clover_of<STAGE>(Ai, tm, j, h, m);
     herm6_mv(m, r_e, tmp);
   #pragma unroll
     for (int i = 0; i < 6; i++) {
@@ -534,7 +655,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
         exchange(xch, Vh, j, h, part, hv);
   #pragma unroll
         for (int i = 0; i < 6; i++) u[i] = last ? cpx<C>{r_e[i].re - hv[i].re, r_e[i].im - hv[i].im} : hv[i];
-        tile_block(Ai, j, h, m);
+        clover_of<STAGE>(Ai, tm, j, h, m);
         herm6_mv(m, u, mu);
         if (last) {
   #pragma unroll
@@ -551,7 +672,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
         hops_inner(Vh, Vh + j, h, nbr_o, 0, te, Lt, part);
         cpx<C> hv[6], mu[6], p[6];
         exchange(xch, Vh, j, h, part, hv);
-        tile_block(Ao, j, h, m);
+        clover_of<STAGE>(Ao, tm + 64, j, h, m);
         herm6_mv(m, rh, mu);
         C pr_re = 0, pr_im = 0, pp = 0;
   #pragma unroll
@@ -595,7 +716,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
   #pragma unroll
       for (int i = 0; i < 6; i++)
         u[i] = odd ? rh[i] : (step == last ? cpx<C>{r_e[i].re - hv[i].re, r_e[i].im - hv[i].im} : hv[i]);
-      tile_block(odd ? Ao : Ai, j, h, m);
+      clover_of<STAGE>(odd ? Ao : Ai, tm + (odd ? 64 : 0), j, h, m);
       herm6_mv(m, u, mu);
       if (odd) {
         cpx<C> p[6];
@@ -671,7 +792,13 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
     }
     __syncthreads();   // shared vectors are reused by the next right-hand side
   }
+  if (quit) break;
   }  // work items
+  if constexpr (STAGE == 3) {
+    // every thread's TMEM reads are complete; the allocating warp frees
+    tmem_sync();
+    if (threadIdx.x < 32) tmem_dealloc<TCOLS>(*tmem_at);
+  }
 }
 
 template <typename S, int STAGE, int MINB, int NT, int SHAPE, bool UNROLL = false, bool MULTI = false>
@@ -746,8 +873,13 @@ int sap_t(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp
   if (shape_of(L[0].g) == SH)
     return nl > 1 ? sap_k<S, STAGE, MINB, NT, SH, false, true>(L, nl, p, rp, ax, tile, persistent, st)
                   : sap_k<S, STAGE, MINB, NT, SH>(L, nl, p, rp, ax, tile, persistent, st);
-  return nl > 1 ? sap_k<S, STAGE, MINB, NT, 0, false, true>(L, nl, p, rp, ax, tile, persistent, st)
-                : sap_k<S, STAGE, MINB, NT, 0>(L, nl, p, rp, ax, tile, persistent, st);
+  if constexpr (STAGE == 3) {   // TMEM clover: specialised shapes only
+    set_error("sap: the TMEM clover layout exists for the specialised block shapes only");
+    return (int)DD_EINVAL;
+  } else {
+    return nl > 1 ? sap_k<S, STAGE, MINB, NT, 0, false, true>(L, nl, p, rp, ax, tile, persistent, st)
+                  : sap_k<S, STAGE, MINB, NT, 0>(L, nl, p, rp, ax, tile, persistent, st);
+  }
 }
 // the MR loop unrolled by parity (specialised shape only)
 template <typename S, int STAGE, int MINB, int NT = 256>
@@ -768,8 +900,9 @@ template <typename S> constexpr bool sixteen_bit() { return Store<S>::prec == DD
 // links staged, with two CTAs per SM (when the full staging does not fit
 // twice); tiles read through L1/L2 with two CTAs per SM; for 16-bit storage
 // on the 4^4 shape with one right-hand side, the two-CTA layouts again with
-// the MR loop unrolled by parity. Variants that do not fit are skipped.
-// With several right-hand sides a CTA also solves `tile` of them with one
+// the MR loop unrolled by parity; for 32- and 16-bit storage on the
+// specialised shapes, the links staged and the clover blocks in TMEM.
+// Variants that do not fit are skipped. With several right-hand sides a CTA also solves `tile` of them with one
 // staging of its block's operator (rhs_tile; 0 lets the autotuner choose).
 template <typename S>
 int sap_variants(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp, const AuxPtrs *ax,
@@ -784,10 +917,15 @@ int sap_variants(const SapLattice *L, int nl, const dd_sap_params &p, const RhsP
     set_error("sap: block of %d sites needs more shared memory than available", g.Vb);
     return DD_EINVAL;
   }
-  int layouts[6], nlay = 0;
+  // links staged and the clover blocks in TMEM (32- and 16-bit storage on
+  // the specialised shapes)
+  constexpr bool tmem_ok = Store<S>::prec != DD_F64;
+  const int sh = shape_of(g);
+  int layouts[8], nlay = 0;
   if (g.Vb > 256) {
     // 512-site blocks (e.g. 8 x 4^3): 512 threads, one CTA per SM
     layouts[nlay++] = stage1 ? 3 : 4;
+    if (tmem_ok && sh == 2 && SapSmem<S>::bytes(g, 3) <= limit) layouts[nlay++] = 9;
   } else {
     if (stage1) layouts[nlay++] = 0;
     if (stage2) layouts[nlay++] = 1;
@@ -800,6 +938,7 @@ int sap_variants(const SapLattice *L, int nl, const dd_sap_params &p, const RhsP
       if (stage2) layouts[nlay++] = 6;
       if (nost2 || !stage1) layouts[nlay++] = 7;
     }
+    if (tmem_ok && sh == 1 && SapSmem<S>::bytes(g, 3) <= half) layouts[nlay++] = 8;
   }
   int tiles[6], nt = 0;
   if (p.rhs_tile > 0) {
@@ -819,6 +958,13 @@ int sap_variants(const SapLattice *L, int nl, const dd_sap_params &p, const RhsP
       case 3: return sap_t<S, 1, 1, 512>(L, nl, p, rp, ax, tile, pers, st);
       case 4: return sap_t<S, 0, 1, 512>(L, nl, p, rp, ax, tile, pers, st);
       case 5: return sap_t<S, 2, 2>(L, nl, p, rp, ax, tile, pers, st);
+      case 8:
+      case 9:
+        if constexpr (tmem_ok) {
+          if (layout == 8) return sap_t<S, 3, 2>(L, nl, p, rp, ax, tile, pers, st);
+          return sap_t<S, 3, 1, 512>(L, nl, p, rp, ax, tile, pers, st);
+        }
+        return (int)DD_EINVAL;
       case 6:
       case 7:
         if constexpr (sixteen_bit<S>()) {

@@ -2,7 +2,8 @@
 (DD_TUNE_VARIANT), against the FP64 oracle: the Schwarz smoother's
 shared-memory layouts (all tiles staged with one or two CTAs per SM, links
 only staged, nothing staged; for 16-bit storage also the two-CTA layouts with
-the MR loop unrolled by parity), each with the one-CTA-per-block and the
+the MR loop unrolled by parity; for 32- and 16-bit storage the links staged
+with the clover blocks in tensor memory), each with the one-CTA-per-block and the
 persistent grid, and the four Dslash launch shapes; on the 4^4 block shape
 and, in the second half, on the 8 x 4^3 block (512-thread CTAs, the shape
 the batched workload picks) in every precision, and FP64 on the 4^4 shape.
@@ -45,7 +46,7 @@ def setup(request):
     s.close()
 
 
-@pytest.mark.parametrize("k", range(10))
+@pytest.mark.parametrize("k", range(12))
 def test_sap_variant(setup, k):
     s, b, want, _ = setup
     fb = s.lat.to_field(b, s.prec)
@@ -68,8 +69,9 @@ def test_dslash_variant(setup, k):
 
 
 # The 8 x 4^3 block (SHAPE 2: 512 threads per CTA) in every precision, and
-# FP64 on the 4^4 block: two Schwarz variants each (one CTA per block, the
-# persistent grid), four Dslash launch shapes.
+# FP64 on the 4^4 block: the Schwarz layouts (tiles in shared memory; for 32-
+# and 16-bit storage also the clover blocks in tensor memory), each with one
+# CTA per block and the persistent grid; four Dslash launch shapes.
 @pytest.fixture(scope="module",
                 params=[(dd.F64, (4, 4, 4, 4)), (dd.F64, (8, 4, 4, 4)), (dd.F32, (8, 4, 4, 4)),
                         (dd.F16, (8, 4, 4, 4)), (dd.BF16, (8, 4, 4, 4))],
@@ -82,7 +84,7 @@ def setup2(request):
     s.close()
 
 
-@pytest.mark.parametrize("k", range(2))
+@pytest.mark.parametrize("k", range(4))
 def test_sap_variant_shapes(setup2, k):
     s, b, want, _ = setup2
     fb = s.lat.to_field(b, s.prec)
