@@ -778,9 +778,11 @@ RhsPtrs contiguous(const void *in, void *out, int nrhs, size_t field_bytes);
 
 // Per-right-hand-side work fields of the Schwarz smoother's incremental
 // colour residual (fields of the smoother's storage precision): e[r] the
-// latest block corrections, r[r] each block's residual after its own latest
-// solve (odd sites; the even-site residual of an even-odd block solve is
-// zero).
+// latest block corrections, as the face flux into the neighbouring blocks
+// (6 complex per face site, see the Schwarz kernel) or, where that does not
+// fit a spinor field or for FP64, as a spinor field; r[r] each block's
+// residual after its own latest solve (odd sites; the even-site residual of
+// an even-odd block solve is zero).
 struct AuxPtrs {
   void *e[MAX_RHS];
   void *r[MAX_RHS];

@@ -6,15 +6,20 @@
 //
 // One CTA per block (x one right-hand side). Per phase the CTA
 //   1. stages the block's links, odd-site clover A_oo and even-site inverse
-//      A_ee^-1 into shared memory with bulk (TMA) copies (overlapping step 2),
+//      A_ee^-1 into shared memory with bulk (TMA) copies (overlapping step 2;
+//      in one layout the clover blocks go to tensor memory instead, each
+//      thread's two blocks into its own TMEM lane),
 //   2. forms its residual: r = b - D x on its sites (neighbour x read from
 //      the other colour's blocks in HBM; skipped when x = 0), or, given work
 //      fields, incrementally: after its own solve a block's residual is zero
 //      on even sites and the MR residual rho on odd ones, and until its next
 //      phase only the neighbouring blocks' corrections e change x, so
 //      r = (stored residual, or b on the first solve from x = 0) minus the
-//      hops of e across the block faces; each phase stores its e and rho for
-//      the next phases (DD_SAP_INCR=0 turns this off),
+//      hops of e across the block faces; each phase stores its rho and, as
+//      face flux, the hops of its e into the neighbouring blocks' face sites
+//      (computed from the staged links and e in shared memory; the receiver
+//      reads its flux contiguously) for the next phases (DD_SAP_INCR=0
+//      turns this off),
 //   3. Schur right-hand side  bhat = r_o - D_oe A_ee^-1 r_e,
 //   4. n_MR steps on Dhat = A_oo - D_oe A_ee^-1 D_eo from e_o = 0:
 //        p = Dhat rho, alpha = <p,rho>/<p,p>, e_o += alpha rho, rho -= alpha p,

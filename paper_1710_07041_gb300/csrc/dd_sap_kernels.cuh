@@ -22,8 +22,8 @@ int sap_launch_as_graph(const std::string &key, int variant, int nkernels, const
 // in HBM). With it, r = (b if SAP_FROM_B, else the block's stored residual
 // after its own previous solve) minus, with SAP_HALO_E, the hops from the
 // neighbouring blocks' latest corrections e: x changed only there since.
-// SAP_WRITE_E / SAP_WRITE_R store this phase's corrections and residuals for
-// the next phases.
+// SAP_WRITE_E / SAP_WRITE_R store this phase's corrections (as face flux
+// where flux_layout holds, else e itself) and residuals for the next phases.
 enum { SAP_INCR = 1, SAP_FROM_B = 2, SAP_HALO_E = 4, SAP_WRITE_E = 8, SAP_WRITE_R = 16 };
 
 namespace {
@@ -288,6 +288,264 @@ __device__ __forceinline__ void hops_global(const Geom &g, const Site &t, int h,
   }
 }
 
+// ---- the face flux of a block's correction (SAP_HALO_E, flux layout).
+// Halo entry q of a block: face f = 2 mu + (0: the block's upper face in mu,
+// 1: its lower face), faces in order, and position k on the face (the three
+// other directions in increasing order, the lowest fastest). When a block
+// has solved for its correction e, it computes for each of its face sites x
+// the hop of e(x) into the neighbouring block's site y = x +- mu and stores
+// it at the entry of y (the opposite face, same position) in that block's
+// part of the flux buffer: across its upper face W P e(x) with W =
+// U_mu(x)^dagger, its own link; across its lower face only P e(x), whose
+// link U_mu(y) belongs to the receiving block, which multiplies by it from
+// its own tile. Both carry the antiperiodic sign. The receiving block reads
+// its entries contiguously, instead of gathering e and the links of the
+// neighbours at scattered sites; an entry is 6 complex (rows of two pairs).
+__device__ __forceinline__ int face_area(const Geom &g, int mu) { return g.Vb >> g.lbd[mu]; }
+__device__ __forceinline__ int halo_entries(const Geom &g) {
+  return 2 * (face_area(g, 0) + face_area(g, 1) + face_area(g, 2) + face_area(g, 3));
+}
+__device__ __forceinline__ int face_offset(const Geom &g, int f) {
+  int o = 0;
+#pragma unroll
+  for (int mu = 0; mu < 4; mu++) o += (2 * mu < f ? face_area(g, mu) : 0) + (2 * mu + 1 < f ? face_area(g, mu) : 0);
+  return o;
+}
+// the flux layout: 32-bit arithmetic, and the buffer (6 complex per entry)
+// fits in a spinor field of the lattice (true for blocks of extent >= 4)
+template <typename C> __device__ __forceinline__ bool flux_layout(const Geom &g) {
+  return sizeof(C) == 4 && halo_entries(g) <= 2 * g.Vb;
+}
+// entry q -> face f and position k on it
+__device__ __forceinline__ void face_of(const Geom &g, int q, int &f, int &k) {
+  f = 0;
+  k = q;
+#pragma unroll
+  for (int ff = 0; ff < 7; ff++) {   // compile-time face directions
+    const int a = face_area(g, ff >> 1);
+    if (f == ff && k >= a) {
+      k -= a;
+      f++;
+    }
+  }
+}
+// the site at position k of face 2 MU + !UP of the block with coordinates
+// bc (compile-time directions: no register array is indexed at run time)
+template <int MU, bool UP> __device__ __forceinline__ Site face_site(const Geom &g, int b, const int *bc, int k) {
+  constexpr int D0 = MU == 0 ? 1 : 0, D1 = MU <= 1 ? 2 : 1, D2 = MU <= 2 ? 3 : 2;
+  Site t;
+  t.b = b;
+  t.lc[MU] = UP ? g.bd[MU] - 1 : 0;
+  t.lc[D0] = k & (g.bd[D0] - 1);
+  k >>= g.lbd[D0];
+  t.lc[D1] = k & (g.bd[D1] - 1);
+  t.lc[D2] = k >> g.lbd[D1];
+  t.p = parity_of(t.lc);
+  t.s = pos_of(g, t.lc);
+#pragma unroll
+  for (int d = 0; d < 4; d++) t.bc[d] = bc[d];
+  return t;
+}
+// position on the face normal to MU of the site with local coordinates lc
+template <int MU> __device__ __forceinline__ int face_pos(const Geom &g, const int *lc) {
+  constexpr int D0 = MU == 0 ? 1 : 0, D1 = MU <= 1 ? 2 : 1, D2 = MU <= 2 ? 3 : 2;
+  return lc[D0] + (lc[D1] << g.lbd[D0]) + (lc[D2] << (g.lbd[D0] + g.lbd[D1]));
+}
+
+template <typename P> struct alignas(2 * sizeof(P)) PairPair {
+  P a, b;
+};
+// entry q of block bb: rows c = 0..2 of two pairs at ((bb * 3 + c) * E + q)
+template <typename P, typename C>
+__device__ __forceinline__ void flux_store(void *H, int E, int bb, int q, const cpx<C> *v) {
+  PairPair<P> *p = (PairPair<P> *)H + (size_t)bb * 3 * E + q;
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+    p[(size_t)c * E] = {to_pair<P, C>(v[2 * c].re, v[2 * c].im), to_pair<P, C>(v[2 * c + 1].re, v[2 * c + 1].im)};
+}
+template <typename P, typename C>
+__device__ __forceinline__ void flux_load(const void *H, int E, int bb, int q, cpx<C> *v) {
+  const PairPair<P> *p = (const PairPair<P> *)H + (size_t)bb * 3 * E + q;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const PairPair<P> w = p[(size_t)c * E];
+    v[2 * c] = from_pair<C, P>(w.a);
+    v[2 * c + 1] = from_pair<C, P>(w.b);
+  }
+}
+
+// Entry k of face 2 MU + !UP of block b (coordinates bc) as producer: the
+// flux of e(x) into the neighbouring block's entry (see above)
+template <int MU, bool UP, typename S, typename C, typename P>
+__device__ __forceinline__ void flux_produce_entry(const Geom &g, int b, const int *bc, int k, const Tile<P> &Lt,
+                                                   const cpx<C> *ve, const cpx<C> *vo, int E, void *H) {
+  const Site t = face_site<MU, UP>(g, b, bc, k);
+  int nb, ns;
+  float sg;
+  bool inside;
+  neighbour(g, t, MU, UP ? +1 : -1, &nb, &ns, &sg, &inside);
+  Spinor<C> ev;
+  vec_load(t.p ? vo : ve, g.Vh, t.s - t.p * g.Vh, ev);
+  cpx<C> chi[6], out[6];
+  project<MU, !UP>(ev, chi);
+  if constexpr (UP) {
+    Link<C> u;
+    cpx<C> hv[6];
+    tile_link(Lt, t.s, MU, u);
+    su3_dmul(u, chi, hv);
+#pragma unroll
+    for (int i = 0; i < 6; i++) out[i] = {(C)sg * hv[i].re, (C)sg * hv[i].im};
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; i++) out[i] = {(C)sg * chi[i].re, (C)sg * chi[i].im};
+  }
+  // the receiving entry: the opposite face, same position
+  flux_store<P>(H, E, nb, face_offset(g, 2 * MU + (UP ? 1 : 0)) + k, out);
+}
+// A block's correction (even sites in ve, odd sites in vo: [12][Vh] shared
+// vectors) into the flux buffer H of its neighbours, one entry per thread
+// at a time.
+template <typename S, typename C, typename P>
+__device__ __forceinline__ void flux_produce(const Geom &g, int b, const int *bc, const Tile<P> &Lt, const cpx<C> *ve,
+                                             const cpx<C> *vo, void *H) {
+  const int E = halo_entries(g);
+#pragma unroll 1
+  for (int q = threadIdx.x; q < E; q += blockDim.x) {
+    int f, k;
+    face_of(g, q, f, k);
+    switch (f) {   // uniform across a warp where faces hold whole warps of entries
+      case 0: flux_produce_entry<0, true, S>(g, b, bc, k, Lt, ve, vo, E, H); break;
+      case 1: flux_produce_entry<0, false, S>(g, b, bc, k, Lt, ve, vo, E, H); break;
+      case 2: flux_produce_entry<1, true, S>(g, b, bc, k, Lt, ve, vo, E, H); break;
+      case 3: flux_produce_entry<1, false, S>(g, b, bc, k, Lt, ve, vo, E, H); break;
+      case 4: flux_produce_entry<2, true, S>(g, b, bc, k, Lt, ve, vo, E, H); break;
+      case 5: flux_produce_entry<2, false, S>(g, b, bc, k, Lt, ve, vo, E, H); break;
+      case 6: flux_produce_entry<3, true, S>(g, b, bc, k, Lt, ve, vo, E, H); break;
+      default: flux_produce_entry<3, false, S>(g, b, bc, k, Lt, ve, vo, E, H); break;
+    }
+  }
+}
+// entry q (face 2 MU + !UP, position k) as receiver: the upper faces'
+// projections multiplied by this block's link U_mu(y)
+template <int MU, bool UP, typename C, typename P>
+__device__ __forceinline__ void flux_receive_entry(const Geom &g, int k, int q, int E, const Tile<P> &Lt,
+                                                   const void *H, int b, cpx<C> *hs) {
+  cpx<C> v[6];
+  flux_load<P>(H, E, b, q, v);
+  if constexpr (UP) {
+    constexpr int D0 = MU == 0 ? 1 : 0, D1 = MU <= 1 ? 2 : 1, D2 = MU <= 2 ? 3 : 2;
+    int lc[4];
+    lc[MU] = g.bd[MU] - 1;
+    lc[D0] = k & (g.bd[D0] - 1);
+    k >>= g.lbd[D0];
+    lc[D1] = k & (g.bd[D1] - 1);
+    lc[D2] = k >> g.lbd[D1];
+    Link<C> u;
+    cpx<C> hv[6];
+    tile_link(Lt, pos_of(g, lc), MU, u);
+    su3_mul(u, v, hv);
+#pragma unroll
+    for (int i = 0; i < 6; i++) v[i] = hv[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 6; i++) hs[i * E + q] = v[i];
+}
+// The block's incoming flux into hs (shared, [6][E] complex); ends with a
+// barrier.
+template <typename S, typename C, typename P>
+__device__ __forceinline__ void flux_receive(const Geom &g, int b, const Tile<P> &Lt, const void *H, cpx<C> *hs) {
+  const int E = halo_entries(g);
+#pragma unroll 1
+  for (int q = threadIdx.x; q < E; q += blockDim.x) {
+    int f, k;
+    face_of(g, q, f, k);
+    switch (f) {
+      case 0: flux_receive_entry<0, true>(g, k, q, E, Lt, H, b, hs); break;
+      case 1: flux_receive_entry<0, false>(g, k, q, E, Lt, H, b, hs); break;
+      case 2: flux_receive_entry<1, true>(g, k, q, E, Lt, H, b, hs); break;
+      case 3: flux_receive_entry<1, false>(g, k, q, E, Lt, H, b, hs); break;
+      case 4: flux_receive_entry<2, true>(g, k, q, E, Lt, H, b, hs); break;
+      case 5: flux_receive_entry<2, false>(g, k, q, E, Lt, H, b, hs); break;
+      case 6: flux_receive_entry<3, true>(g, k, q, E, Lt, H, b, hs); break;
+      default: flux_receive_entry<3, false>(g, k, q, E, Lt, H, b, hs); break;
+    }
+  }
+  __syncthreads();
+}
+
+// acc (spin half h of a site) += sgn * that half of reconstruct(hv)
+template <int MU, bool FWD, typename C>
+__device__ __forceinline__ void recon_half(cpx<C> *acc, const cpx<C> *hv, int h, C sgn) {
+  if (h == 0) {
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+      acc[i].re = mad(sgn, hv[i].re, acc[i].re);
+      acc[i].im = mad(sgn, hv[i].im, acc[i].im);
+    }
+    return;
+  }
+  const C s = FWD ? -sgn : sgn;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const cpx<C> h0 = hv[c], h1 = hv[3 + c];
+    cpx<C> &l0 = acc[c], &l1 = acc[3 + c];
+    if constexpr (MU == 0) {
+      l0.re = mad(-s, h1.im, l0.re); l0.im = mad(s, h1.re, l0.im);
+      l1.re = mad(-s, h0.im, l1.re); l1.im = mad(s, h0.re, l1.im);
+    } else if constexpr (MU == 1) {
+      l0.re = mad(s, h1.re, l0.re); l0.im = mad(s, h1.im, l0.im);
+      l1.re = mad(-s, h0.re, l1.re); l1.im = mad(-s, h0.im, l1.im);
+    } else if constexpr (MU == 2) {
+      l0.re = mad(-s, h0.im, l0.re); l0.im = mad(s, h0.re, l0.im);
+      l1.re = mad(s, h1.im, l1.re); l1.im = mad(-s, h1.re, l1.im);
+    } else {
+      l0.re = mad(s, h0.re, l0.re); l0.im = mad(s, h0.im, l0.im);
+      l1.re = mad(s, h1.re, l1.re); l1.im = mad(s, h1.im, l1.im);
+    }
+  }
+}
+// the entry of site t's face in direction MU, if t lies on one
+template <int MU, typename C>
+__device__ __forceinline__ void flux_gather_dir(const Geom &g, const Site &t, int h, int E, const cpx<C> *hs,
+                                                cpx<C> *acc) {
+  const bool up = t.lc[MU] == g.bd[MU] - 1, lo = t.lc[MU] == 0;
+  if (!up && !lo) return;
+  const int q = face_offset(g, 2 * MU + (up ? 0 : 1)) + face_pos<MU>(g, t.lc);
+  cpx<C> hv[6];
+#pragma unroll
+  for (int i = 0; i < 6; i++) hv[i] = hs[i * E + q];
+  if (up) recon_half<MU, true>(acc, hv, h, (C)-0.5);
+  else recon_half<MU, false>(acc, hv, h, (C)-0.5);
+}
+// r (spin half h of the thread's even and odd site) -= the incoming hops
+template <typename C>
+__device__ __forceinline__ void flux_gather(const Geom &g, const Site &se, const Site &so, int h, const cpx<C> *hs,
+                                            cpx<C> *r_e, cpx<C> *r_o) {
+  const int E = halo_entries(g);
+  cpx<C> acc[6];
+#pragma unroll
+  for (int i = 0; i < 6; i++) acc[i] = {0, 0};
+  flux_gather_dir<0>(g, se, h, E, hs, acc);
+  flux_gather_dir<1>(g, se, h, E, hs, acc);
+  flux_gather_dir<2>(g, se, h, E, hs, acc);
+  flux_gather_dir<3>(g, se, h, E, hs, acc);
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    r_e[i].re -= acc[i].re;
+    r_e[i].im -= acc[i].im;
+    acc[i] = {0, 0};
+  }
+  flux_gather_dir<0>(g, so, h, E, hs, acc);
+  flux_gather_dir<1>(g, so, h, E, hs, acc);
+  flux_gather_dir<2>(g, so, h, E, hs, acc);
+  flux_gather_dir<3>(g, so, h, E, hs, acc);
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    r_o[i].re -= acc[i].re;
+    r_o[i].im -= acc[i].im;
+  }
+}
+
 // the six components of spin half h (selects, so the register arrays are
 // never indexed at run time)
 template <typename C>
@@ -535,6 +793,12 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
   }
   const Site se = decode(g, b, j), so = decode(g, b, Vh + j);
   const uint2 nbr_e = inner_neighbours(g, se, h), nbr_o = inner_neighbours(g, so, h);
+  // corrections travel between phases as face flux (32-bit arithmetic,
+  // blocks whose flux fits a spinor field; the same for every phase of the
+  // lattice), else as e itself
+  const bool flux = flux_layout<C>(g);
+  // the flux receiver multiplies by the staged links: wait for them first
+  const bool early = flux && (mode & SAP_INCR) && (mode & SAP_HALO_E);
   // right-hand sides blockIdx.y * tile ... share the staged tiles
 #pragma unroll 1
   for (int rr = 0; rr < tile; rr++) {
@@ -543,6 +807,21 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
     const void *bf = rp.in[r];
     void *xf = rp.out[r];
     cpx<C> r_e[6], r_o[6];
+    if constexpr (STAGE != 0) {
+      // the staging of this item completes phase `phase` of the barrier;
+      // a CTA whose wait expired leaves as a whole (the flag is raised)
+      if (rr == 0 && early) {
+        const bool ok = mbar_wait(mbar_s, phase);
+        if (__syncthreads_or(!ok)) {
+          wait_expired(timeouts, mbar_s, phase);
+          quit = true;
+          break;
+        }
+        phase ^= 1u;
+      }
+    }
+    if constexpr (sizeof(C) == 4)
+      if (early) flux_receive<S, C, P>(g, b, Lt, ax.e[r], rho);
 
     // ---- 2. block residual (halves h of the even and odd site): r = b - D x,
     // or incrementally (SAP_INCR) from the stored residual and the hops of
@@ -561,7 +840,10 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
       half_of(bb, h, r_o);
     }
     if (mode & SAP_INCR) {
-      if (mode & SAP_HALO_E) {
+      if (early) {
+        flux_gather(g, se, so, h, rho, r_e, r_o);
+        __syncthreads();
+      } else if (mode & SAP_HALO_E) {
   #pragma unroll 1
         for (int par = 0; par < 2; par++) {
           Spinor<C> part;
@@ -601,9 +883,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
       }
     }
     if constexpr (STAGE != 0) {
-      // the staging of this item completes phase `phase` of the barrier;
-      // a CTA whose wait expired leaves as a whole (the flag is raised)
-      if (rr == 0) {
+      if (rr == 0 && !early) {
         const bool ok = mbar_wait(mbar_s, phase);
         if (__syncthreads_or(!ok)) {
           wait_expired(timeouts, mbar_s, phase);
@@ -772,7 +1052,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
       const int s = h ? Vh + j : j;
       Spinor<C> xs, e;
       vec_load(src, Vh, j, e);
-      if (mode & SAP_WRITE_E) store_spinor<S, C>(ax.e[r], g, b, s, e);
+      if ((mode & SAP_WRITE_E) && !flux) store_spinor<S, C>(ax.e[r], g, b, s, e);
       if ((mode & SAP_WRITE_R) && h) {
         Spinor<C> rs;
         vec_load(rho, Vh, j, rs);
@@ -790,6 +1070,8 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
       }
       store_spinor<S, C>(xf, g, b, s, xs);
     }
+    if constexpr (sizeof(C) == 4)
+      if ((mode & SAP_WRITE_E) && flux) flux_produce<S, C, P>(g, b, se.bc, Lt, te, xch, ax.e[r]);
     __syncthreads();   // shared vectors are reused by the next right-hand side
   }
   if (quit) break;
