@@ -24,6 +24,9 @@ from gpu_common import Setup, relerr, worst_site
 pytestmark = pytest.mark.gpu
 
 TOL = {dd.F64: 1e-12, dd.F32: 5e-7, dd.F16: 1.5e-3, dd.BF16: 1.2e-2}
+# Between colour phases the 32-bit kernels pass corrections as face flux for
+# the 4^4 and 8 x 4^3 blocks and as the correction field e for the 2^4 and
+# 4 x 2 x 4 x 4 blocks (whose flux would not fit a spinor field); FP64 always e.
 CASES = [((4, 4, 4, 4), (2, 2, 2, 2), 4, 3),     # plain FP64 workload geometry (Vh = 8 < warp)
          ((8, 8, 8, 8), (4, 4, 4, 4), 2, 4),
          ((8, 8, 16, 8), (4, 4, 4, 4), 1, 4),
