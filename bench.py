@@ -8,8 +8,9 @@ smoother with 4^4 blocks, 4 sweeps x 4 MR steps in FP32 storage; FGMRES(16)
 whose Krylov basis and true-residual Dslash are double-float (FP32 pairs,
 ~48-bit significands) with an FP64 least-squares update and solution
 (--outer-f64: IEEE FP64 for those too). `config` names what ran.
-`mixed_96x48^3` adds apply_D and the Schwarz phase with FP16 and BF16
-storage on the 96 x 48^3 mixed-precision workload.
+`mixed_96x48^3` adds apply_D and the Schwarz phase with FP16, BF16 and
+F16N (FP16 operator tiles, spinors as 16-bit fixed point with a per-site
+scale) storage on the 96 x 48^3 mixed-precision workload.
 
 Prints one JSON line. `value` is solves/s with all inputs resident in HBM;
 `e2e` is the same metric through dd_solve with host buffers (host-to-device
@@ -487,11 +488,13 @@ def run_ours(args, rank, world):
 
 
 def mixed_kernels(dd, peaks, alu_peak, stream):
-    """apply_D and the Schwarz phase with FP16 and BF16 storage on the
+    """apply_D and the Schwarz phase with FP16, BF16 and F16N storage on the
     mixed-precision workload's 96 x 48^3 lattice (exp(i 0.2 H), 3 stout steps,
     c_sw 1.7, m0 0; 4^4 blocks, 4 MR steps): time, GB/s of algorithmic bytes
-    (apply_D 192 reals per site, a phase 252 reals per site of its colour)
-    and the phase's flop rate. Inputs far exceed L2 (one field 0.5 GB)."""
+    (apply_D 168 reals per site with two-row links, a phase 252 reals per
+    site of its colour, 2 bytes each; F16N adds its 4-byte site scales: 2 per
+    site for apply_D, 3 for a phase) and the phase's flop rate. Inputs far
+    exceed L2 (one field 0.5 GB)."""
     import torch
     wl = synth.WORKLOADS["sap_fgmres_96x48^3_mixed"]
     V = int(np.prod(wl["dims"]))
@@ -502,7 +505,8 @@ def mixed_kernels(dd, peaks, alu_peak, stream):
     b = synth.gaussian_spinor(V, wl["rhs_seed"])
     res = {"workload": "sap_fgmres_96x48^3_mixed", "dims_TZYX": list(wl["dims"]), "block_TZYX": list(wl["block"]),
            "mr_steps": wl["mr_steps"], "m0": wl["m0"]}
-    for name, prec in (("f16", dd.F16), ("bf16", dd.BF16)):
+    for name, prec in (("f16", dd.F16), ("bf16", dd.BF16), ("f16n", dd.F16N)):
+        scales = 4 if prec == dd.F16N else 0   # bytes of one site scale
         op = dd.Op(gauge, wl["c_sw"], wl["m0"], prec)
         fin, fout = lat.to_field(b, prec), lat.new_field(prec)
         for _ in range(5):
@@ -510,11 +514,12 @@ def mixed_kernels(dd, peaks, alu_peak, stream):
         ms_d = ev_time(lambda: op.apply_D(prec, fin, fout), 30, stream)
         op.sap_smooth(fin, fout, wl["sweeps"], wl["mr_steps"])
         ms_s = ev_time(lambda: op.sap_smooth(fin, fout, wl["sweeps"], wl["mr_steps"]), 3, stream) / (2 * wl["sweeps"])
-        gbs_d = DSLASH_REALS_12 * 2 * V / (ms_d * 1e-3) / 1e9
-        gbs_s = SAP_REALS_PER_SWEEP * 2 * (V / 2) / (ms_s * 1e-3) / 1e9
+        bytes_d, bytes_s = DSLASH_REALS_12 * 2 + 2 * scales, SAP_REALS_PER_SWEEP * 2 + 3 * scales
+        gbs_d = bytes_d * V / (ms_d * 1e-3) / 1e9
+        gbs_s = bytes_s * (V / 2) / (ms_s * 1e-3) / 1e9
         tf_s = sap_flops_per_site(wl["mr_steps"]) * (V / 2) / (ms_s * 1e-3) / 1e12
         res[name] = {"dslash": {"ms": ms_d, "GB/s": gbs_d, "frac_hbm": gbs_d / peaks["hbm_gbs"],
-                                "bytes_per_site": DSLASH_REALS_12 * 2},
+                                "bytes_per_site": bytes_d},
                      "sap_phase": {"ms": ms_s, "TFLOP/s": tf_s, "frac_fp32_peak": tf_s / alu_peak, "GB/s": gbs_s,
                                    "frac_hbm": gbs_s / peaks["hbm_gbs"]}}
         del fin, fout
@@ -849,7 +854,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
-    ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "bf16"])
+    ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "bf16", "f16n"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 96x48^3 FP16/BF16 kernel measurements")
     ap.add_argument("--outer-f64", action="store_true",

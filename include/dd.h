@@ -70,6 +70,17 @@ enum {
 
 /* storage precisions; arithmetic is FP32 for all but DD_F64 */
 enum { DD_F64 = 0, DD_F32 = 1, DD_F16 = 2, DD_BF16 = 3 };
+/* Half-precision storage with a per-site scale ("block-float"; the paper's
+ * half precision, Sec. 3.1, is plain FP16, the scale is this library's
+ * reduced-byte variant of it): spinor fields hold 16-bit fixed-point
+ * components q (|q| <= 32767) and per site one FP32 scale n, the largest
+ * modulus of its 24 real
+ * components, the value being q n / 32767 (q = round-to-nearest-even of
+ * v 32767 / n; n = 0 stores zeros); 52 bytes per site, block-major like the
+ * other fields (per block 3 chunk rows of 16 bytes x Vb sites, then Vb FP32
+ * scales). Operator tiles (links, clover, inverses) are stored as in DD_F16.
+ * Accepted wherever DD_F16 is, except by dd_create_mg (DD_EINVAL). */
+enum { DD_F16N = 5 };
 /* dd_apply_D only (no counterpart in the paper): FP64 input and output
  * fields, double-float arithmetic (pairs of FP32, ~48-bit significands) on
  * the operator's pre-split FP64 links and clover; the operator a
@@ -143,7 +154,7 @@ int dd_create_gauge(dd_lattice_t lat, const double *links_host, dd_gauge_t *out)
 
 /* Wilson-clover operator on `gauge` with clover coefficient c_sw and bare mass
  * m0, for the Schwarz smoother's storage precision `prec` (DD_F64, DD_F32,
- * DD_F16, DD_BF16). Builds on the device (FP64): the clover term C(n) from the
+ * DD_F16, DD_BF16, DD_F16N). Builds on the device (FP64): the clover term C(n) from the
  * four-leaf plaquette sum, A(n) = 4 + m0 + C(n) as two 6x6 Hermitian chirality
  * blocks per site, and the inverses of the even-site blocks; stores them in
  * FP64 (true residual), FP32 (outer-solver operator) and `prec` (smoother);

@@ -19,7 +19,8 @@ from . import build as _build
 
 F64, F32, F16, BF16 = 0, 1, 2, 3
 F64_DF = 4   # apply_D only: FP64 fields in and out, double-float arithmetic
-PREC = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+F16N = 5     # FP16 operator tiles, spinors as 16-bit fixed point with a per-site scale
+PREC = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "f16n": F16N}
 HOST, DEVICE = 0, 1
 QUEUED, RUNNING, DONE, FAILED, CANCELLED = 0, 1, 2, 3, 4
 ERRORS = {0: "DD_OK", -1: "DD_EINVAL", -2: "DD_ENOMEM", -3: "DD_ECUDA", -4: "DD_ENOTCONV",

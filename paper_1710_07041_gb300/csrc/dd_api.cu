@@ -84,7 +84,7 @@ void release_op(Op *op) {
   if (!op || --op->refs > 0) return;
   free_fields(op->f64);
   free_fields(op->f32);
-  if (op->prec == DD_F16 || op->prec == DD_BF16) free_fields(op->fp);
+  if (half_tiles(op->prec)) free_fields(op->fp);
   free_fields(op->fdf);
   release_gauge(op->gauge);
   op->magic = 0;
@@ -171,8 +171,8 @@ long dd_lattice_volume(dd_lattice_t lat) {
 
 size_t dd_field_bytes(dd_lattice_t lat, int prec) {
   Lattice *l = (Lattice *)lat;
-  if (!l || l->magic != MAGIC_LAT || prec < DD_F64 || prec > DD_BF16) return 0;
-  return (size_t)l->g.V * 24 * real_bytes(prec);
+  if (!l || l->magic != MAGIC_LAT || !storage_prec(prec)) return 0;
+  return (size_t)l->g.V * spinor_site_bytes(prec);
 }
 
 int dd_create_gauge(dd_lattice_t lat, const double *links, dd_gauge_t *out) {
@@ -236,7 +236,7 @@ static int create_op(Gauge *ga, double c_sw, double m0, int prec, Fill fill, dd_
   op->prec = prec;
   int rc = alloc_fields(g, DD_F64, op->f64);
   if (rc == DD_OK) rc = alloc_fields(g, DD_F32, op->f32);
-  if (rc == DD_OK && (prec == DD_F16 || prec == DD_BF16)) rc = alloc_fields(g, prec, op->fp);
+  if (rc == DD_OK && half_tiles(prec)) rc = alloc_fields(g, prec, op->fp);
   int *bad = nullptr;
   if (rc == DD_OK && cudaMalloc(&bad, sizeof(int)) != cudaSuccess) rc = DD_ENOMEM;
   cudaStream_t st = 0;
@@ -247,7 +247,7 @@ static int create_op(Gauge *ga, double c_sw, double m0, int prec, Fill fill, dd_
   if (rc == DD_OK) rc = launch_pack_links_full(g, DD_F32, ga->links_canon, op->f32.links_full, st);
   if (rc == DD_OK) rc = launch_convert_clover(DD_F32, (const double *)op->f64.clov, op->f32.clov, g.nblocks, g.Vb, st);
   if (rc == DD_OK) rc = launch_convert_clover(DD_F32, (const double *)op->f64.cinv, op->f32.cinv, g.nblocks, g.Vh, st);
-  if (rc == DD_OK && (prec == DD_F16 || prec == DD_BF16)) {
+  if (rc == DD_OK && half_tiles(prec)) {
     rc = launch_pack_links(g, prec, ga->links_canon, op->fp.links, bad, st);
     if (rc == DD_OK) rc = launch_pack_links_full(g, prec, ga->links_canon, op->fp.links_full, st);
     if (rc == DD_OK) rc = launch_convert_clover(prec, (const double *)op->f64.clov, op->fp.clov, g.nblocks, g.Vb, st);
@@ -297,7 +297,7 @@ extern "C" {
 
 int dd_create_op(dd_gauge_t gauge, double c_sw, double m0, int prec, dd_op_t *out) {
   Gauge *ga = (Gauge *)gauge;
-  if (!ga || ga->magic != MAGIC_GAUGE || !out || prec < DD_F64 || prec > DD_BF16 || !std::isfinite(c_sw) ||
+  if (!ga || ga->magic != MAGIC_GAUGE || !out || !storage_prec(prec) || !std::isfinite(c_sw) ||
       !std::isfinite(m0)) {
     set_error("dd_create_op: bad argument");
     return DD_EINVAL;
@@ -312,7 +312,7 @@ int dd_create_op(dd_gauge_t gauge, double c_sw, double m0, int prec, dd_op_t *ou
 
 int dd_create_op_clover(dd_gauge_t gauge, const double *clover_host, int prec, dd_op_t *out) {
   Gauge *ga = (Gauge *)gauge;
-  if (!ga || ga->magic != MAGIC_GAUGE || !clover_host || !out || prec < DD_F64 || prec > DD_BF16) {
+  if (!ga || ga->magic != MAGIC_GAUGE || !clover_host || !out || !storage_prec(prec)) {
     set_error("dd_create_op_clover: bad argument");
     return DD_EINVAL;
   }
@@ -388,7 +388,7 @@ void dd_destroy(void *h) {
 
 int dd_pack(dd_lattice_t lat, int prec, const double *canon, void *field, int nrhs, double scale, void *stream) {
   Lattice *l = (Lattice *)lat;
-  if (!l || l->magic != MAGIC_LAT || !canon || !field || nrhs < 1 || prec < DD_F64 || prec > DD_BF16) {
+  if (!l || l->magic != MAGIC_LAT || !canon || !field || nrhs < 1 || !storage_prec(prec)) {
     set_error("dd_pack: bad argument");
     return DD_EINVAL;
   }
@@ -397,7 +397,7 @@ int dd_pack(dd_lattice_t lat, int prec, const double *canon, void *field, int nr
 
 int dd_unpack(dd_lattice_t lat, int prec, const void *field, double *canon, int nrhs, double scale, void *stream) {
   Lattice *l = (Lattice *)lat;
-  if (!l || l->magic != MAGIC_LAT || !canon || !field || nrhs < 1 || prec < DD_F64 || prec > DD_BF16) {
+  if (!l || l->magic != MAGIC_LAT || !canon || !field || nrhs < 1 || !storage_prec(prec)) {
     set_error("dd_unpack: bad argument");
     return DD_EINVAL;
   }
@@ -446,7 +446,7 @@ int dd_sap_smooth(dd_op_t opp, const dd_sap_params *p, const void *b, void *x, i
   // them, e.g. when this allocation fails, every phase forms b - D x)
   cudaStream_t st = (cudaStream_t)stream;
   const Geom &g = op->lat->g;
-  const size_t fb = (size_t)g.V * 24 * real_bytes(op->fp.prec);
+  const size_t fb = (size_t)g.V * spinor_site_bytes(op->fp.prec);
   void *aux = nullptr;
   if (cudaMallocAsync(&aux, 2 * (size_t)nrhs * fb, st) != cudaSuccess) {
     cudaGetLastError();
@@ -474,7 +474,7 @@ int dd_sap_smooth_multi(int nops, const dd_op_t *ops, const int *nrhs, const dd_
       set_error("dd_sap_smooth_multi: bad operator %d or right-hand sides (at most %d in all)", k, MAX_RHS);
       return DD_EINVAL;
     }
-    const size_t fb = (size_t)op->lat->g.V * 24 * real_bytes(op->fp.prec);
+    const size_t fb = (size_t)op->lat->g.V * spinor_site_bytes(op->fp.prec);
     for (int r = 0; r < nrhs[k]; r++, rp.n++) {
       rp.in[rp.n] = (const char *)b[k] + r * fb;
       rp.out[rp.n] = (char *)x[k] + r * fb;
@@ -491,7 +491,7 @@ int dd_sap_smooth_multi(int nops, const dd_op_t *ops, const int *nrhs, const dd_
   }
   AuxPtrs ax{};
   for (int k = 0, i = 0; aux && k < nops; k++) {
-    const size_t fb = (size_t)lats[k].g.V * 24 * real_bytes(lats[k].f.prec);
+    const size_t fb = (size_t)lats[k].g.V * spinor_site_bytes(lats[k].f.prec);
     for (int r = 0; r < nrhs[k]; r++, i++) {
       ax.e[i] = aux;
       ax.r[i] = aux + fb;

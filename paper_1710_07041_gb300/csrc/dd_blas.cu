@@ -583,6 +583,7 @@ int Blas::df_to_field(const Geom &g, const float *in, int prec, void *out, doubl
     case DD_F32: k_df_to_field<float><<<grid, 128, 0, st>>>(g, x, out, (float)scale); break;
     case DD_F16: k_df_to_field<__half><<<grid, 128, 0, st>>>(g, x, out, (float)scale); break;
     case DD_BF16: k_df_to_field<__nv_bfloat16><<<grid, 128, 0, st>>>(g, x, out, (float)scale); break;
+    case DD_F16N: k_df_to_field<hn16><<<grid, 128, 0, st>>>(g, x, out, (float)scale); break;
     default: set_error("df_to_field: bad precision"); return DD_EINVAL;
   }
   return launched("k_df_to_field");

@@ -122,6 +122,7 @@ int launch_dirac(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_
     case DD_F32: return dirac_t<float>(g, f, p, st);
     case DD_F16: return dirac_t<__half>(g, f, p, st);
     case DD_BF16: return dirac_t<__nv_bfloat16>(g, f, p, st);
+    case DD_F16N: return dirac_t<hn16>(g, f, p, st);
   }
   set_error("apply_D: precision %d not available", f.prec);
   return DD_EINVAL;
@@ -136,7 +137,7 @@ int launch_dirac_df(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStre
 }
 
 int launch_dirac(const Geom &g, const OpFields &f, const void *in, void *out, int nrhs, cudaStream_t st) {
-  const size_t fb = (size_t)g.V * 24 * real_bytes(f.prec);
+  const size_t fb = (size_t)g.V * spinor_site_bytes(f.prec);
   for (int r0 = 0; r0 < nrhs; r0 += MAX_RHS) {
     int n = nrhs - r0 < MAX_RHS ? nrhs - r0 : MAX_RHS;
     int rc = launch_dirac(g, f, contiguous((const char *)in + r0 * fb, (char *)out + r0 * fb, n, fb), st);

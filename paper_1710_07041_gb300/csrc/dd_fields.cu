@@ -26,8 +26,19 @@ __global__ void k_pack(Geom g, const double2 *__restrict__ canon, void *field, i
   // narrow directly from the FP64 product so every value is rounded once
   // (round-to-nearest-even for FP16/BF16)
   constexpr int NC = spinor_chunks<S>();
-  char *base = (char *)field + r * field_bytes + (((size_t)b * NC) * g.Vb + s) * 16;
+  char *base = (char *)field + r * field_bytes + (size_t)b * g.Vb * spinor_site_bytes(Store<S>::prec) + (size_t)s * 16;
   const size_t cstride = (size_t)g.Vb * 16;
+  if constexpr (Store<S>::prec == DD_F16N) {
+    // the scale and every component from the FP64 product, each rounded once
+    double a[24];
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+      a[2 * i] = src[i].x * scale;
+      a[2 * i + 1] = src[i].y * scale;
+    }
+    store_fixed16(base, cstride, NC, s, a);
+    return;
+  }
   using P = typename Store<S>::pair_t;
   constexpr int PPC = Store<S>::reals_per_chunk / 2;  // complex entries per chunk
 #pragma unroll
@@ -329,20 +340,20 @@ __global__ void k_load_clover(Geom g, const double2 *__restrict__ A_canon, doubl
 }
 
 template <typename S> int pack_t(const Geom &g, const double *canon, void *field, int nrhs, double scale, cudaStream_t st) {
-  size_t fb = (size_t)g.V * 24 * sizeof(S);
+  size_t fb = field_bytes(g, Store<S>::prec);
   k_pack<S><<<grid_for(g.V * nrhs), TPB, 0, st>>>(g, (const double2 *)canon, field, nrhs, scale, fb);
   return launched("k_pack");
 }
 template <typename S> int unpack_t(const Geom &g, const void *field, double *canon, int nrhs, double scale, cudaStream_t st) {
-  size_t fb = (size_t)g.V * 24 * sizeof(S);
+  size_t fb = field_bytes(g, Store<S>::prec);
   k_unpack<S><<<grid_for(g.V * nrhs), TPB, 0, st>>>(g, field, (double2 *)canon, nrhs, scale, fb);
   return launched("k_unpack");
 }
 
 template <typename SI, typename SO>
 int convert_t(const Geom &g, const void *in, void *out, int nrhs, double scale, cudaStream_t st) {
-  k_convert_field<SI, SO><<<grid_for(g.V * nrhs), TPB, 0, st>>>(g, in, out, nrhs, scale, (size_t)g.V * 24 * sizeof(SI),
-                                                                (size_t)g.V * 24 * sizeof(SO));
+  k_convert_field<SI, SO><<<grid_for(g.V * nrhs), TPB, 0, st>>>(g, in, out, nrhs, scale, field_bytes(g, Store<SI>::prec),
+                                                                field_bytes(g, Store<SO>::prec));
   return launched("k_convert_field");
 }
 
@@ -353,6 +364,7 @@ int convert_out(const Geom &g, const void *in, int po, void *out, int nrhs, doub
     case DD_F32: return convert_t<SI, float>(g, in, out, nrhs, scale, st);
     case DD_F16: return convert_t<SI, __half>(g, in, out, nrhs, scale, st);
     case DD_BF16: return convert_t<SI, __nv_bfloat16>(g, in, out, nrhs, scale, st);
+    case DD_F16N: return convert_t<SI, hn16>(g, in, out, nrhs, scale, st);
   }
   set_error("bad precision %d", po);
   return DD_EINVAL;
@@ -366,6 +378,7 @@ int launch_pack(const Geom &g, int prec, const double *canon, void *field, int n
     case DD_F32: return pack_t<float>(g, canon, field, nrhs, scale, st);
     case DD_F16: return pack_t<__half>(g, canon, field, nrhs, scale, st);
     case DD_BF16: return pack_t<__nv_bfloat16>(g, canon, field, nrhs, scale, st);
+    case DD_F16N: return pack_t<hn16>(g, canon, field, nrhs, scale, st);
   }
   set_error("bad precision %d", prec);
   return DD_EINVAL;
@@ -377,6 +390,7 @@ int launch_unpack(const Geom &g, int prec, const void *field, double *canon, int
     case DD_F32: return unpack_t<float>(g, field, canon, nrhs, scale, st);
     case DD_F16: return unpack_t<__half>(g, field, canon, nrhs, scale, st);
     case DD_BF16: return unpack_t<__nv_bfloat16>(g, field, canon, nrhs, scale, st);
+    case DD_F16N: return unpack_t<hn16>(g, field, canon, nrhs, scale, st);
   }
   set_error("bad precision %d", prec);
   return DD_EINVAL;
@@ -389,7 +403,8 @@ int launch_convert_clover(int prec, const double *in, void *out, size_t ntiles, 
   switch (prec) {
     case DD_F64: k_convert_clover<double2><<<grid, TPB, 0, st>>>(c, (double2 *)out, ntiles, n); break;
     case DD_F32: k_convert_clover<float2><<<grid, TPB, 0, st>>>(c, (float2 *)out, ntiles, n); break;
-    case DD_F16: k_convert_clover<__half2><<<grid, TPB, 0, st>>>(c, (__half2 *)out, ntiles, n); break;
+    case DD_F16:
+    case DD_F16N: k_convert_clover<__half2><<<grid, TPB, 0, st>>>(c, (__half2 *)out, ntiles, n); break;
     case DD_BF16: k_convert_clover<__nv_bfloat162><<<grid, TPB, 0, st>>>(c, (__nv_bfloat162 *)out, ntiles, n); break;
     default: set_error("bad precision %d", prec); return DD_EINVAL;
   }
@@ -403,6 +418,7 @@ int launch_convert_field(const Geom &g, int pi, const void *in, int po, void *ou
     case DD_F32: return convert_out<float>(g, in, po, out, nrhs, scale, st);
     case DD_F16: return convert_out<__half>(g, in, po, out, nrhs, scale, st);
     case DD_BF16: return convert_out<__nv_bfloat16>(g, in, po, out, nrhs, scale, st);
+    case DD_F16N: return convert_out<hn16>(g, in, po, out, nrhs, scale, st);
   }
   set_error("bad precision %d", pi);
   return DD_EINVAL;
@@ -413,7 +429,8 @@ int launch_pack_links(const Geom &g, int prec, const double *canon, void *out, i
   switch (prec) {
     case DD_F64: k_pack_links<double2><<<grid_for(g.V), TPB, 0, st>>>(g, c, (double2 *)out, bad); break;
     case DD_F32: k_pack_links<float2><<<grid_for(g.V), TPB, 0, st>>>(g, c, (float2 *)out, bad); break;
-    case DD_F16: k_pack_links<__half2><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__half2 *)out, bad); break;
+    case DD_F16:
+    case DD_F16N: k_pack_links<__half2><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__half2 *)out, bad); break;
     case DD_BF16:
       k_pack_links<__nv_bfloat162><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__nv_bfloat162 *)out, bad);
       break;
@@ -427,7 +444,8 @@ int launch_pack_links_full(const Geom &g, int prec, const double *canon, void *o
   switch (prec) {
     case DD_F64: k_pack_links<double2, 9, false><<<grid_for(g.V), TPB, 0, st>>>(g, c, (double2 *)out, nullptr); break;
     case DD_F32: k_pack_links<float2, 9, false><<<grid_for(g.V), TPB, 0, st>>>(g, c, (float2 *)out, nullptr); break;
-    case DD_F16: k_pack_links<__half2, 9, false><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__half2 *)out, nullptr); break;
+    case DD_F16:
+    case DD_F16N: k_pack_links<__half2, 9, false><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__half2 *)out, nullptr); break;
     case DD_BF16:
       k_pack_links<__nv_bfloat162, 9, false><<<grid_for(g.V), TPB, 0, st>>>(g, c, (__nv_bfloat162 *)out, nullptr);
       break;

@@ -240,6 +240,15 @@ template <> struct Store<__nv_bfloat16> {
   using pair_t = __nv_bfloat162;
   using comp_t = float;
 };
+// DD_F16N: spinors as 16-bit fixed point with a per-site FP32 scale (see
+// dd.h), operator tiles as FP16 pairs
+struct hn16 {};
+template <> struct Store<hn16> {
+  static constexpr int prec = DD_F16N;
+  static constexpr int reals_per_chunk = 8;   // 8 int16 in a uint4
+  using pair_t = __half2;
+  using comp_t = float;
+};
 
 // Double-float numbers: an unevaluated sum hi + lo of two FP32 values
 // (|lo| <= ulp(hi) / 2), about 48 significant bits, from error-free FP32
@@ -331,6 +340,17 @@ template <int CP> __host__ __device__ constexpr int clover_slot(int h, int k) {
 }
 
 inline size_t real_bytes(int prec) { return (prec == DD_F64 || prec == DD_PREC_DF) ? 8 : prec == DD_F32 ? 4 : 2; }
+// bytes per site of a spinor field (DD_F16N: 24 int16 and one FP32 scale)
+__host__ __device__ constexpr size_t spinor_site_bytes(int prec) {
+  return prec == DD_F16N ? 52 : 24 * ((prec == DD_F64 || prec == DD_PREC_DF) ? 8 : prec == DD_F32 ? 4 : 2);
+}
+inline size_t field_bytes(const Geom &g, int prec) { return (size_t)g.V * spinor_site_bytes(prec); }
+// the storage precisions an operator or field may have
+inline bool storage_prec(int prec) {
+  return prec == DD_F64 || prec == DD_F32 || prec == DD_F16 || prec == DD_BF16 || prec == DD_F16N;
+}
+// 16-bit operator tiles (a separate smoother copy of the operator)
+inline bool half_tiles(int prec) { return prec == DD_F16 || prec == DD_BF16 || prec == DD_F16N; }
 inline size_t pair_bytes(int prec) { return 2 * real_bytes(prec); }
 
 template <typename S> __host__ __device__ constexpr int spinor_chunks() { return 24 / Store<S>::reals_per_chunk; }
@@ -381,15 +401,50 @@ __device__ __forceinline__ double to_d(double v) { return v; }
 __device__ __forceinline__ double to_d(float v) { return (double)v; }
 __device__ __forceinline__ double to_d(dfl v) { return (double)v.hi + (double)v.lo; }
 
+// One site of a DD_F16N field from its 24 real components a (FP32): the
+// scale n = max |a_i| (FP32), q_i = round-to-nearest-even(a_i 32767 / n),
+// |q_i| <= 32767 (n = 0: zeros). base: the site's first chunk; cstride: bytes
+// between chunk rows; the scale row follows the NC chunk rows.
+template <typename R>
+__device__ __forceinline__ void store_fixed16(char *base, size_t cstride, int NC, int s, const R *a) {
+  R m = 0;
+#pragma unroll
+  for (int i = 0; i < 24; i++) m = fmax(m, fabs(a[i]));
+  const float n = (float)m;
+  const R inv = n > 0.0f ? (R)32767 / (R)n : (R)0;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    uint4 w;
+    short *q = (short *)&w;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const R x = a[8 * c + k] * inv;
+      q[k] = (short)fmin(fmax(rint(x), (R)-32767), (R)32767);
+    }
+    *(uint4 *)(base + c * cstride) = w;
+  }
+  ((float *)(base - (size_t)s * 16 + NC * cstride))[s] = n;
+}
+
 // Load spinor (b, s) from a field of storage S.
 template <typename S, typename C>
 __device__ __forceinline__ void load_spinor(const void *field, const Geom &g, int b, int s, Spinor<C> &out) {
   DD_CHECK_INDEX(b, g.nblocks);
   DD_CHECK_INDEX(s, g.Vb);
   constexpr int NC = spinor_chunks<S>();
-  const char *base = (const char *)field + (((size_t)b * NC) * g.Vb + s) * 16;
+  const char *base = (const char *)field + (size_t)b * g.Vb * spinor_site_bytes(Store<S>::prec) + (size_t)s * 16;
   const size_t cstride = (size_t)g.Vb * 16;
-  if constexpr (Store<S>::prec == DD_F64) {
+  if constexpr (Store<S>::prec == DD_F16N) {
+    // the site's scale follows the block's NC chunk rows
+    const float n = __ldg((const float *)(base - (size_t)s * 16 + NC * cstride) + s) * (1.0f / 32767.0f);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const uint4 v = __ldg((const uint4 *)(base + c * cstride));
+      const short *q = (const short *)&v;
+#pragma unroll
+      for (int k = 0; k < 4; k++) out.c[4 * c + k] = {(C)((float)q[2 * k] * n), (C)((float)q[2 * k + 1] * n)};
+    }
+  } else if constexpr (Store<S>::prec == DD_F64) {
 #pragma unroll
     for (int c = 0; c < 12; c++) {
       double2 v = __ldg((const double2 *)(base + c * cstride));
@@ -422,9 +477,17 @@ __device__ __forceinline__ void store_spinor(void *field, const Geom &g, int b, 
   DD_CHECK_INDEX(b, g.nblocks);
   DD_CHECK_INDEX(s, g.Vb);
   constexpr int NC = spinor_chunks<S>();
-  char *base = (char *)field + (((size_t)b * NC) * g.Vb + s) * 16;
+  char *base = (char *)field + (size_t)b * g.Vb * spinor_site_bytes(Store<S>::prec) + (size_t)s * 16;
   const size_t cstride = (size_t)g.Vb * 16;
-  if constexpr (Store<S>::prec == DD_F64) {
+  if constexpr (Store<S>::prec == DD_F16N) {
+    float a[24];
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+      a[2 * i] = (float)to_d(v.c[i].re);
+      a[2 * i + 1] = (float)to_d(v.c[i].im);
+    }
+    store_fixed16(base, cstride, NC, s, a);
+  } else if constexpr (Store<S>::prec == DD_F64) {
 #pragma unroll
     for (int c = 0; c < 12; c++) *(double2 *)(base + c * cstride) = make_double2(to_d(v.c[c].re), to_d(v.c[c].im));
   } else if constexpr (Store<S>::prec == DD_F32) {

@@ -667,7 +667,7 @@ MgWork::~MgWork() {
 int MgWork::init(const Mg *mg) {
   const Geom &g = mg->op->lat->g;
   nc = (size_t)g.nblocks * 2 * mg->N;
-  const size_t f32 = (size_t)g.V * 24 * 4, fp = (size_t)g.V * 24 * real_bytes(mg->op->prec);
+  const size_t f32 = (size_t)g.V * 24 * 4, fp = (size_t)g.V * spinor_site_bytes(mg->op->prec);
   const int kmax = mg->p.coarse_max_iter;
   bool ok = cudaMalloc(&Vc, sizeof(float2) * nc * (kmax + 1)) == cudaSuccess &&
             cudaMalloc(&w, sizeof(float2) * nc) == cudaSuccess && cudaMalloc(&w2, sizeof(float2) * nc) == cudaSuccess &&
@@ -966,6 +966,10 @@ int dd_create_mg(dd_op_t opp, const dd_mg_params *p, const double *tv_host, dd_m
   const Geom &g = op->lat->g;
   if (g.Vb > MG_TPB) {
     set_error("dd_create_mg: aggregates (Schwarz blocks) of more than %d sites are not supported", MG_TPB);
+    return DD_EINVAL;
+  }
+  if (op->prec == DD_F16N) {
+    set_error("dd_create_mg: operators with DD_F16N storage are not supported");
     return DD_EINVAL;
   }
   Mg *mg = new (std::nothrow) Mg;

@@ -89,7 +89,7 @@ constexpr int MAXM = 64;
 size_t noalloc_bytes_needed(const Geom &g, int prec, int m, int nblk) {
   const int zprec = prec == DD_F64 ? DD_F64 : DD_F32;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-  size_t f64 = (size_t)g.V * 24 * 8, fz = (size_t)g.V * 24 * real_bytes(zprec), fp = (size_t)g.V * 24 * real_bytes(prec);
+  size_t f64 = (size_t)g.V * 24 * 8, fz = (size_t)g.V * spinor_site_bytes(zprec), fp = (size_t)g.V * spinor_site_bytes(prec);
   return al(sizeof(double) * (size_t)nblk * 33) + al(sizeof(double) * 256) + al(sizeof(double) * 136) +
          al(sizeof(double) * 2 * MAXM) + (size_t)(m + 1) * al(f64) + (size_t)m * al(fz) + 4 * al(f64) + 4 * al(fp) +
          al(fz);
@@ -134,7 +134,7 @@ extern "C" int dd_solve_noalloc(dd_op_t opp, const dd_solve_params *p, const dou
   const int zprec = op->prec == DD_F64 ? DD_F64 : DD_F32;
   const bool df = zprec == DD_F32 && !p->outer_f64;
   const size_t n = (size_t)g.V * 12, f64 = (size_t)g.V * 24 * 8;
-  const size_t fz = (size_t)g.V * 24 * real_bytes(zprec), fp = (size_t)g.V * 24 * real_bytes(op->prec);
+  const size_t fz = (size_t)g.V * spinor_site_bytes(zprec), fp = (size_t)g.V * spinor_site_bytes(op->prec);
   const size_t fz_al = (fz + 255) / 256 * 256, f64_al = (f64 + 255) / 256 * 256;
   Carve cv{(char *)base};
   Blas bl;

@@ -87,6 +87,8 @@ int sap_run_f32(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPt
                 const AuxPtrs *ax, cudaStream_t st);
 int sap_run_f16(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp,
                 const AuxPtrs *ax, cudaStream_t st);
+int sap_run_f16n(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp,
+                 const AuxPtrs *ax, cudaStream_t st);
 int sap_run_bf16(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp,
                 const AuxPtrs *ax, cudaStream_t st);
 
@@ -203,13 +205,14 @@ size_t sap_smem_bytes(const Geom &g, int prec, bool stage) {
     case DD_F64: return SapSmem<double>::bytes(g, stage ? 1 : 0);
     case DD_F32: return SapSmem<float>::bytes(g, stage ? 1 : 0);
     case DD_F16: return SapSmem<__half>::bytes(g, stage ? 1 : 0);
+    case DD_F16N: return SapSmem<hn16>::bytes(g, stage ? 1 : 0);
     default: return SapSmem<__nv_bfloat16>::bytes(g, stage ? 1 : 0);
   }
 }
 
 int launch_sap(const Geom &g, const OpFields &f, const dd_sap_params &p, const void *b, void *x, int nrhs,
                cudaStream_t st, void *aux_base) {
-  const size_t fb = (size_t)g.V * 24 * real_bytes(f.prec);
+  const size_t fb = (size_t)g.V * spinor_site_bytes(f.prec);
   for (int r0 = 0; r0 < nrhs; r0 += MAX_RHS) {
     int n = nrhs - r0 < MAX_RHS ? nrhs - r0 : MAX_RHS;
     AuxPtrs ax{};
@@ -277,6 +280,7 @@ int launch_sap_lattices(const SapLattice *L, int nl, const dd_sap_params &p, con
     case DD_F32: return sap_run_f32(L, nl, p, rp, ax, st);
     case DD_F16: return sap_run_f16(L, nl, p, rp, ax, st);
     case DD_BF16: return sap_run_bf16(L, nl, p, rp, ax, st);
+    case DD_F16N: return sap_run_f16n(L, nl, p, rp, ax, st);
   }
   set_error("sap: bad precision %d", f.prec);
   return DD_EINVAL;

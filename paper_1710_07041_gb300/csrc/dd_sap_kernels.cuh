@@ -729,11 +729,14 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
     for (int q = 0; q < tile; q++) {
       const int r = nrt * tile + q;
       if (r >= nnrhs) break;
-      const size_t off = (size_t)nb * NC * Vb * 16;
-      if (from_b) prefetch_l2((const char *)rp.in[nrhs0 + r] + off, NC * Vb * 16u);
+      // a block of a spinor field: NC chunk rows of Vb x 16 bytes (then, for
+      // DD_F16N, Vb FP32 scales), contiguous
+      constexpr unsigned SB = (unsigned)spinor_site_bytes(Store<S>::prec);
+      const size_t off = (size_t)nb * Vb * SB;
+      if (from_b) prefetch_l2((const char *)rp.in[nrhs0 + r] + off, Vb * SB);
       else
         for (int c = 0; c < NC; c++) prefetch_l2((const char *)ax.r[nrhs0 + r] + off + ((size_t)c * Vb + Vh) * 16, Vh * 16u);
-      if (!self_zero) prefetch_l2((const char *)rp.out[nrhs0 + r] + off, NC * Vb * 16u);
+      if (!self_zero) prefetch_l2((const char *)rp.out[nrhs0 + r] + off, Vb * SB);
     }
   }
 
@@ -1175,7 +1178,9 @@ int sap_u(const SapLattice *L, int nl, const dd_sap_params &p, const RhsPtrs &rp
   return sap_k<S, STAGE, MINB, NT, SH, true>(L, nl, p, rp, ax, tile, persistent, st);
 }
 
-template <typename S> constexpr bool sixteen_bit() { return Store<S>::prec == DD_F16 || Store<S>::prec == DD_BF16; }
+template <typename S> constexpr bool sixteen_bit() {
+  return Store<S>::prec == DD_F16 || Store<S>::prec == DD_BF16 || Store<S>::prec == DD_F16N;
+}
 
 // Launch variants: tiles staged in shared memory with one CTA per SM; tiles
 // staged with two CTAs per SM (fits when the storage is 16-bit); only the

@@ -54,7 +54,7 @@ int check_solve_params(const dd_solve_params *p) {
 size_t BatchSolver::bytes_per_slot(const Geom &g, int prec, int m) {
   size_t f64 = (size_t)g.V * 24 * 8;
   int zprec = prec == DD_F64 ? DD_F64 : DD_F32;
-  size_t fz = (size_t)g.V * 24 * real_bytes(zprec), fp = (size_t)g.V * 24 * real_bytes(prec);
+  size_t fz = (size_t)g.V * spinor_site_bytes(zprec), fp = (size_t)g.V * spinor_site_bytes(prec);
   return (size_t)(m + 1) * f64 + (size_t)m * fz + 4 * f64 + 4 * fp + fz;
 }
 
@@ -70,8 +70,8 @@ BatchSolver::BatchSolver(const Op *op, const dd_solve_params &p, int slots, cuda
 // walk the same list).
 std::vector<std::pair<void **, size_t>> BatchSolver::slot_buffers(Slot &s, long long V) const {
   const size_t m = (size_t)m_alloc_;
-  const size_t f64 = (size_t)V * 24 * 8, fz = (size_t)V * 24 * real_bytes(zprec_),
-               fp = (size_t)V * 24 * real_bytes(op_->prec);
+  const size_t f64 = (size_t)V * 24 * 8, fz = (size_t)V * spinor_site_bytes(zprec_),
+               fp = (size_t)V * spinor_site_bytes(op_->prec);
   return {{(void **)&s.Vb, (m + 1) * f64}, {(void **)&s.Z, m * fz},   {(void **)&s.x, f64},
           {(void **)&s.b, f64},           {(void **)&s.w, f64},       {(void **)&s.canon, f64},
           {&s.tin, fp},                   {&s.tout, fp},              {&s.zt, fz},
@@ -108,8 +108,8 @@ int BatchSolver::size_slot(Slot &s, const Op *op) {
   const Geom &g = op->lat->g;
   s.op = op;
   s.f64 = (size_t)g.V * 24 * 8;
-  s.fz = (size_t)g.V * 24 * real_bytes(zprec_);
-  s.fp = (size_t)g.V * 24 * real_bytes(op->prec);
+  s.fz = (size_t)g.V * spinor_site_bytes(zprec_);
+  s.fp = (size_t)g.V * spinor_site_bytes(op->prec);
   s.sigma = std::sqrt(24.0 * (double)g.V);  // unit-norm vector -> unit RMS entries
   if (s.vol >= g.V) return DD_OK;
   int rc = free_slot(s);

@@ -44,7 +44,10 @@ def test_lattice_validation_on_host():
     assert lat.field_bytes(dd.F64) == lat.V * 24 * 8
     assert lat.field_bytes(dd.F32) == lat.V * 24 * 4
     assert lat.field_bytes(dd.F16) == lat.field_bytes(dd.BF16) == lat.V * 24 * 2
+    # 16-bit fixed point with one FP32 scale per site
+    assert lat.field_bytes(dd.F16N) == lat.V * (24 * 2 + 4)
     assert L.dd_field_bytes(lat.handle, 7) == 0
+    assert L.dd_field_bytes(lat.handle, dd.F64_DF) == 0   # not a storage format
     lat.close()
 
 

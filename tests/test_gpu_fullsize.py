@@ -91,7 +91,7 @@ def mixed_problem():
     lat.close()
 
 
-@pytest.mark.parametrize("prec,tol", [(dd.F16, 1e-3), (dd.BF16, 1e-2)])
+@pytest.mark.parametrize("prec,tol", [(dd.F16, 1e-3), (dd.BF16, 1e-2), (dd.F16N, 1e-3)])
 def test_mixed_workload_dslash_sampled(mixed_problem, prec, tol):
     U, b, lat, gauge = mixed_problem
     op = dd.Op(gauge, W3["c_sw"], W3["m0"], prec)
@@ -106,7 +106,7 @@ def test_mixed_workload_dslash_sampled(mixed_problem, prec, tol):
     op.close()
 
 
-@pytest.mark.parametrize("prec", [dd.F16, dd.BF16])
+@pytest.mark.parametrize("prec", [dd.F16, dd.BF16, dd.F16N])
 def test_mixed_workload_solves(mixed_problem, prec):
     U, b, lat, gauge = mixed_problem
     op = dd.Op(gauge, W3["c_sw"], W3["m0"], prec)

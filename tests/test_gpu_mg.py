@@ -145,3 +145,14 @@ def test_two_level_refuses_512_site_aggregates():
         dd.Multigrid(s.op, tv, setup_iters=0, coarse_max_iter=8)
     assert e.value.code == -1 and "256" in str(e.value)
     s.close()
+
+
+def test_two_level_refuses_f16n_operators():
+    """The two-level set-up has no DD_F16N path: such an operator is refused
+    with DD_EINVAL before any work."""
+    s = Setup((8, 8, 8, 8), (4, 4, 4, 4), prec=dd.F16N, seed=73)
+    tv = np.stack([synth.gaussian_spinor(s.V, 74 + k) for k in range(4)])
+    with pytest.raises(dd.DDError) as e:
+        dd.Multigrid(s.op, tv, setup_iters=0, coarse_max_iter=8)
+    assert e.value.code == -1 and "F16N" in str(e.value)
+    s.close()

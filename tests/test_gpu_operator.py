@@ -2,7 +2,10 @@
 
 Tolerances (relative L2 over the whole result): FP64 1e-13; FP32 1e-6 and
 FP16 1e-3 (the Dslash bounds the specification states); BF16 1e-2, derived
-from its unit roundoff 2^-8 = 3.9e-3 on inputs, links and clover. Inputs are
+from its unit roundoff 2^-8 = 3.9e-3 on inputs, links and clover; F16N (FP16
+operator tiles, spinors in 16-bit fixed point with a per-site scale) 1e-3,
+as FP16: its tiles round as FP16's, its spinors to 2^-16 of the site's
+largest component, well inside that bound. Inputs are
 rounded to the storage precision by the library, the oracle gets the exact
 FP64 values, so the bound covers storage rounding end to end.
 """
@@ -16,7 +19,7 @@ from gpu_common import Setup, relerr
 
 pytestmark = pytest.mark.gpu
 
-TOL = {dd.F64: 1e-13, dd.F32: 1e-6, dd.F16: 1e-3, dd.BF16: 1e-2}
+TOL = {dd.F64: 1e-13, dd.F32: 1e-6, dd.F16: 1e-3, dd.BF16: 1e-2, dd.F16N: 1e-3}
 SHAPES = [((4, 4, 4, 4), (2, 2, 2, 2)), ((8, 4, 4, 12), (2, 2, 2, 2)), ((8, 8, 8, 8), (4, 4, 4, 4)),
           ((16, 8, 8, 8), (4, 4, 2, 4)), ((16, 8, 8, 8), (8, 4, 4, 4))]
 
@@ -32,7 +35,7 @@ def test_clover_blocks_match_oracle(dims, block):
     s.close()
 
 
-@pytest.mark.parametrize("prec", [dd.F64, dd.F32, dd.F16, dd.BF16])
+@pytest.mark.parametrize("prec", [dd.F64, dd.F32, dd.F16, dd.BF16, dd.F16N])
 @pytest.mark.parametrize("dims,block", SHAPES)
 def test_apply_D_matches_oracle(prec, dims, block):
     s = Setup(dims, block, eps=0.3, n_stout=1, c_sw=1.7, m0=-0.02, prec=prec, seed=7)
@@ -90,6 +93,37 @@ def test_pack_rounds_to_nearest_even(prec):
     r = rounders[prec]
     want = r(psi.real) + 1j * r(psi.imag)
     assert np.array_equal(back, want)
+    lat.close()
+
+
+def _fixed16_site_round(psi):
+    """The DD_F16N storage of each site, written out: scale n = FP32 of the
+    largest |component| of the site's 24 reals; q = round-half-even(v *
+    (32767 / n)) in FP64, |q| <= 32767; the value read back is FP32 q times
+    the FP32 product n * (1 / 32767)."""
+    v = np.stack([psi.real, psi.imag], axis=-1).reshape(psi.shape[0], 24)
+    n = np.abs(v).max(axis=1).astype(np.float32)
+    inv = np.where(n > 0, 32767.0 / np.where(n > 0, n.astype(np.float64), 1.0), 0.0)
+    q = np.clip(np.rint(v * inv[:, None]), -32767, 32767)
+    step = (n * (np.float32(1.0) / np.float32(32767.0))).astype(np.float32)
+    back = (q.astype(np.float32) * step[:, None]).astype(np.float64).reshape(psi.shape[0], 12, 2)
+    return (back[..., 0] + 1j * back[..., 1]).reshape(psi.shape)
+
+
+def test_pack_f16n_matches_its_definition():
+    """F16N pack and unpack, bit for bit against the definition above, on
+    sites of very different magnitudes (the per-site scale follows them) and
+    an all-zero site."""
+    lat = dd.Lattice((4, 4, 4, 4), (2, 2, 2, 2))
+    psi = synth.gaussian_spinor(lat.V, 6)
+    psi *= (10.0 ** np.linspace(-12, 6, lat.V))[:, None, None]
+    psi[5] = 0
+    back = lat.from_field(lat.to_field(psi, dd.F16N), dd.F16N)
+    assert np.array_equal(back, _fixed16_site_round(psi))
+    # 2^-16 of the site's largest component at most
+    err = np.abs(back - psi).reshape(lat.V, -1).max(axis=1)
+    big = np.abs(psi).reshape(lat.V, -1).max(axis=1)
+    assert np.all(err <= big * 2.0 ** -15)
     lat.close()
 
 

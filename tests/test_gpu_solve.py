@@ -32,7 +32,7 @@ def test_plain_fp64_workload_4x4x4x4_matches_lu():
     s.close()
 
 
-@pytest.mark.parametrize("prec", [dd.F64, dd.F32, dd.F16, dd.BF16])
+@pytest.mark.parametrize("prec", [dd.F64, dd.F32, dd.F16, dd.BF16, dd.F16N])
 def test_mixed_precision_solve_reaches_1e10(prec):
     s = Setup((8, 8, 8, 8), (4, 4, 4, 4), eps=0.25, n_stout=2, c_sw=1.7, m0=-0.02, prec=prec, seed=21)
     b = synth.gaussian_spinor(s.V, 22)

@@ -19,8 +19,8 @@ from gpu_common import Setup, relerr
 
 pytestmark = pytest.mark.gpu
 
-SAP_TOL = {dd.F64: 1e-12, dd.F32: 5e-7, dd.F16: 1.5e-3, dd.BF16: 1.2e-2}
-DSLASH_TOL = {dd.F64: 1e-13, dd.F32: 1e-6, dd.F16: 1e-3, dd.BF16: 1e-2}
+SAP_TOL = {dd.F64: 1e-12, dd.F32: 5e-7, dd.F16: 1.5e-3, dd.BF16: 1.2e-2, dd.F16N: 1e-3}
+DSLASH_TOL = {dd.F64: 1e-13, dd.F32: 1e-6, dd.F16: 1e-3, dd.BF16: 1e-2, dd.F16N: 1e-3}
 
 
 class forced_variant:
@@ -38,7 +38,7 @@ class forced_variant:
             os.environ["DD_TUNE_VARIANT"] = self.old
 
 
-@pytest.fixture(scope="module", params=[dd.F32, dd.F16, dd.BF16])
+@pytest.fixture(scope="module", params=[dd.F32, dd.F16, dd.BF16, dd.F16N])
 def setup(request):
     s = Setup((8, 8, 8, 16), (4, 4, 4, 4), eps=0.3, n_stout=1, c_sw=1.7, m0=-0.02, prec=request.param, seed=13)
     b = synth.gaussian_spinor(s.V, 14)
