@@ -15,7 +15,7 @@ from gpu_common import Setup, relerr
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", [dd.F32, dd.F16])
+@pytest.mark.parametrize("prec", [dd.F32, dd.F16, dd.F16N])
 def test_batched_solve_equals_single(prec):
     s = Setup((8, 8, 8, 8), (4, 4, 4, 4), eps=0.25, n_stout=2, c_sw=1.7, m0=-0.02, prec=prec, seed=31)
     bs = np.stack([synth.gaussian_spinor(s.V, 40 + r) for r in range(3)])
@@ -52,6 +52,25 @@ def test_server_mixed_lattices_match_solo():
     srv.close()
     small.close()
     large.close()
+
+
+def test_server_serves_f16n_operators():
+    """Requests on an operator with DD_F16N smoother storage: served to 1e-10
+    and bitwise the same as the solo solves."""
+    s = Setup((8, 8, 8, 8), (4, 4, 4, 4), eps=0.25, n_stout=2, c_sw=1.7, m0=-0.02, prec=dd.F16N, seed=47)
+    srv = dd.Server(max_slots=4, max_batch_rhs=4)
+    bs = [np.stack([synth.gaussian_spinor(s.V, 150 + 10 * k + r) for r in range(1 + k)]) for k in range(2)]
+    tickets = [srv.submit(s.op, b if b.shape[0] > 1 else b[0], tol=1e-10) for b in bs]
+    for b, t in zip(bs, tickets):
+        st, x, info = srv.wait(t)
+        assert st == dd.DONE, info
+        x = x.reshape(b.shape)
+        for r in range(b.shape[0]):
+            assert relerr(s.ref.apply(x[r]), b[r]) <= 1e-10
+            x1, _ = s.op.solve(b[r], tol=1e-10)
+            assert np.array_equal(x1, x[r])
+    srv.close()
+    s.close()
 
 
 def test_server_budget_and_cancel():

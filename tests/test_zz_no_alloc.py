@@ -54,7 +54,7 @@ def test_noalloc_solve_matches_dd_solve_twice():
     s.close()
 
 
-@pytest.mark.parametrize("prec", [dd.F64, dd.F32, dd.F16], ids=["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec", [dd.F64, dd.F32, dd.F16, dd.F16N], ids=["f64", "f32", "f16", "f16n"])
 def test_noalloc_on_own_stream_twice(prec):
     """On a non-default stream: two calls in a row, each against dd_solve and
     the oracle's residual (FP64 smoother: native FP64 basis; FP16: the
