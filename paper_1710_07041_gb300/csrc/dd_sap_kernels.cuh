@@ -706,6 +706,26 @@ __global__ void __launch_bounds__(NT, MINB) k_sap_phase(const SapGroups G, const
   const int nbc = g.nblocks / 2, rhs0 = MULTI ? G.grp[k].rhs0 : 0, nrhs = MULTI ? G.grp[k].nrhs : rp.n;
   const int loc = MULTI ? item - G.grp[k].item0 : item;
   const int b = sap_block_of(g, colour, loc % nbc), rt = loc / nbc;
+  if (threadIdx.x == 0) {
+    // this item's own fields that are read later in its lifetime (x at the
+    // end, the stored residual and the incoming flux after the operator's
+    // staging), requested into L2 now; with one CTA per block nothing else
+    // prefetches them
+    constexpr unsigned SB = (unsigned)spinor_site_bytes(Store<S>::prec);
+    constexpr int NC = spinor_chunks<S>();
+    const size_t off = (size_t)b * Vb * SB;
+    for (int q = 0; q < tile; q++) {
+      const int r = rt * tile + q;
+      if (r >= nrhs) break;
+      if (!self_zero) prefetch_l2((const char *)rp.out[rhs0 + r] + off, Vb * SB);
+      if ((mode & SAP_INCR) && !(mode & SAP_FROM_B))
+        for (int c = 0; c < NC; c++) prefetch_l2((const char *)ax.r[rhs0 + r] + off + ((size_t)c * Vb + Vh) * 16, Vh * 16u);
+      if (sizeof(C) == 4 && (mode & SAP_INCR) && (mode & SAP_HALO_E) && flux_layout<C>(g)) {
+        const unsigned fb = 3u * halo_entries(g) * sizeof(PairPair<P>);
+        prefetch_l2((const char *)ax.e[rhs0 + r] + (size_t)b * fb, fb);
+      }
+    }
+  }
   if (threadIdx.x == 0 && item + (int)gridDim.x < G.nitems) {
     const int nitem = item + gridDim.x, nk = MULTI ? sap_group_of(G, nitem) : 0;
     const Geom ng = MULTI ? block_shape<SHAPE>(G.grp[nk].g) : g0;
