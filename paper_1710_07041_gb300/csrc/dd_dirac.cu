@@ -11,6 +11,32 @@
 namespace dd {
 namespace {
 
+// Like load_spinor, but a DD_F16N site comes back unscaled (its 16-bit
+// integers as C): the spinor is out times the returned factor, which the
+// caller folds into a later coefficient (one multiply instead of 24). The
+// other storages return their values and the factor 1.
+template <typename S, typename C>
+__device__ __forceinline__ C load_spinor_unscaled(const void *field, const Geom &g, int b, int s, Spinor<C> &out) {
+  if constexpr (Store<S>::prec == DD_F16N) {
+    DD_CHECK_INDEX(b, g.nblocks);
+    DD_CHECK_INDEX(s, g.Vb);
+    constexpr int NC = spinor_chunks<S>();
+    const char *blk = (const char *)field + (size_t)b * g.Vb * spinor_site_bytes(DD_F16N);
+    const size_t cstride = (size_t)g.Vb * 16;
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      const uint4 v = __ldg((const uint4 *)(blk + c * cstride + (size_t)s * 16));
+      const short *q = (const short *)&v;
+#pragma unroll
+      for (int k = 0; k < 4; k++) out.c[4 * c + k] = {(C)q[2 * k], (C)q[2 * k + 1]};
+    }
+    // the site's scale row follows the block's NC chunk rows
+    return (C)(__ldg((const float *)(blk + NC * cstride) + s) * (1.0f / 32767.0f));
+  } else {
+    load_spinor<S, C>(field, g, b, s, out);
+    return (C)1;
+  }
+}
 
 template <int MU, typename S, typename C>
 __device__ __forceinline__ void dirac_dir(const Geom &g, const Site &t, const void *links, const void *in,
@@ -20,14 +46,20 @@ __device__ __forceinline__ void dirac_dir(const Geom &g, const Site &t, const vo
   bool inside;
   Link<C> u;
   Spinor<C> psi;
+  // hop coefficient -1/2 (times the antiperiodic sign; for DD_F16N also the
+  // neighbour's site scale, its spinor being loaded unscaled)
+  auto coef = [&](C f) {
+    if constexpr (Store<S>::prec == DD_F16N) return (C)(-0.5f * sg) * f;
+    else return (C)(-0.5f * sg);
+  };
   neighbour(g, t, MU, +1, &nb, &ns, &sg, &inside);
-  load_spinor<S, C>(in, g, nb, ns, psi);
+  C f = load_spinor_unscaled<S, C>(in, g, nb, ns, psi);
   load_link<S, C>(links, g, t.b, t.s, MU, u);
-  hop<MU, true>(acc, u, psi, (C)(-0.5f * sg));
+  hop<MU, true>(acc, u, psi, coef(f));
   neighbour(g, t, MU, -1, &nb, &ns, &sg, &inside);
-  load_spinor<S, C>(in, g, nb, ns, psi);
+  f = load_spinor_unscaled<S, C>(in, g, nb, ns, psi);
   load_link<S, C>(links, g, nb, ns, MU, u);
-  hop<MU, false>(acc, u, psi, (C)(-0.5f * sg));
+  hop<MU, false>(acc, u, psi, coef(f));
 }
 
 // TPB threads per CTA; MINB resident CTAs per SM requested from the compiler
