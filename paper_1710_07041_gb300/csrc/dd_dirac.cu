@@ -38,6 +38,61 @@ __device__ __forceinline__ C load_spinor_unscaled(const void *field, const Geom 
   }
 }
 
+// Loads that bypass L1 (the read-only path without allocating a line): for
+// the clover tiles, which the Dslash reads once per site, so that L1 keeps
+// the spinor and link lines that neighbouring sites read again.
+__device__ __forceinline__ uint4 ld_no_l1(const uint4 *p) {
+  uint4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_no_l1(const uint2 *p) {
+  uint2 v;
+  asm("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+
+// out = A psi for a full site, as clover_apply, with the tile chunks read by
+// ld_no_l1 (the chunked layout of clover_block_chunked: chunk c of site s at
+// q[c * n]; with 4 pairs per chunk the last two pairs of both chirality
+// blocks share chunk 8)
+template <typename S, typename C>
+__device__ __forceinline__ void clover_apply_no_l1(const void *clov, size_t n, int b, int s, const Spinor<C> &in,
+                                                   Spinor<C> &out) {
+  using P = typename Store<S>::pair_t;
+  constexpr int CP = chunk_pairs<P>();
+  DD_CHECK_INDEX(s, n);
+  const uint4 *q = (const uint4 *)((const P *)clov + (size_t)b * 36 * n) + s;
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    cpx<C> m[18];
+    if constexpr (CP == 4) {
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const uint4 v = ld_no_l1(q + (size_t)(4 * h + c) * n);
+        const P *pv = (const P *)&v;
+#pragma unroll
+        for (int k = 0; k < 4; k++) m[4 * c + k] = from_pair<C, P>(pv[k]);
+      }
+      const uint2 w = ld_no_l1((const uint2 *)(q + (size_t)8 * n) + h);
+      const P *pw = (const P *)&w;
+      m[16] = from_pair<C, P>(pw[0]);
+      m[17] = from_pair<C, P>(pw[1]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 18 / CP; c++) {
+        const uint4 v = ld_no_l1(q + (size_t)((18 / CP) * h + c) * n);
+        const P *pv = (const P *)&v;
+#pragma unroll
+        for (int k = 0; k < CP; k++) m[CP * c + k] = from_pair<C, P>(pv[k]);
+      }
+    }
+    herm6_mv(m, &in.c[6 * h], &out.c[6 * h]);
+  }
+}
+
 template <int MU, typename S, typename C>
 __device__ __forceinline__ void dirac_dir(const Geom &g, const Site &t, const void *links, const void *in,
                                           Spinor<C> &acc) {
@@ -66,7 +121,8 @@ __device__ __forceinline__ void dirac_dir(const Geom &g, const Site &t, const vo
 // (caps registers so more warps keep loads in flight).
 // SHAPE: the block shape as compile-time constants (see block_shape), or 0.
 // SO: storage of the output fields (the input's, or FP64 for double-float inputs).
-template <typename S, int TPB, int MINB, int SHAPE, typename SO = S>
+// NL1: the clover tiles read without allocating L1 lines.
+template <typename S, int TPB, int MINB, int SHAPE, bool NL1, typename SO = S>
 __global__ void __launch_bounds__(TPB, MINB) k_dirac(Geom g_in, const void *__restrict__ links,
                                                      const void *__restrict__ clov, const RhsPtrs p) {
   using C = typename Store<S>::comp_t;
@@ -81,7 +137,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_dirac(Geom g_in, const void *__re
   Site st = decode(g, b, s);
   Spinor<C> x, acc;
   load_spinor<S, C>(inr, g, b, s, x);
-  clover_apply<S, C>(clov, g.Vb, b, s, x, acc);
+  if constexpr (NL1) clover_apply_no_l1<S, C>(clov, g.Vb, b, s, x, acc);
+  else clover_apply<S, C>(clov, g.Vb, b, s, x, acc);
   dirac_dir<0, S, C>(g, st, links, inr, acc);
   dirac_dir<1, S, C>(g, st, links, inr, acc);
   dirac_dir<2, S, C>(g, st, links, inr, acc);
@@ -89,41 +146,46 @@ __global__ void __launch_bounds__(TPB, MINB) k_dirac(Geom g_in, const void *__re
   store_spinor<SO, C>(p.out[r], g, b, s, acc);
 }
 
-template <typename S, int TPB, int MINB, typename SO = S>
+template <typename S, int TPB, int MINB, bool NL1, typename SO = S>
 int dirac_v(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st) {
   long long n = g.V * p.n;
   const unsigned grid = (unsigned)((n + TPB - 1) / TPB);
-  if (shape_of(g) == 1) k_dirac<S, TPB, MINB, 1, SO><<<grid, TPB, 0, st>>>(g, f.links, f.clov, p);
-  else k_dirac<S, TPB, MINB, 0, SO><<<grid, TPB, 0, st>>>(g, f.links, f.clov, p);
+  if (shape_of(g) == 1) k_dirac<S, TPB, MINB, 1, NL1, SO><<<grid, TPB, 0, st>>>(g, f.links, f.clov, p);
+  else k_dirac<S, TPB, MINB, 0, NL1, SO><<<grid, TPB, 0, st>>>(g, f.links, f.clov, p);
   return launched("k_dirac");
 }
 
 // Launch variants (threads per CTA, CTAs per SM the register budget must
 // allow): (128, 5) ~100 registers, (128, 6) ~80, (256, 2) ~128 and (256, 3)
-// ~85; for FP64 (128, 4) ~128, (128, 3) ~168, (256, 2) ~128, (256, 1) 255.
+// ~85; for FP64 (128, 4) ~128, (128, 3) ~168, (256, 2) ~128, (256, 1) 255;
+// variants 4-7 are 0-3 with the clover tiles read past L1.
 // A 256-thread CTA covers one whole 4^4 block, so interior neighbours are
 // read by the same SM.
-constexpr int DIRAC_VARIANTS = 4;
+constexpr int DIRAC_VARIANTS = 8;
 
 template <typename S, typename SO = S>
 int dirac_t(const Geom &g, const OpFields &f, const RhsPtrs &p, cudaStream_t st) {
-  auto run = [&](int v) {
+  auto shape = [&](int v, auto nl1) {
+    constexpr bool N = decltype(nl1)::value;
     if constexpr (Store<S>::prec == DD_F64 || Store<S>::prec == DD_PREC_DF) {
       // FP64 and double-float values take two registers each: looser caps
       switch (v) {
-        case 1: return dirac_v<S, 128, 3, SO>(g, f, p, st);
-        case 2: return dirac_v<S, 256, 2, SO>(g, f, p, st);
-        case 3: return dirac_v<S, 256, 1, SO>(g, f, p, st);
-        default: return dirac_v<S, 128, 4, SO>(g, f, p, st);
+        case 1: return dirac_v<S, 128, 3, N, SO>(g, f, p, st);
+        case 2: return dirac_v<S, 256, 2, N, SO>(g, f, p, st);
+        case 3: return dirac_v<S, 256, 1, N, SO>(g, f, p, st);
+        default: return dirac_v<S, 128, 4, N, SO>(g, f, p, st);
       }
     } else {
       switch (v) {
-        case 1: return dirac_v<S, 128, 6>(g, f, p, st);
-        case 2: return dirac_v<S, 256, 2>(g, f, p, st);
-        case 3: return dirac_v<S, 256, 3>(g, f, p, st);
-        default: return dirac_v<S, 128, 5>(g, f, p, st);
+        case 1: return dirac_v<S, 128, 6, N>(g, f, p, st);
+        case 2: return dirac_v<S, 256, 2, N>(g, f, p, st);
+        case 3: return dirac_v<S, 256, 3, N>(g, f, p, st);
+        default: return dirac_v<S, 128, 5, N>(g, f, p, st);
       }
     }
+  };
+  auto run = [&](int v) {
+    return v >= 4 ? shape(v - 4, std::true_type{}) : shape(v, std::false_type{});
   };
   int v = 0;
   int rc = tuned_variant(tune_key("dirac", g, f.prec, p.n), DIRAC_VARIANTS, run, st, &v);

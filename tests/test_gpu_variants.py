@@ -4,7 +4,8 @@ shared-memory layouts (all tiles staged with one or two CTAs per SM, links
 only staged, nothing staged; for 16-bit storage also the two-CTA layouts with
 the MR loop unrolled by parity; for 32- and 16-bit storage the links staged
 with the clover blocks in tensor memory), each with the one-CTA-per-block and the
-persistent grid, and the four Dslash launch shapes; on the 4^4 block shape
+persistent grid, and the eight Dslash launch variants (four launch shapes,
+each with the clover tiles read through L1 or past it); on the 4^4 block shape
 and, in the second half, on the 8 x 4^3 block (512-thread CTAs, the shape
 the batched workload picks) in every precision, and FP64 on the 4^4 shape.
 Bounds as in test_gpu_sap.py and test_gpu_operator.py."""
@@ -58,7 +59,7 @@ def test_sap_variant(setup, k):
     assert relerr(got, want) <= SAP_TOL[s.prec]
 
 
-@pytest.mark.parametrize("k", range(4))
+@pytest.mark.parametrize("k", range(8))
 def test_dslash_variant(setup, k):
     s, b, _, want = setup
     fin, fout = s.lat.to_field(b, s.prec), s.lat.new_field(s.prec)
@@ -71,7 +72,7 @@ def test_dslash_variant(setup, k):
 # The 8 x 4^3 block (SHAPE 2: 512 threads per CTA) in every precision, and
 # FP64 on the 4^4 block: the Schwarz layouts (tiles in shared memory; for 32-
 # and 16-bit storage also the clover blocks in tensor memory), each with one
-# CTA per block and the persistent grid; four Dslash launch shapes.
+# CTA per block and the persistent grid; eight Dslash launch variants.
 @pytest.fixture(scope="module",
                 params=[(dd.F64, (4, 4, 4, 4)), (dd.F64, (8, 4, 4, 4)), (dd.F32, (8, 4, 4, 4)),
                         (dd.F16, (8, 4, 4, 4)), (dd.BF16, (8, 4, 4, 4))],
@@ -96,7 +97,7 @@ def test_sap_variant_shapes(setup2, k):
     assert relerr(got, want) <= SAP_TOL[s.prec]
 
 
-@pytest.mark.parametrize("k", range(4))
+@pytest.mark.parametrize("k", range(8))
 def test_dslash_variant_shapes(setup2, k):
     s, b, _, want = setup2
     fin, fout = s.lat.to_field(b, s.prec), s.lat.new_field(s.prec)
