@@ -10,7 +10,8 @@ dense linear algebra on tiny lattices and by exact invariances:
     reconstruction), and one MR step is the least-squares optimum on span{bhat},
   * one sweep with exact block solves equals K0 b + K1 (b - D K0 b),
   * complex homogeneity and gauge covariance of the fixed-step smoother,
-  * FGMRES reaches a true residual of 1e-10 and agrees with a dense LU solve.
+  * FGMRES reaches a true residual of 1e-10 and agrees with a dense LU solve,
+    and on the free field with the exact solution built in momentum space.
 """
 import numpy as np
 import pytest
@@ -197,3 +198,41 @@ def test_gram_schmidt_step_is_orthogonal_projection():
     assert np.abs(Q.conj().T @ w2).max() < 1e-13
     w0, h0 = oracle.gram_schmidt(np.zeros((0, n), dtype=complex), w)
     assert h0.size == 0 and np.array_equal(w0, w)
+
+
+def test_free_field_solve_matches_momentum_space():
+    """U = 1 on 8 x 4^3 (antiperiodic time): the SAP-FGMRES solution equals
+    the exact solution built in momentum space, independent of any dense
+    solve. With the time twist e^{i pi t / T}, a field is a sum of plane waves
+    e^{ipn} with p_mu = 2 pi k / L_mu (space) and p_t = (2k + 1) pi / T, and on
+    each the operator is the 12 x 12 matrix
+    D(p) = (m0 + sum_mu (1 - cos p_mu)) + i sum_mu (g_mu x 1_3) sin p_mu
+    (the closed form pinned by test_free_field_plane_waves). D(p) is normal, so
+    the condition number of D is the ratio of the largest and smallest
+    |M(p) +- i |sin p||; the solution error is bounded by it times 1e-10."""
+    dims = (8, 4, 4, 4)
+    T, Z, Y, X = dims
+    Vf = T * Z * Y * X
+    m0 = 0.1
+    opf = oracle.Operator(dims, synth.unit_gauge(dims), c_sw=1.0, m0=m0)
+    b = synth.gaussian_spinor(Vf, 91).reshape(T, Z, Y, X, 12)
+    t = np.arange(T).reshape(T, 1, 1, 1, 1)
+    twist = np.exp(1j * np.pi * t / T)
+    c = np.fft.fftn(b / twist, axes=(0, 1, 2, 3))   # plane-wave coefficients x V
+    g = [np.kron(oracle.gamma(mu), np.eye(3)) for mu in range(4)]
+    kt, kz, ky, kx = np.meshgrid(np.arange(T), np.arange(Z), np.arange(Y), np.arange(X), indexing="ij")
+    p = [2 * np.pi * kx / X, 2 * np.pi * ky / Y, 2 * np.pi * kz / Z, (2 * kt + 1) * np.pi / T]
+    M = m0 + sum(1 - np.cos(q) for q in p)
+    s2 = sum(np.sin(q) ** 2 for q in p)
+    Dp = M[..., None, None] * np.eye(12) + 1j * sum(np.sin(p[mu])[..., None, None] * g[mu] for mu in range(4))
+    xt = np.linalg.solve(Dp, c[..., None])[..., 0]
+    x_exact = (np.fft.ifftn(xt, axes=(0, 1, 2, 3)) * twist).reshape(Vf, 12)
+    b = b.reshape(Vf, 12)
+    # the momentum-space construction is the inverse of the oracle's D
+    assert np.linalg.norm(opf.apply(x_exact).reshape(Vf, 12) - b) / np.linalg.norm(b) < 1e-13
+    x, ok, st = opf.fgmres((2, 2, 2, 2), b, restart=16, tol=1e-10, max_iter=500, nsweep=4, nmr=3)
+    assert ok and st["rel_residual"] <= 1e-10
+    sv = np.sqrt(M ** 2 + s2)
+    kappa = sv.max() / sv.min()
+    err = np.linalg.norm(x.reshape(Vf, 12) - x_exact) / np.linalg.norm(x_exact)
+    assert err <= kappa * 1e-10
