@@ -52,7 +52,7 @@ struct Request {
   std::vector<dd_solve_info> info;
   int state = DD_QUEUED;
   int remaining = 0, next_rhs = 0, worst = DD_OK;
-  volatile int cancel = 0;
+  std::atomic<int> cancel{0};   // set by dd_cancel / shutdown, read by running solves
   clk::time_point t_submit, t_done;
 };
 
@@ -66,7 +66,10 @@ struct Worker {
   size_t per = 0;          // reserved device bytes per slot
   size_t bytes = 0;        // slots x per
   cudaStream_t stream = nullptr;
-  std::deque<Request *> queue;  // admitted requests with right-hand sides left to start
+  // admitted requests with right-hand sides left to start: a request leaves
+  // the queue when its last right-hand side is handed to a slot, so the queue
+  // never points at a request that can finish (and be freed by dd_poll)
+  std::deque<Request *> queue;
   std::thread th;
   bool exited = false;
 };
@@ -149,6 +152,7 @@ static void worker_main(Worker *w) {
       }
       int k = r->next_rhs++;
       r->state = DD_RUNNING;
+      if (r->next_rhs >= r->nrhs) w->queue.pop_front();   // every right-hand side started
       const size_t fs = (size_t)r->op->lat->g.V * 24;
       job.op = r->op;
       job.b = r->b.data() + k * fs;

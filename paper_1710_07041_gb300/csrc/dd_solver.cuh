@@ -1,5 +1,6 @@
 // Outer FGMRES solver internals (see dd_solver.cu).
 #pragma once
+#include <atomic>
 #include <chrono>
 #include <complex>
 #include <functional>
@@ -21,7 +22,7 @@ struct RhsJob {
   int x_on_device = 0;
   int use_x0 = 0;
   dd_solve_info *info = nullptr;      // result record (may be null)
-  const volatile int *cancel = nullptr;
+  const std::atomic<int> *cancel = nullptr;
   std::function<void(int status)> done;  // called after x and info are written
 };
 
