@@ -34,6 +34,7 @@
 // graph cache, the wait counter); the kernel templates are in
 // dd_sap_kernels.cuh and instantiated per precision in dd_sap_<prec>.cu.
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 
@@ -125,11 +126,22 @@ __global__ void k_wait_selftest(const uint4 *src, int expire, int *result, unsig
 // When the caller's stream is itself being captured the launches go into the
 // caller's graph directly. DD_SAP_GRAPHS=0 disables the graphs, and so does
 // a DirectLaunch scope on the calling thread (dd_solve_noalloc).
+// An instantiated graph, destroyed when its last holder lets go: a thread
+// that looked one up keeps it alive through its launch even if another thread
+// flushes the cache meanwhile (a destroyed graph that is still running on the
+// device is freed by the driver once it completes).
+struct GraphExec {
+  cudaGraphExec_t exec = nullptr;
+  ~GraphExec() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
 struct GraphCache {
   std::mutex mu;
-  std::map<std::string, cudaGraphExec_t> execs;
+  std::map<std::string, std::shared_ptr<GraphExec>> execs;
 };
-static GraphCache g_graphs;
+// never destroyed: no CUDA call runs at process exit
+static GraphCache &g_graphs = *new GraphCache;
 
 int sap_launch_as_graph(const std::string &key, int variant, int nkernels, const RhsPtrs &rp, const AuxPtrs *ax,
                         const std::function<int()> &enqueue, cudaStream_t st) {
@@ -145,13 +157,14 @@ int sap_launch_as_graph(const std::string &key, int variant, int nkernels, const
     k += "|" + std::to_string((uintptr_t)rp.in[i]) + ":" + std::to_string((uintptr_t)rp.out[i]);
     if (ax) k += ":" + std::to_string((uintptr_t)ax->e[i]) + ":" + std::to_string((uintptr_t)ax->r[i]);
   }
-  cudaGraphExec_t exec = nullptr;
+  std::shared_ptr<GraphExec> held;
   {
     std::lock_guard<std::mutex> lk(g_graphs.mu);
     auto it = g_graphs.execs.find(k);
-    if (it != g_graphs.execs.end()) exec = it->second;
+    if (it != g_graphs.execs.end()) held = it->second;
   }
-  if (!exec) {
+  if (!held) {
+    cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     DD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     int rc = enqueue();
@@ -164,16 +177,17 @@ int sap_launch_as_graph(const std::string &key, int variant, int nkernels, const
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "sap graph instantiate");
+    held = std::make_shared<GraphExec>();
+    held->exec = exec;
     std::lock_guard<std::mutex> lk(g_graphs.mu);
-    if (g_graphs.execs.size() >= 256) {   // bounded cache: start over when full
-      for (auto &kv : g_graphs.execs) cudaGraphExecDestroy(kv.second);
-      g_graphs.execs.clear();
-    }
-    g_graphs.execs[k] = exec;
+    if (g_graphs.execs.size() >= 256) g_graphs.execs.clear();   // bounded cache: start over when full
+    // (another thread may have stored the same key meanwhile: this one's
+    // graph is then launched once and freed)
+    g_graphs.execs.emplace(k, held);
   } else {
     count_launches(nkernels);
   }
-  return cuda_fail(cudaGraphLaunch(exec, st), "sap graph launch");
+  return cuda_fail(cudaGraphLaunch(held->exec, st), "sap graph launch");
 }
 
 
