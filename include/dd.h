@@ -373,7 +373,10 @@ enum { DD_QUEUED = 0, DD_RUNNING = 1, DD_DONE = 2, DD_FAILED = 3, DD_CANCELLED_S
 int dd_server_create(const dd_server_params *p, dd_server_t *out);
 
 /* Queue a request (b is copied). *ticket identifies it. DD_EBUSY if the
- * request alone can never fit the memory budget. */
+ * request alone can never fit the memory budget. The server does not take a
+ * reference on req->op (or on params.mg): keep them alive until the request
+ * has reached a final state (DONE, FAILED or CANCELLED, seen by dd_poll) or
+ * the server has been destroyed. */
 int dd_submit(dd_server_t s, const dd_request *req, uint64_t *ticket);
 
 /* State of a ticket. When DONE, x_out (may be NULL) receives nrhs canonical
