@@ -441,12 +441,12 @@ class Server(Handle):
         req = Request(op.handle, b.ctypes.data, nrhs, sp)
         t = ctypes.c_uint64()
         _check(lib().dd_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "dd_submit")
-        self._keep[t.value] = (op, nrhs)
+        self._keep[t.value] = (op, nrhs, mg)   # the library holds no reference on op or mg
         return t.value
 
     def poll(self, ticket: int):
         """(state, x or None, infos or None); x/infos once the request has ended."""
-        op, nrhs = self._keep[ticket]
+        op, nrhs, _ = self._keep[ticket]
         st = ctypes.c_int()
         x = np.empty((nrhs, op.lat.V, 4, 3), dtype=np.complex128)
         infos = (SolveInfo * nrhs)()
